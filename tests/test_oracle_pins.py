@@ -1,0 +1,340 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+Each test checks the oracle against a closed form, an exact invariant, a
+special case that reduces to a textbook result, or an independent matrix
+construction, chosen so that a plausible slip (dropped term, wrong sign,
+wrong index, transposed axis, wrong boundary rule) breaks at least one.
+
+Definitions pinned: eq. (1)/(2) diffusion with diagonal D, the 7-point
+Laplacian, eq. (5) forward Euler, first-order upwind advection and the
+Cahn-Hilliard chained Laplacian of Section 4.1, boundary layers of
+Section 4.1, and the reaction terms of the benchmark problems.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1004_0480_gb300 import workloads as W
+
+
+def _diff_cfg(shape, D=(1.0, 1.0, 1.0), dt=0.05, bc="neumann", h=1.0):
+    cfg = W.diffusion_blob(shape=shape, dt=dt, h=h)
+    cfg["D"] = [list(D)]
+    cfg["bc"] = [[bc] * 6]
+    return cfg
+
+
+# --------------------------------------------------------------------------
+# Laplacian + Euler: Fourier modes decay by the exact discrete symbol
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("impl", ["c", "np"])
+def test_fourier_mode_periodic(orc, impl):
+    nx, ny, nz = 16, 12, 10
+    m = (2, 1, 3)
+    D = (1.0, 0.5, 0.25)
+    h, dt = 0.7, 0.05
+    cfg = _diff_cfg((nx, ny, nz), D=D, dt=dt, bc="periodic", h=h)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    mode = (np.cos(2 * np.pi * m[0] * x / nx) * np.cos(2 * np.pi * m[1] * y / ny)
+            * np.cos(2 * np.pi * m[2] * z / nz))
+    c0 = (1.0 + mode)[None]
+    n = 25
+    g = 1.0 - 4.0 * sum(D[d] * dt / h ** 2 * math.sin(math.pi * m[d] / N) ** 2
+                        for d, N in enumerate((nx, ny, nz)))
+    run = orc.run if impl == "c" else orc.np_run
+    out = run(cfg, c0, n)[0]
+    np.testing.assert_allclose(out, 1.0 + g ** n * mode, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("impl", ["c", "np"])
+def test_fourier_mode_neumann(orc, impl):
+    # cell-centred zero-flux eigenmodes cos(pi m (i + 1/2) / n)
+    nx, ny, nz = 9, 14, 11
+    m = (1, 3, 2)
+    D = (0.3, 1.0, 0.6)
+    dt = 0.08
+    cfg = _diff_cfg((nx, ny, nz), D=D, dt=dt, bc="neumann")
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    mode = (np.cos(np.pi * m[0] * (x + 0.5) / nx) * np.cos(np.pi * m[1] * (y + 0.5) / ny)
+            * np.cos(np.pi * m[2] * (z + 0.5) / nz))
+    n = 30
+    g = 1.0 - 4.0 * sum(D[d] * dt * math.sin(math.pi * m[d] / (2 * N)) ** 2
+                        for d, N in enumerate((nx, ny, nz)))
+    run = orc.run if impl == "c" else orc.np_run
+    out = run(cfg, (2.0 + mode)[None], n)[0]
+    np.testing.assert_allclose(out, 2.0 + g ** n * mode, rtol=0, atol=1e-12)
+
+
+def test_stability_bound_checkerboard(orc):
+    # the checkerboard is the fastest mode: g = 1 - 12 r with r = D dt / h^2;
+    # it stays bounded iff dt <= h^2 / (6 D)
+    n = 8
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    cb = ((-1.0) ** (x + y + z))[None]
+    for factor, grows in ((1.0 + 1e-2, True), (1.0 - 1e-2, False)):
+        dt = factor / 6.0
+        cfg = _diff_cfg((n, n, n), dt=dt, bc="periodic")
+        out = orc.run(cfg, cb, 200)
+        g = 1.0 - 12.0 * dt
+        np.testing.assert_allclose(out, g ** 200 * cb, rtol=1e-10, atol=0)
+        assert (np.abs(out).max() > 1.0) == grows
+
+
+@pytest.mark.parametrize("bc", ["neumann", "periodic"])
+def test_mass_conserved_pure_diffusion(orc, bc):
+    cfg = _diff_cfg((10, 7, 9), D=(1.0, 0.4, 0.7), dt=0.1, bc=bc)
+    c0 = W.initial_fields(W.with_(cfg, init="uniform_noise"), seed=11).astype(np.float64)
+    out = orc.run(cfg, c0, 40)
+    assert abs(out.sum() - c0.sum()) <= 1e-12 * abs(c0.sum())
+    assert not np.allclose(out, c0)
+
+
+# --------------------------------------------------------------------------
+# independent matrix construction on a tiny grid (Kronecker sums)
+# --------------------------------------------------------------------------
+def _lap1d(n, periodic):
+    A = -2.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+    if periodic:
+        A[0, -1] = A[-1, 0] = 1.0
+    else:
+        A[0, 0] = A[-1, -1] = -1.0   # zero flux: ghost equals the face cell
+    return A
+
+
+def _upwind1d(n, periodic):
+    # -(c_i - c_{i-1}) for positive velocity
+    B = -np.eye(n) + np.eye(n, k=-1)
+    if periodic:
+        B[0, -1] = 1.0
+    else:
+        B[0, 0] = 0.0                # zero-gradient inflow
+    return B
+
+
+@pytest.mark.parametrize("bc", ["neumann", "periodic"])
+def test_dense_operator_power(orc, bc):
+    nx, ny, nz = 3, 4, 5
+    per = bc == "periodic"
+    D = (0.3, 0.2, 0.1)
+    h, dt, u = 1.0, 0.2, 0.8
+    cfg = _diff_cfg((nx, ny, nz), D=D, dt=dt, bc=bc, h=h)
+    cfg["wind"] = dict(kind="const", u0=u)
+    Ix, Iy, Iz = np.eye(nx), np.eye(ny), np.eye(nz)
+    # array index order (z, y, x) -> kron(z, y, x)
+    A = (D[0] * np.kron(Iz, np.kron(Iy, _lap1d(nx, per)))
+         + D[1] * np.kron(Iz, np.kron(_lap1d(ny, per), Ix))
+         + D[2] * np.kron(_lap1d(nz, per), np.kron(Iy, Ix))) / h ** 2
+    A += u / h * np.kron(Iz, np.kron(Iy, _upwind1d(nx, per)))
+    step = np.eye(nx * ny * nz) + dt * A
+    c0 = W.uniform01(5, 0, nx * ny * nz)
+    n = 17
+    ref = np.linalg.matrix_power(step, n) @ c0
+    out = orc.run(cfg, c0.reshape(1, nz, ny, nx), n).ravel()
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# advection
+# --------------------------------------------------------------------------
+def test_upwind_courant_one_is_exact_shift(orc):
+    nx, ny, nz = 12, 3, 4
+    h, dt = 1.0, 0.25
+    cfg = _diff_cfg((nx, ny, nz), D=(0, 0, 0), dt=dt, bc="periodic", h=h)
+    cfg["wind"] = dict(kind="const", u0=h / dt)
+    c0 = W.uniform01(9, 0, nx * ny * nz).reshape(1, nz, ny, nx)
+    n = 5
+    out = orc.run(cfg, c0, n)
+    np.testing.assert_allclose(out, np.roll(c0, n, axis=3), rtol=0, atol=1e-15)
+
+
+def test_log_wind_profile_on_linear_field(orc):
+    # c = alpha x + beta, no diffusion: away from the inflow face the update
+    # is c - dt u(z) alpha / h with u(z) = ln(1+z)/ln(1+nz), z the cell index;
+    # at x = 0 the zero-gradient ghost gives no change
+    nx, ny, nz = 6, 2, 7
+    alpha, beta, dt, h = 0.5, 2.0, 0.1, 1.0
+    cfg = _diff_cfg((nx, ny, nz), D=(0, 0, 0), dt=dt, bc="neumann", h=h)
+    cfg["wind"] = dict(kind="log", u0=1.0)
+    x = np.arange(nx)[None, None, :] * np.ones((nz, ny, 1))
+    c0 = (alpha * x + beta)[None]
+    out = orc.run(cfg, c0, 1)[0]
+    uz = np.log(1.0 + np.arange(nz)) / np.log(1.0 + nz)
+    expect = c0[0] - dt * uz[:, None, None] * alpha / h
+    expect[:, :, 0] = c0[0][:, :, 0]
+    np.testing.assert_allclose(out, expect, rtol=0, atol=1e-14)
+
+
+def test_log_wind_budget_telescopes(orc):
+    # sum over x of the upwind term telescopes to -u (c_{n-1} - c_0) / h
+    cfg = W.air((10, 6, 8), src=(1, 1, 1), src_rate=0.0, j=0.0, k=0.0)
+    c0 = W.initial_fields(W.with_(cfg, init="uniform_noise"), seed=3).astype(np.float64)
+    c1 = orc.run(cfg, c0, 1)
+    uz = np.log1p(np.arange(8.0)) / np.log1p(8.0)
+    for s in range(3):
+        flux = (uz[:, None] * (c0[s, :, :, -1] - c0[s, :, :, 0])).sum()
+        assert abs((c1[s].sum() - c0[s].sum()) - (-cfg["dt"] * flux)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# reactions
+# --------------------------------------------------------------------------
+def test_brusselator_steady_state_bitwise(orc):
+    cfg = W.brusselator(shape=(6, 5, 4), bc="periodic")
+    c0 = np.empty((2, 4, 5, 6))
+    c0[0], c0[1] = 3.0, 3.0     # (a, b/a) with a = 3, b = 9
+    out = orc.run(cfg, c0, 50)
+    assert np.array_equal(out, c0)
+
+
+def test_brusselator_sum_identity(orc):
+    # f + g = a - u for the Brusselator, so for a uniform state
+    # (u + v)_{n+1} = (u + v)_n + dt (a - u_n), whatever u^2 v is
+    cfg = W.brusselator(shape=(4, 4, 4))
+    c0 = np.empty((2, 4, 4, 4))
+    c0[0], c0[1] = 1.3, 2.1
+    c1 = orc.run(cfg, c0, 1)
+    assert np.ptp(c1[0]) == 0 and np.ptp(c1[1]) == 0
+    lhs = c1[0, 0, 0, 0] + c1[1, 0, 0, 0]
+    rhs = 1.3 + 2.1 + cfg["dt"] * (3.0 - 1.3)
+    assert abs(lhs - rhs) < 1e-14
+
+
+def test_brusselator_linearised_mode(orc):
+    # small periodic mode about (a, b/a): per step the amplitudes follow
+    # I + dt (J - lam diag(Du, Dv)), J = [[b-1, a^2], [-b, -a^2]] (textbook
+    # Brusselator Jacobian), lam = 4 sin^2(pi m / n) / h^2
+    a, b, Du, Dv, dt, n = 3.0, 9.0, 2.0, 16.0, 0.005, 16
+    cfg = W.brusselator(shape=(n, 4, 4), a=a, b=b, Du=Du, Dv=Dv, dt=dt)
+    m = 2
+    x = np.arange(n)
+    mode = np.cos(2 * np.pi * m * x / n)[None, None, :] * np.ones((4, 4, 1))
+    eps = np.array([1e-7, -2e-7])
+    c0 = np.stack([a + eps[0] * mode, b / a + eps[1] * mode])
+    steps = 60
+    out = orc.run(cfg, c0, steps)
+    lam = 4.0 * math.sin(math.pi * m / n) ** 2
+    J = np.array([[b - 1.0, a * a], [-b, -a * a]]) - lam * np.diag([Du, Dv])
+    amp = np.linalg.matrix_power(np.eye(2) + dt * J, steps) @ eps
+    got = np.array([(out[0] - a)[0, 0, 0], (out[1] - b / a)[0, 0, 0]])
+    np.testing.assert_allclose(got, amp, rtol=2e-5)
+
+
+def test_air_photostationary_state_bitwise(orc):
+    # j NO2 = k NO O3 is a steady state of NO2 <-> NO + O3
+    cfg = W.air((5, 4, 3), src=(0, 0, 0), src_rate=0.0, j=0.5, k=2.0)
+    cfg["wind"] = None
+    c0 = np.empty((3, 3, 4, 5))
+    c0[0], c0[1], c0[2] = 1.0, 4.0, 1.0     # NO, NO2, O3
+    out = orc.run(cfg, c0, 20)
+    assert np.array_equal(out, c0)
+
+
+def test_air_first_order_photolysis(orc):
+    # with k = 0, NO2 decays as (1 - j dt)^n, NO and O3 gain what it loses
+    cfg = W.air((4, 4, 4), src=(0, 0, 0), src_rate=0.0, j=0.5, k=0.0)
+    cfg["wind"] = None
+    c0 = np.zeros((3, 4, 4, 4))
+    c0[1] = 1.0
+    n = 7
+    out = orc.run(cfg, c0, n)
+    nd = (1.0 - 0.5 * cfg["dt"]) ** n
+    np.testing.assert_allclose(out[1], nd, rtol=1e-14)
+    np.testing.assert_allclose(out[0], 1.0 - nd, rtol=1e-13)
+    np.testing.assert_allclose(out[2], 1.0 - nd, rtol=1e-13)
+
+
+def test_air_budgets_and_source_position(orc):
+    cfg = W.air((9, 7, 6), src=(2, 5, 3), src_rate=1.0)
+    cfg["wind"] = None
+    c0 = W.initial_fields(cfg).astype(np.float64)
+    n = 6
+    out = orc.run(cfg, c0, n)
+    tot = lambda a: a.sum()
+    # NO2 + O3 is conserved; NO + NO2 grows by dt * rate per step
+    assert abs(tot(out[1] + out[2]) - tot(c0[1] + c0[2])) < 1e-11
+    assert abs(tot(out[0] + out[1]) - tot(c0[0] + c0[1]) - n * cfg["dt"]) < 1e-11
+    # the emission lands at (x, y, z) = (2, 5, 3)
+    z0 = np.zeros_like(c0)
+    one = orc.run(cfg, z0, 1)
+    assert np.unravel_index(np.argmax(one[0]), one[0].shape) == (3, 5, 2)
+    assert one[0].sum() == pytest.approx(cfg["dt"], abs=1e-15)
+
+
+def test_front_reaction_invariants(orc):
+    # a + b -> c: a - b and a + c are conserved; one step of a uniform state
+    # removes dt k a b from a and b
+    cfg = W.ch_front(shape=(5, 5, 5))
+    cfg["bc"] = [["neumann"] * 6 for _ in range(3)]
+    c0 = np.empty((3, 5, 5, 5))
+    c0[0], c0[1], c0[2] = 0.7, 1.4, 0.25
+    out = orc.run(cfg, c0, 10)
+    assert np.ptp(out) < 1e-15 or all(np.ptp(out[s]) == 0 for s in range(3))
+    np.testing.assert_allclose(out[0] - out[1], 0.7 - 1.4, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(out[0] + out[2], 0.95, rtol=0, atol=1e-14)
+    one = orc.run(cfg, c0, 1)
+    np.testing.assert_allclose(one[0], 0.7 - cfg["dt"] * 0.7 * 1.4, rtol=1e-15)
+
+
+@pytest.mark.parametrize("cbar,fprime", [(0.0, 2.0), (0.5, -1.0)])
+def test_cahn_hilliard_linear_symbol(orc, cbar, fprime):
+    # about a uniform c, a small mode evolves by
+    # 1 - dt M lam (kappa lam + f''(cbar)),  f'(c) = 2c(c-1)(2c-1)
+    n, dt, M, kappa = 12, 0.01, 0.1, 1.0
+    cfg = W.ch_front(shape=(n, n, 4), dt=dt, M=M, kappa=kappa, k=0.0, Da=0.0, Db=0.0)
+    cfg["bc"] = [["periodic"] * 6 for _ in range(3)]
+    cfg["bc_value"] = [[0.0] * 6 for _ in range(3)]
+    mx, my = 1, 2
+    z, y, x = np.meshgrid(np.arange(4), np.arange(n), np.arange(n), indexing="ij")
+    mode = np.cos(2 * np.pi * mx * x / n) * np.cos(2 * np.pi * my * y / n)
+    eps = 1e-7
+    c0 = np.zeros((3, 4, n, n))
+    c0[2] = cbar + eps * mode
+    steps = 40
+    out = orc.run(cfg, c0, steps)
+    lam = 4.0 * (math.sin(math.pi * mx / n) ** 2 + math.sin(math.pi * my / n) ** 2)
+    g = 1.0 - dt * M * lam * (kappa * lam + fprime)
+    np.testing.assert_allclose(out[2] - cbar, g ** steps * eps * mode, rtol=0,
+                               atol=1e-5 * eps)
+
+
+def test_cahn_hilliard_mass_conserved_neumann(orc):
+    cfg = W.ch_front(shape=(8, 7, 6), k=0.0)
+    cfg["bc"] = [["neumann"] * 6 for _ in range(3)]
+    c0 = W.initial_fields(cfg).astype(np.float64)
+    c0[2] += 0.3
+    out = orc.run(cfg, c0, 50)
+    assert abs(out[2].sum() - c0[2].sum()) < 1e-12 * c0[2].size
+    assert not np.allclose(out[2], c0[2])
+
+
+# --------------------------------------------------------------------------
+# held (Dirichlet) boundary layers
+# --------------------------------------------------------------------------
+def test_dirichlet_linear_profile_is_steady(orc):
+    # held layers at z = 0 (value 10) and z = nz-1 (value 0): the linear
+    # profile through the cell planes has zero second difference
+    nz = 9
+    cfg = _diff_cfg((5, 4, nz), dt=0.1, bc="neumann")
+    cfg["bc"][0][4] = cfg["bc"][0][5] = "dirichlet"
+    cfg["bc_value"] = [[0, 0, 0, 0, 10.0, 0.0]]
+    prof = 10.0 * (1.0 - np.arange(nz) / (nz - 1))
+    c0 = (prof[:, None, None] * np.ones((nz, 4, 5)))[None]
+    out = orc.run(cfg, c0, 30)
+    np.testing.assert_allclose(out, c0, rtol=0, atol=1e-12)
+    # a zero start relaxes towards that profile, the layers held throughout
+    out = orc.run(cfg, np.zeros_like(c0), 3000)
+    assert np.all(out[0, 0] == 10.0) and np.all(out[0, -1] == 0.0)
+    np.testing.assert_allclose(out, c0, rtol=0, atol=1e-6)
+
+
+def test_oracles_agree_on_every_family(orc):
+    cases = [W.diffusion_blob(8), W.brusselator(8), W.ch_front(8),
+             W.air((8, 8, 8), src=(3, 4, 2)),
+             W.brusselator(shape=(7, 9, 6), bc="neumann"),
+             W.ch_front(shape=(9, 7, 10)), W.air((11, 6, 5), src=(10, 0, 4))]
+    for cfg in cases:
+        f = W.initial_fields(cfg)
+        a = orc.run(cfg, f, 9)
+        b = orc.np_run(cfg, f, 9)
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12 * np.abs(a).max())
