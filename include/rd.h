@@ -1,0 +1,260 @@
+/*
+ * rd.h -- C ABI of the GB300 (sm_103a) reaction-diffusion stepper.
+ *
+ * The library advances reaction-diffusion systems with the method of lines
+ * of the paper's Section 2: a 7-point finite-difference Laplacian per
+ * species and axis, the pointwise reaction term R(c) of eq. (1), optional
+ * first-order upwind advection and a point emission term (Section 4.1 and
+ * Table 1), and the forward-Euler update of eq. (5).  Every species is
+ * stored as its own array, x fastest, as in the paper's kernels (Tables
+ * 4-5), two time levels per species (the "first"/"second" arrays of the
+ * paper's host loop, Table 3).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns rd_status; nothing is thrown across the ABI.
+ *   - Grid fields exchanged with the caller are DENSE float32 arrays of
+ *     nz*ny*nx values, index ((z*ny)+y)*nx+x, i.e. C order (z, y, x).
+ *     Pointers may be host or device memory (detected per call).
+ *   - Host arrays always belong to the caller.  Device state belongs to the
+ *     context unless the caller attached its own memory (RD_FLAG_NO_ALLOC +
+ *     rd_attach), in which case rd_destroy does not free it.
+ *   - Work is enqueued on the context's CUDA stream (its own non-blocking
+ *     stream unless rd_set_stream gave another).  rd_step is asynchronous;
+ *     rd_get_field, rd_mass and rd_sync synchronise that stream.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef RD_H
+#define RD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RD_MAX_SPECIES 4
+
+typedef enum rd_status {
+    RD_OK = 0,
+    RD_EINVAL = 1,        /* bad argument or configuration                  */
+    RD_ENOMEM = 2,        /* device or host allocation failed               */
+    RD_ECUDA = 3,         /* a CUDA call failed; see rd_last_error          */
+    RD_EUNSTABLE = 4,     /* dt violates the explicit stability bound       */
+    RD_ENONFINITE = 5,    /* a reduction found NaN/Inf in the state         */
+    RD_ETIMEOUT = 6,      /* rd_wait gave up before the stream finished     */
+    RD_EBUDGET = 7,       /* a batch or server memory budget was exceeded   */
+    RD_EUNSUPPORTED = 8   /* valid request this build does not implement    */
+} rd_status;
+
+/* Boundary rule of one face of one species (faces -x,+x,-y,+y,-z,+z). */
+typedef enum rd_bc_kind {
+    RD_BC_NEUMANN = 0,    /* zero flux: the ghost value equals the face cell */
+    RD_BC_PERIODIC = 1,   /* wrap-around; both faces of the axis, every
+                             species the same                                */
+    RD_BC_DIRICHLET = 2   /* the outermost cell layer on that face is held at
+                             bc_value and never updated (the paper keeps its
+                             boundary points in the outermost layer,
+                             Section 4.1)                                    */
+} rd_bc_kind;
+
+/* Model families (paper Table 1 rows, in the benchmark parameterisation). */
+typedef enum rd_model {
+    RD_MODEL_DIFFUSION = 0,   /* R = 0, any species count 1..4              */
+    RD_MODEL_BRUSSELATOR = 1, /* 2 species u, v:  R_u = a-(b+1)u+u^2 v,
+                                 R_v = b u - u^2 v;  params[0]=a, [1]=b      */
+    RD_MODEL_CH_FRONT = 2,    /* 3 species a, b, c: a+b->c at rate k a b;
+                                 c also moves by M Lap(f'(c) - kappa Lap c),
+                                 f'(c) = 2c(c-1)(2c-1) (Cahn-Hilliard, the
+                                 biharmonic as two chained Laplacians,
+                                 Section 4.1); params[0]=k, [1]=M, [2]=kappa;
+                                 species c has no Fickian term (D[2] = 0)    */
+    RD_MODEL_AIR = 3          /* 3 species NO, NO2, O3: NO2 -> NO + O3 at
+                                 j NO2, NO + O3 -> NO2 at k NO O3;
+                                 params[0]=j, [1]=k                          */
+} rd_model;
+
+typedef enum rd_storage {
+    RD_STORE_F32 = 0,     /* float32 state                                  */
+    RD_STORE_BF16 = 1     /* bfloat16 state, float32 arithmetic, each new
+                             value rounded to nearest-even when stored      */
+} rd_storage;
+
+/* Advection velocity along +x (first-order upwind, Section 4.1). */
+typedef enum rd_wind {
+    RD_WIND_NONE = 0,
+    RD_WIND_LOG = 1,      /* u_x(z) = wind_u0 * ln(1+z) / ln(1+nz), z the
+                             cell index 0..nz-1                              */
+    RD_WIND_CONST = 2     /* u_x = wind_u0 everywhere                       */
+} rd_wind;
+
+enum {
+    RD_FLAG_NO_ALLOC = 1, /* rd_create allocates no device memory; the
+                             caller must rd_attach state and scratch        */
+    RD_FLAG_FORCE = 2     /* skip the stability check                       */
+};
+
+/*
+ * Problem statement.  Units are the caller's; cells are cubes of edge h.
+ *   nx, ny, nz   cells per axis, each >= 2
+ *   nspecies     species count (fixed by the model except for diffusion)
+ *   h, dt        grid spacing and time step of eq. (5)
+ *   D[s][a]      diffusivity of species s along axis a (x, y, z): eq. (1)
+ *                with D diagonal, per axis where a problem needs it
+ *   bc, bc_value per species and face (-x,+x,-y,+y,-z,+z)
+ *   params       model constants (see rd_model)
+ *   wind_*       advection (see rd_wind); applies to every species
+ *   src_*        point emission: species src_species gains src_rate per
+ *                unit time at cell (src_x, src_y, src_z); src_species < 0
+ *                means none
+ */
+typedef struct rd_config {
+    int32_t nx, ny, nz, nspecies;
+    int32_t model, storage;
+    double h, dt;
+    double D[RD_MAX_SPECIES][3];
+    int32_t bc[RD_MAX_SPECIES][6];
+    double bc_value[RD_MAX_SPECIES][6];
+    double params[8];
+    int32_t wind_kind, reserved0;
+    double wind_u0;
+    int32_t src_x, src_y, src_z, src_species;
+    double src_rate;
+    int32_t flags, reserved1;
+} rd_config;
+
+typedef struct rd_ctx rd_ctx;
+
+/* Zero the config and set neutral defaults (h = 1, no source, no wind). */
+rd_status rd_config_init(rd_config* cfg);
+
+/* Bytes of device memory a context for ``cfg`` needs: the two time levels of
+ * all species (pitched rows) and the scratch area (staging for field I/O,
+ * reduction partials, instance descriptor, wind table).  Either output
+ * pointer may be NULL. */
+rd_status rd_query_sizes(const rd_config* cfg, size_t* state_bytes,
+                         size_t* scratch_bytes);
+
+/* Validate ``cfg`` and create a context on the current CUDA device.
+ * Checks: sizes >= 2, species count for the model, periodic faces paired
+ * and the same for every species, Dirichlet only on non-periodic faces and
+ * not on the Cahn-Hilliard species, and the explicit stability bound
+ *   dt * (sum_a 2 D[s][a] / h^2 + |u|max / h) <= 1 for every species
+ * (isotropic diffusion: dt <= h^2 / (6 D)), plus, for the Cahn-Hilliard
+ * species, dt * M * L (kappa L + 2) <= 2 with L = 12 / h^2 (the largest
+ * 7-point symbol); RD_EUNSTABLE otherwise unless RD_FLAG_FORCE.
+ * Allocates both levels and scratch unless RD_FLAG_NO_ALLOC.  The state is
+ * zero until rd_set_field.  *out receives the context. */
+rd_status rd_create(const rd_config* cfg, rd_ctx** out);
+
+/* Attach caller-owned device memory (RD_FLAG_NO_ALLOC contexts only):
+ * ``state`` of state_bytes and ``scratch`` of scratch_bytes as reported by
+ * rd_query_sizes, both 256-byte aligned.  The caller keeps ownership and
+ * must keep both alive until rd_destroy. */
+rd_status rd_attach(rd_ctx* ctx, void* state, void* scratch);
+
+/* Free what the context owns (device memory, stream, graphs). */
+rd_status rd_destroy(rd_ctx* ctx);
+
+/* Enqueue subsequent work on ``stream`` (a cudaStream_t; NULL = the legacy
+ * default stream).  The context does not take ownership. */
+rd_status rd_set_stream(rd_ctx* ctx, void* stream);
+
+/* Copy ``count`` = nx*ny*nz dense float32 values (host or device pointer)
+ * into species ``s`` of the current level, converting to the storage type.
+ * Cells of held (Dirichlet) layers are set to their bc_value.  Returns
+ * after the source buffer may be reused. */
+rd_status rd_set_field(rd_ctx* ctx, int s, const float* src, size_t count);
+
+/* Advance every species by ``nsteps`` forward-Euler steps (eq. (5)).
+ * Asynchronous: enqueued on the context's stream.  Internally the steps
+ * run as fused kernels advancing T steps per launch (temporal blocking),
+ * replayed from a captured CUDA graph when enabled. */
+rd_status rd_step(rd_ctx* ctx, int64_t nsteps);
+
+/* Copy species ``s`` of the current level out as ``count`` = nx*ny*nz dense
+ * float32 values (host or device pointer).  Synchronises the stream. */
+rd_status rd_get_field(rd_ctx* ctx, int s, float* dst, size_t count);
+
+/* FP64 reduction of species ``s`` of the current level: out[0] = sum,
+ * out[1] = sum of squares, out[2] = count of non-finite values.  The sums
+ * are accumulated in double precision in a fixed order, so repeated calls
+ * on the same state give bitwise identical results.  Synchronises the
+ * stream; returns RD_ENONFINITE (with out filled) if out[2] > 0. */
+rd_status rd_mass(rd_ctx* ctx, int s, double out[3]);
+
+/* Wait for all work enqueued on the context's stream. */
+rd_status rd_sync(rd_ctx* ctx);
+
+/* Like rd_sync, but give up after timeout_ms milliseconds of polling and
+ * return RD_ETIMEOUT (the work keeps running; the context stays usable). */
+rd_status rd_wait(rd_ctx* ctx, int64_t timeout_ms);
+
+/* Time steps taken since creation (or the last rd_set_step_count). */
+int64_t rd_step_count(const rd_ctx* ctx);
+rd_status rd_set_step_count(rd_ctx* ctx, int64_t n);
+
+/* Kernel tuning of a context.
+ *   tsteps  steps per launch (temporal blocking depth), 1..3 (1..2 for
+ *           the Cahn-Hilliard model)
+ *   tile_q  tile width in vectors of 16 bytes (x extent = tile_q * 4 float32
+ *           or tile_q * 8 bfloat16 cells), 8..32
+ *   tile_y  tile height in rows, 4..32
+ *   zchunk  z planes per work item, >= 1
+ *   graph   1: replay rd_step launches from a captured CUDA graph
+ * rd_set_tuning validates; RD_EINVAL if the shared-memory footprint does not
+ * fit one SM. */
+typedef struct rd_tuning {
+    int32_t tsteps, tile_q, tile_y, zchunk, graph, reserved;
+} rd_tuning;
+rd_status rd_get_tuning(const rd_ctx* ctx, rd_tuning* out);
+rd_status rd_set_tuning(rd_ctx* ctx, const rd_tuning* t);
+
+/* Time a built-in list of tunings on this context's problem (launches read
+ * the current level and write the spare level, so the state is unchanged)
+ * and keep the fastest.  Results are cached per (model, storage, grid, BC)
+ * in-process and, if the environment variable RD_AUTOTUNE_CACHE names a
+ * file, in that file (one JSON object per line).  *best may be NULL. */
+rd_status rd_autotune(rd_ctx* ctx, rd_tuning* best);
+
+/* Launch statistics: kernels this context enqueued since creation. */
+int64_t rd_launch_count(const rd_ctx* ctx);
+
+/* Text of a status code, and of the last error seen by a context. */
+const char* rd_status_str(rd_status st);
+const char* rd_last_error(const rd_ctx* ctx);
+
+/*
+ * Batches: many independent instances (contexts) of the same model and
+ * storage stepped together by one persistent kernel launch per T steps.
+ * The launch walks a work list of (instance, x-tile, y-tile, z-chunk) items
+ * across all members, so uneven grids share the GPU in one launch.  Members
+ * remain ordinary contexts: rd_get_field / rd_mass work on them between
+ * batch steps.
+ */
+typedef struct rd_batch rd_batch;
+
+/* Create an empty batch for one model and storage kind. */
+rd_status rd_batch_create(int32_t model, int32_t storage, rd_batch** out);
+/* Add ``ctx`` (same model and storage; at most one batch at a time). */
+rd_status rd_batch_add(rd_batch* b, rd_ctx* ctx);
+/* Remove ``ctx``; it becomes a standalone context again. */
+rd_status rd_batch_remove(rd_batch* b, rd_ctx* ctx);
+/* Number of members. */
+int32_t rd_batch_size(const rd_batch* b);
+/* Enqueue on ``stream`` (NULL = legacy default stream). */
+rd_status rd_batch_set_stream(rd_batch* b, void* stream);
+/* Tuning shared by all members (tile_q, tile_y, zchunk, tsteps, graph). */
+rd_status rd_batch_set_tuning(rd_batch* b, const rd_tuning* t);
+/* Advance every member by nsteps (asynchronous). */
+rd_status rd_batch_step(rd_batch* b, int64_t nsteps);
+/* Wait for the batch's stream. */
+rd_status rd_batch_sync(rd_batch* b);
+/* Destroy the batch (members are left intact and detached). */
+rd_status rd_batch_destroy(rd_batch* b);
+int64_t rd_batch_launch_count(const rd_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RD_H */

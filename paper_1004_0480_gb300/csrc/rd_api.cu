@@ -1,0 +1,1086 @@
+// rd_api.cu -- host runtime behind the C ABI declared in include/rd.h.
+//
+// Owns contexts (device state, scratch, stream, CUDA graphs), batches of
+// contexts, tuning and the autotuner.  All arithmetic of the step runs in the
+// kernels of rd_k_*.cu and rd_aux.cu; this file only validates, lays out
+// memory, builds instance descriptors and enqueues launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "rd.h"
+#include "rd_internal.h"
+
+using namespace rdk;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;        // kernel launches in the graph (even)
+    int tsteps = 0;
+    long long key = -1;      // tuning/membership signature it was built for
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        launches = 0;
+        key = -1;
+    }
+};
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+int max_smem_optin() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (n <= 0) n = 48 * 1024;
+    }
+    return n;
+}
+
+int vec_of(int storage) { return storage == RD_STORE_BF16 ? 8 : 4; }
+int elem_bytes(int storage) { return storage == RD_STORE_BF16 ? 2 : 4; }
+
+size_t smem_of(int model, int storage, int T, int tq, int ty) {
+    switch (model) {
+    case RD_MODEL_DIFFUSION: return smem_diffusion(storage, T, tq, ty);
+    case RD_MODEL_BRUSSELATOR: return smem_brusselator(storage, T, tq, ty);
+    case RD_MODEL_CH_FRONT: return smem_ch_front(storage, T, tq, ty);
+    case RD_MODEL_AIR: return smem_air(storage, T, tq, ty);
+    }
+    return 0;
+}
+
+cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int grid,
+                         size_t smem, cudaStream_t st, int* occ) {
+    switch (model) {
+    case RD_MODEL_DIFFUSION: return launch_diffusion(storage, T, a, grid, smem, st, occ);
+    case RD_MODEL_BRUSSELATOR: return launch_brusselator(storage, T, a, grid, smem, st, occ);
+    case RD_MODEL_CH_FRONT: return launch_ch_front(storage, T, a, grid, smem, st, occ);
+    case RD_MODEL_AIR: return launch_air(storage, T, a, grid, smem, st, occ);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int max_tsteps(int model) { return model == RD_MODEL_CH_FRONT ? 2 : 3; }
+
+// CTAs per SM for a variant (cached).
+int occupancy(int model, int storage, int T, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, size_t>, int> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_tuple(model, storage, T, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int occ = 0;
+    LaunchArgs dummy{};
+    if (launch_model(model, storage, T, dummy, 0, smem, nullptr, &occ) != cudaSuccess) occ = 0;
+    cudaGetLastError();
+    cache[key] = occ;
+    return occ;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- context
+struct rd_ctx {
+    rd_config cfg{};
+    int S = 0, vec = 4, ebytes = 4;
+    int pitch = 0;                 // elements per row
+    long long plane = 0;           // elements per plane
+    size_t field_bytes = 0;        // one species, one level (256-aligned)
+    size_t state_bytes = 0, scratch_bytes = 0;
+    char* state = nullptr;
+    char* scratch = nullptr;
+    bool own_mem = false;
+    // scratch carve-up
+    float* staging = nullptr;      // dense float field for I/O
+    double* partials = nullptr;    // reduction partials
+    double* result = nullptr;      // reduction result (3 doubles)
+    InstDesc* desc_dev = nullptr;  // this context's descriptor
+    float* courant = nullptr;      // u(z) dt / h per plane
+    int cur = 0;                   // current time level
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t capture_stream = nullptr;
+    rd_tuning tun{};
+    bool desc_dirty = true;
+    InstDesc desc{};
+    Graph graph;
+    int64_t steps = 0;
+    int64_t launches = 0;
+    rd_batch* batch = nullptr;
+    char err[512] = "";
+};
+
+struct rd_batch {
+    int model = 0, storage = 0;
+    std::vector<rd_ctx*> members;
+    InstDesc* desc_dev = nullptr;
+    size_t desc_cap = 0;
+    InstDesc* desc_host = nullptr;   // pinned
+    cudaEvent_t upload_done = nullptr;
+    cudaStream_t stream = nullptr;       // where work is enqueued
+    cudaStream_t own_stream = nullptr;   // created by the batch
+    cudaStream_t capture_stream = nullptr;
+    rd_tuning tun{};
+    bool tun_set = false;
+    Graph graph;
+    long long members_version = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+rd_status fail(rd_ctx* c, rd_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    std::snprintf(g_err, sizeof(g_err), "%s", buf);
+    if (c) std::snprintf(c->err, sizeof(c->err), "%s", buf);
+    return st;
+}
+
+rd_status cuda_fail(rd_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, RD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define RD_CUDA(c, call)                                   \
+    do {                                                   \
+        cudaError_t _e = (call);                           \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, #call); \
+    } while (0)
+
+int periodic_axis(const rd_config& c, int s, int a) {
+    return c.bc[s][2 * a] == RD_BC_PERIODIC;
+}
+
+rd_status validate(const rd_config* c) {
+    if (!c) return fail(nullptr, RD_EINVAL, "null config");
+    if (c->nx < 2 || c->ny < 2 || c->nz < 2)
+        return fail(nullptr, RD_EINVAL, "grid must be at least 2 cells per axis");
+    if ((long long)c->nx * c->ny * c->nz > (1LL << 34))
+        return fail(nullptr, RD_EINVAL, "grid too large");
+    if (!(c->h > 0) || !(c->dt > 0)) return fail(nullptr, RD_EINVAL, "h and dt must be > 0");
+    int want = -1;
+    switch (c->model) {
+    case RD_MODEL_DIFFUSION: want = 1; break;
+    case RD_MODEL_BRUSSELATOR: want = 2; break;
+    case RD_MODEL_CH_FRONT: want = 3; break;
+    case RD_MODEL_AIR: want = 3; break;
+    default: return fail(nullptr, RD_EINVAL, "unknown model %d", c->model);
+    }
+    if (c->nspecies != want) {
+        if (c->model == RD_MODEL_DIFFUSION && c->nspecies >= 1 && c->nspecies <= RD_MAX_SPECIES)
+            return fail(nullptr, RD_EUNSUPPORTED,
+                        "the diffusion kernels of this build step one species");
+        return fail(nullptr, RD_EINVAL, "model %d needs %d species", c->model, want);
+    }
+    if (c->storage != RD_STORE_F32 && c->storage != RD_STORE_BF16)
+        return fail(nullptr, RD_EINVAL, "unknown storage %d", c->storage);
+    for (int s = 0; s < c->nspecies; ++s) {
+        for (int f = 0; f < 6; ++f)
+            if (c->bc[s][f] < RD_BC_NEUMANN || c->bc[s][f] > RD_BC_DIRICHLET)
+                return fail(nullptr, RD_EINVAL, "bad boundary kind");
+        for (int a = 0; a < 3; ++a) {
+            const bool lo = c->bc[s][2 * a] == RD_BC_PERIODIC;
+            const bool hi = c->bc[s][2 * a + 1] == RD_BC_PERIODIC;
+            if (lo != hi) return fail(nullptr, RD_EINVAL, "periodic faces must come in pairs");
+            if (lo != (c->bc[0][2 * a] == RD_BC_PERIODIC))
+                return fail(nullptr, RD_EINVAL, "periodicity must be the same for all species");
+            for (int d = 0; d < 3; ++d)
+                if (!(c->D[s][d] >= 0) || !std::isfinite(c->D[s][d]))
+                    return fail(nullptr, RD_EINVAL, "diffusivities must be finite and >= 0");
+        }
+    }
+    if (c->model == RD_MODEL_CH_FRONT) {
+        for (int f = 0; f < 6; ++f)
+            if (c->bc[2][f] == RD_BC_DIRICHLET)
+                return fail(nullptr, RD_EUNSUPPORTED, "no held layer on the Cahn-Hilliard species");
+        if (c->D[2][0] != 0 || c->D[2][1] != 0 || c->D[2][2] != 0)
+            return fail(nullptr, RD_EUNSUPPORTED, "the Cahn-Hilliard species has no Fickian term");
+    }
+    if (c->wind_kind < RD_WIND_NONE || c->wind_kind > RD_WIND_CONST)
+        return fail(nullptr, RD_EINVAL, "unknown wind kind");
+    if (c->src_species >= 0) {
+        if (c->src_species >= c->nspecies || c->src_x < 0 || c->src_x >= c->nx || c->src_y < 0 ||
+            c->src_y >= c->ny || c->src_z < 0 || c->src_z >= c->nz)
+            return fail(nullptr, RD_EINVAL, "source outside the grid");
+    }
+    if (!(c->flags & RD_FLAG_FORCE)) {
+        double umax = 0.0;
+        if (c->wind_kind == RD_WIND_LOG) umax = std::fabs(c->wind_u0) * std::log1p((double)c->nz - 1) / std::log1p((double)c->nz);
+        if (c->wind_kind == RD_WIND_CONST) umax = std::fabs(c->wind_u0);
+        for (int s = 0; s < c->nspecies; ++s) {
+            const double g = c->dt * (2.0 * (c->D[s][0] + c->D[s][1] + c->D[s][2]) / (c->h * c->h) +
+                                      umax / c->h);
+            if (g > 1.0 + 1e-12)
+                return fail(nullptr, RD_EUNSTABLE,
+                            "dt too large for species %d: dt*(2*sum(D)/h^2+|u|/h) = %g > 1", s, g);
+        }
+        if (c->model == RD_MODEL_CH_FRONT) {
+            const double L = 12.0 / (c->h * c->h);
+            const double g = c->dt * c->params[1] * L * (c->params[2] * L + 2.0);
+            if (g > 2.0 + 1e-12)
+                return fail(nullptr, RD_EUNSTABLE, "dt too large for the Cahn-Hilliard term (%g > 2)", g);
+        }
+    }
+    return RD_OK;
+}
+
+void layout(rd_ctx* c) {
+    const rd_config& g = c->cfg;
+    c->S = g.nspecies;
+    c->vec = vec_of(g.storage);
+    c->ebytes = elem_bytes(g.storage);
+    // rows padded to 128 bytes so 16-byte vectors never cross a row end
+    const int row_align = 128 / c->ebytes;
+    c->pitch = (int)align_up((size_t)g.nx, (size_t)row_align);
+    c->plane = (long long)c->pitch * g.ny;
+    c->field_bytes = align_up((size_t)c->plane * g.nz * c->ebytes, 256);
+    c->state_bytes = c->field_bytes * 2 * c->S;
+    const size_t dense = align_up((size_t)g.nx * g.ny * g.nz * sizeof(float), 256);
+    const size_t part = align_up((size_t)reduce_blocks() * 3 * sizeof(double), 256);
+    const size_t res = 256;
+    const size_t desc = align_up(sizeof(InstDesc), 256);
+    const size_t cour = align_up((size_t)g.nz * sizeof(float), 256);
+    c->scratch_bytes = dense + part + res + desc + cour;
+}
+
+void carve(rd_ctx* c) {
+    const rd_config& g = c->cfg;
+    char* p = c->scratch;
+    c->staging = reinterpret_cast<float*>(p);
+    p += align_up((size_t)g.nx * g.ny * g.nz * sizeof(float), 256);
+    c->partials = reinterpret_cast<double*>(p);
+    p += align_up((size_t)reduce_blocks() * 3 * sizeof(double), 256);
+    c->result = reinterpret_cast<double*>(p);
+    p += 256;
+    c->desc_dev = reinterpret_cast<InstDesc*>(p);
+    p += align_up(sizeof(InstDesc), 256);
+    c->courant = reinterpret_cast<float*>(p);
+}
+
+char* field_ptr(rd_ctx* c, int level, int s) {
+    return c->state + ((size_t)level * c->S + s) * c->field_bytes;
+}
+
+// default tile width: as wide as a warp of 16-byte vectors, split evenly
+int default_tq(int nx, int vec) {
+    const int nxv = (nx + vec - 1) / vec;
+    const int ntx = (nxv + 31) / 32;
+    int tq = (nxv + ntx - 1) / ntx;
+    return std::max(2, std::min(32, tq));
+}
+
+int tiles(int n, int t) { return (n + t - 1) / t; }
+
+// z chunk so one launch has about ``waves`` work items per resident CTA
+int auto_zchunk(const rd_config& g, const rd_tuning& t, int occ, int waves) {
+    const int vec = vec_of(g.storage);
+    const long long cols = (long long)tiles(g.nx, t.tile_q * vec) * tiles(g.ny, t.tile_y);
+    const long long slots = (long long)std::max(occ, 1) * num_sms() * waves;
+    long long nzc = std::max<long long>(1, (slots + cols - 1) / cols);
+    int zc = (int)std::max<long long>(1, (g.nz + nzc - 1) / nzc);
+    const int L = (g.model == RD_MODEL_CH_FRONT ? 2 : 1) * t.tsteps;
+    zc = std::max(zc, std::min(g.nz, 4 * L));
+    return zc;
+}
+
+rd_status check_tuning(const rd_config& g, const rd_tuning& t) {
+    if (t.tsteps < 1 || t.tsteps > max_tsteps(g.model))
+        return fail(nullptr, RD_EINVAL, "tsteps out of range");
+    if (t.tile_q < 2 || t.tile_q > 64 || t.tile_y < 1 || t.tile_y > 64 || t.zchunk < 1)
+        return fail(nullptr, RD_EINVAL, "tile out of range");
+    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_q, t.tile_y);
+    if (sm + sizeof(InstDesc) + 64 > (size_t)max_smem_optin())
+        return fail(nullptr, RD_EINVAL, "tile needs %zu bytes of shared memory", sm);
+    return RD_OK;
+}
+
+rd_tuning default_tuning(const rd_config& g) {
+    rd_tuning t{};
+    t.tsteps = 1;
+    t.tile_q = default_tq(g.nx, vec_of(g.storage));
+    t.tile_y = 8;
+    t.graph = 1;
+    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_q, t.tile_y);
+    const int occ = occupancy(g.model, g.storage, t.tsteps, sm);
+    t.zchunk = auto_zchunk(g, t, occ, 1);
+    return t;
+}
+
+void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
+    const rd_config& g = c->cfg;
+    std::memset(&d, 0, sizeof(d));
+    for (int l = 0; l < 2; ++l)
+        for (int s = 0; s < c->S; ++s) d.base[l][s] = field_ptr(c, l, s);
+    d.nx = g.nx; d.ny = g.ny; d.nz = g.nz;
+    d.pitch = c->pitch;
+    d.plane = c->plane;
+    d.par = 0;
+    d.per_x = periodic_axis(g, 0, 0);
+    d.per_y = periodic_axis(g, 0, 1);
+    d.per_z = periodic_axis(g, 0, 2);
+    const double ih2 = 1.0 / (g.h * g.h);
+    for (int s = 0; s < c->S; ++s) {
+        unsigned m = 0;
+        for (int f = 0; f < 6; ++f) {
+            if (g.bc[s][f] == RD_BC_DIRICHLET) m |= 1u << f;
+            d.held_val[s][f] = (float)g.bc_value[s][f];
+        }
+        d.held_mask[s] = m;
+        d.kx[s] = (float)(g.D[s][0] * g.dt * ih2);
+        d.ky[s] = (float)(g.D[s][1] * g.dt * ih2);
+        d.kz[s] = (float)(g.D[s][2] * g.dt * ih2);
+    }
+    d.dt = (float)g.dt;
+    switch (g.model) {
+    case RD_MODEL_BRUSSELATOR:
+        d.p[0] = (float)g.params[0];
+        d.p[1] = (float)(g.params[1] + 1.0);
+        d.p[2] = (float)g.params[1];
+        break;
+    case RD_MODEL_CH_FRONT:
+        d.p[0] = (float)(g.dt * g.params[0]);
+        d.p[1] = (float)(g.dt * g.params[1] * ih2);
+        d.p[2] = (float)(g.params[2] * ih2);
+        break;
+    case RD_MODEL_AIR:
+        d.p[0] = (float)g.params[0];
+        d.p[1] = (float)g.params[1];
+        break;
+    default: break;
+    }
+    d.courant = g.wind_kind != RD_WIND_NONE ? c->courant : nullptr;
+    d.src_s = g.src_species >= 0 ? g.src_species : -1;
+    d.src_x = g.src_x; d.src_y = g.src_y; d.src_z = g.src_z;
+    d.src_amt = (float)(g.src_rate * g.dt);
+    const int vec = c->vec;
+    d.ntx = tiles(g.nx, t.tile_q * vec);
+    d.nty = tiles(g.ny, t.tile_y);
+    d.zchunk = std::max(1, std::min(t.zchunk, g.nz));
+    d.nzc = tiles(g.nz, d.zchunk);
+    d.item_begin = 0;
+}
+
+long long items_of(const InstDesc& d) { return (long long)d.ntx * d.nty * d.nzc; }
+
+rd_status upload_desc(rd_ctx* c) {
+    if (!c->desc_dirty) return RD_OK;
+    fill_desc(c, c->desc, c->tun);
+    RD_CUDA(c, cudaMemcpyAsync(c->desc_dev, &c->desc, sizeof(InstDesc), cudaMemcpyHostToDevice,
+                               c->stream));
+    RD_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->desc_dirty = false;
+    return RD_OK;
+}
+
+rd_status write_courant(rd_ctx* c) {
+    const rd_config& g = c->cfg;
+    if (g.wind_kind == RD_WIND_NONE) return RD_OK;
+    std::vector<float> cz(g.nz);
+    for (int z = 0; z < g.nz; ++z) {
+        double u = 0.0;
+        if (g.wind_kind == RD_WIND_LOG) u = g.wind_u0 * std::log1p((double)z) / std::log1p((double)g.nz);
+        else u = g.wind_u0;
+        cz[z] = (float)(u * g.dt / g.h);
+    }
+    RD_CUDA(c, cudaMemcpy(c->courant, cz.data(), sizeof(float) * g.nz, cudaMemcpyHostToDevice));
+    return RD_OK;
+}
+
+rd_status finish_setup(rd_ctx* c) {
+    carve(c);
+    RD_CUDA(c, cudaMemsetAsync(c->state, 0, c->state_bytes, c->stream));
+    RD_CUDA(c, cudaStreamSynchronize(c->stream));
+    rd_status st = write_courant(c);
+    if (st != RD_OK) return st;
+    c->desc_dirty = true;
+    return upload_desc(c);
+}
+
+// One fused launch advancing T steps, reading level ``c->cur``.
+rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
+    LaunchArgs a{};
+    a.desc = c->desc_dev;
+    a.ninst = 1;
+    a.parity = parity;
+    a.nitems = items_of(c->desc);
+    a.tq = c->tun.tile_q;
+    a.ty = c->tun.tile_y;
+    const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.tq, a.ty);
+    const int occ = std::max(1, occupancy(c->cfg.model, c->cfg.storage, T, sm));
+    const long long grid = std::min<long long>(a.nitems, (long long)occ * num_sms());
+    cudaError_t e = launch_model(c->cfg.model, c->cfg.storage, T, a, (int)grid, sm, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+    c->launches++;
+    return RD_OK;
+}
+
+long long ctx_graph_key(const rd_ctx* c) {
+    const rd_tuning& t = c->tun;
+    return ((((long long)t.tsteps * 64 + t.tile_q) * 64 + t.tile_y) * 100000 + t.zchunk);
+}
+
+constexpr int kGraphLaunches = 16;
+
+rd_status build_ctx_graph(rd_ctx* c) {
+    const long long key = ctx_graph_key(c);
+    if (c->graph.exec && c->graph.key == key) return RD_OK;
+    c->graph.reset();
+    if (!c->capture_stream)
+        RD_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    RD_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+    rd_status st = RD_OK;
+    for (int i = 0; i < kGraphLaunches && st == RD_OK; ++i)
+        st = launch_ctx(c, c->tun.tsteps, i & 1, c->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->capture_stream, &g);
+    if (st != RD_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+    e = cudaGraphInstantiate(&c->graph.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    c->launches -= kGraphLaunches;   // captured, not run
+    c->graph.launches = kGraphLaunches;
+    c->graph.tsteps = c->tun.tsteps;
+    c->graph.key = key;
+    return RD_OK;
+}
+
+rd_status step_ctx(rd_ctx* c, int64_t n) {
+    rd_status st = upload_desc(c);
+    if (st != RD_OK) return st;
+    const int T = c->tun.tsteps;
+    int64_t full = n / T;
+    const int rem = (int)(n % T);
+    if (c->tun.graph && full >= kGraphLaunches) {
+        st = build_ctx_graph(c);
+        if (st != RD_OK) return st;
+        if (c->cur == 1) {   // the graph starts from level 0
+            if ((st = launch_ctx(c, T, 1, c->stream)) != RD_OK) return st;
+            c->cur = 0;
+            --full;
+        }
+        while (full >= kGraphLaunches) {
+            cudaError_t e = cudaGraphLaunch(c->graph.exec, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+            c->launches += kGraphLaunches;
+            full -= kGraphLaunches;
+        }
+    }
+    for (int64_t i = 0; i < full; ++i) {
+        if ((st = launch_ctx(c, T, c->cur, c->stream)) != RD_OK) return st;
+        c->cur ^= 1;
+    }
+    if (rem) {
+        if ((st = launch_ctx(c, rem, c->cur, c->stream)) != RD_OK) return st;
+        c->cur ^= 1;
+    }
+    c->steps += n;
+    return RD_OK;
+}
+
+// Work of a batch member may still be queued on the batch's stream.
+void drain_batch(rd_ctx* c) {
+    if (c->batch) cudaStreamSynchronize(c->batch->stream);
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+std::mutex g_tune_mu;
+std::map<std::string, rd_tuning> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+std::string tune_key(const rd_config& g) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "m%d_s%d_%dx%dx%d_p%d%d%d_w%d_sm%d", g.model, g.storage, g.nx,
+                  g.ny, g.nz, periodic_axis(g, 0, 0), periodic_axis(g, 0, 1),
+                  periodic_axis(g, 0, 2), g.wind_kind != RD_WIND_NONE, num_sms());
+    return buf;
+}
+
+void load_tune_file() {
+    if (g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    const char* path = std::getenv("RD_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        char key[256];
+        rd_tuning t{};
+        if (std::sscanf(line,
+                        " {\"key\": \"%255[^\"]\", \"tsteps\": %d, \"tile_q\": %d, \"tile_y\": %d, "
+                        "\"zchunk\": %d, \"graph\": %d",
+                        key, &t.tsteps, &t.tile_q, &t.tile_y, &t.zchunk, &t.graph) == 6)
+            g_tune_cache[key] = t;
+    }
+    std::fclose(f);
+}
+
+void save_tune(const std::string& key, const rd_tuning& t, double gcups) {
+    const char* path = std::getenv("RD_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f,
+                 "{\"key\": \"%s\", \"tsteps\": %d, \"tile_q\": %d, \"tile_y\": %d, \"zchunk\": %d, "
+                 "\"graph\": %d, \"gcups\": %.3f}\n",
+                 key.c_str(), t.tsteps, t.tile_q, t.tile_y, t.zchunk, t.graph, gcups);
+    std::fclose(f);
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+rd_status rd_config_init(rd_config* cfg) {
+    if (!cfg) return RD_EINVAL;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->h = 1.0;
+    cfg->src_species = -1;
+    return RD_OK;
+}
+
+rd_status rd_query_sizes(const rd_config* cfg, size_t* state_bytes, size_t* scratch_bytes) {
+    rd_status st = validate(cfg);
+    if (st != RD_OK) return st;
+    rd_ctx tmp;
+    tmp.cfg = *cfg;
+    layout(&tmp);
+    if (state_bytes) *state_bytes = tmp.state_bytes;
+    if (scratch_bytes) *scratch_bytes = tmp.scratch_bytes;
+    return RD_OK;
+}
+
+rd_status rd_create(const rd_config* cfg, rd_ctx** out) {
+    if (!out) return fail(nullptr, RD_EINVAL, "null output pointer");
+    *out = nullptr;
+    rd_status st = validate(cfg);
+    if (st != RD_OK) return st;
+    rd_ctx* c = new (std::nothrow) rd_ctx();
+    if (!c) return fail(nullptr, RD_ENOMEM, "host allocation failed");
+    c->cfg = *cfg;
+    layout(c);
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete c; return cuda_fail(nullptr, e, "cudaStreamCreate"); }
+    c->own_stream = true;
+    c->tun = default_tuning(c->cfg);
+    if (!(cfg->flags & RD_FLAG_NO_ALLOC)) {
+        e = cudaMalloc(&c->state, c->state_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&c->scratch, c->scratch_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            const size_t sb = c->state_bytes, xb = c->scratch_bytes;
+            rd_destroy(c);
+            return fail(nullptr, RD_ENOMEM, "cudaMalloc of %zu + %zu bytes failed", sb, xb);
+        }
+        c->own_mem = true;
+        st = finish_setup(c);
+        if (st != RD_OK) { rd_destroy(c); return st; }
+    }
+    *out = c;
+    return RD_OK;
+}
+
+rd_status rd_attach(rd_ctx* c, void* state, void* scratch) {
+    if (!c || !state || !scratch) return fail(c, RD_EINVAL, "null argument");
+    if (!(c->cfg.flags & RD_FLAG_NO_ALLOC) || c->state)
+        return fail(c, RD_EINVAL, "context already has memory");
+    if ((reinterpret_cast<uintptr_t>(state) | reinterpret_cast<uintptr_t>(scratch)) & 255)
+        return fail(c, RD_EINVAL, "attached memory must be 256-byte aligned");
+    c->state = static_cast<char*>(state);
+    c->scratch = static_cast<char*>(scratch);
+    c->own_mem = false;
+    return finish_setup(c);
+}
+
+rd_status rd_destroy(rd_ctx* c) {
+    if (!c) return RD_EINVAL;
+    if (c->batch) rd_batch_remove(c->batch, c);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->graph.reset();
+    if (c->own_mem) {
+        cudaFree(c->state);
+        cudaFree(c->scratch);
+    }
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return RD_OK;
+}
+
+rd_status rd_set_stream(rd_ctx* c, void* stream) {
+    if (!c) return RD_EINVAL;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->own_stream = false;
+    return RD_OK;
+}
+
+rd_status rd_set_field(rd_ctx* c, int s, const float* src, size_t count) {
+    if (!c || !src) return fail(c, RD_EINVAL, "null argument");
+    if (!c->state) return fail(c, RD_EINVAL, "no memory attached");
+    if (s < 0 || s >= c->S) return fail(c, RD_EINVAL, "species %d out of range", s);
+    drain_batch(c);
+    const rd_config& g = c->cfg;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    if (count != n) return fail(c, RD_EINVAL, "count %zu != nx*ny*nz = %zu", count, n);
+    const bool dev = is_device_ptr(src);
+    RD_CUDA(c, cudaMemcpyAsync(c->staging, src, n * sizeof(float),
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    float hv[6];
+    unsigned m = 0;
+    for (int f = 0; f < 6; ++f) {
+        hv[f] = (float)g.bc_value[s][f];
+        if (g.bc[s][f] == RD_BC_DIRICHLET) m |= 1u << f;
+    }
+    cudaError_t e = launch_pack(c->staging, field_ptr(c, c->cur, s), g.storage, g.nx, g.ny, g.nz,
+                                c->pitch, m, hv, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
+    c->launches++;
+    RD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return RD_OK;
+}
+
+rd_status rd_get_field(rd_ctx* c, int s, float* dst, size_t count) {
+    if (!c || !dst) return fail(c, RD_EINVAL, "null argument");
+    if (!c->state) return fail(c, RD_EINVAL, "no memory attached");
+    if (s < 0 || s >= c->S) return fail(c, RD_EINVAL, "species %d out of range", s);
+    drain_batch(c);
+    const rd_config& g = c->cfg;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    if (count != n) return fail(c, RD_EINVAL, "count %zu != nx*ny*nz = %zu", count, n);
+    cudaError_t e = launch_unpack(field_ptr(c, c->cur, s), c->staging, g.storage, g.nx, g.ny,
+                                  g.nz, c->pitch, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "unpack kernel");
+    c->launches++;
+    const bool dev = is_device_ptr(dst);
+    RD_CUDA(c, cudaMemcpyAsync(dst, c->staging, n * sizeof(float),
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    RD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return RD_OK;
+}
+
+rd_status rd_step(rd_ctx* c, int64_t nsteps) {
+    if (!c || nsteps < 0) return fail(c, RD_EINVAL, "bad argument");
+    if (!c->state) return fail(c, RD_EINVAL, "no memory attached");
+    if (c->batch) return fail(c, RD_EINVAL, "context is in a batch; step the batch");
+    if (nsteps == 0) return RD_OK;
+    return step_ctx(c, nsteps);
+}
+
+rd_status rd_mass(rd_ctx* c, int s, double out[3]) {
+    if (!c || !out) return fail(c, RD_EINVAL, "null argument");
+    if (!c->state) return fail(c, RD_EINVAL, "no memory attached");
+    if (s < 0 || s >= c->S) return fail(c, RD_EINVAL, "species %d out of range", s);
+    drain_batch(c);
+    const rd_config& g = c->cfg;
+    cudaError_t e = launch_reduce(field_ptr(c, c->cur, s), g.storage, g.nx, g.ny, g.nz, c->pitch,
+                                  c->partials, c->result, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reduce kernel");
+    c->launches += 2;
+    RD_CUDA(c, cudaMemcpyAsync(out, c->result, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+    RD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return out[2] > 0 ? RD_ENONFINITE : RD_OK;
+}
+
+rd_status rd_sync(rd_ctx* c) {
+    if (!c) return RD_EINVAL;
+    RD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return RD_OK;
+}
+
+rd_status rd_wait(rd_ctx* c, int64_t timeout_ms) {
+    if (!c) return RD_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaSuccess) return RD_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(c, e, "cudaStreamQuery");
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                            std::chrono::steady_clock::now() - t0).count();
+        if (ms >= timeout_ms) return fail(c, RD_ETIMEOUT, "stream still busy after %lld ms", (long long)ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+int64_t rd_step_count(const rd_ctx* c) { return c ? c->steps : -1; }
+
+rd_status rd_set_step_count(rd_ctx* c, int64_t n) {
+    if (!c) return RD_EINVAL;
+    c->steps = n;
+    return RD_OK;
+}
+
+int64_t rd_launch_count(const rd_ctx* c) { return c ? c->launches : -1; }
+
+rd_status rd_get_tuning(const rd_ctx* c, rd_tuning* out) {
+    if (!c || !out) return RD_EINVAL;
+    *out = c->tun;
+    return RD_OK;
+}
+
+rd_status rd_set_tuning(rd_ctx* c, const rd_tuning* t) {
+    if (!c || !t) return fail(c, RD_EINVAL, "null argument");
+    rd_status st = check_tuning(c->cfg, *t);
+    if (st != RD_OK) return fail(c, st, "%s", g_err);
+    c->tun = *t;
+    c->tun.zchunk = std::min(c->tun.zchunk, c->cfg.nz);
+    c->desc_dirty = true;
+    return RD_OK;
+}
+
+rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
+    if (!c) return RD_EINVAL;
+    if (!c->state) return fail(c, RD_EINVAL, "no memory attached");
+    const rd_config& g = c->cfg;
+    const std::string key = tune_key(g);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        load_tune_file();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && check_tuning(g, it->second) == RD_OK) {
+            c->tun = it->second;
+            c->desc_dirty = true;
+            if (best_out) *best_out = c->tun;
+            return RD_OK;
+        }
+    }
+    const rd_tuning saved = c->tun;
+    const int vec = c->vec;
+    const int tq0 = default_tq(g.nx, vec);
+    std::vector<int> tqs = {tq0};
+    if (tq0 > 16) tqs.push_back((tq0 + 1) / 2);
+    std::vector<rd_tuning> cands;
+    for (int T = 1; T <= max_tsteps(g.model); ++T)
+        for (int tq : tqs)
+            for (int ty : {4, 8, 16, 32}) {
+                rd_tuning t{};
+                t.tsteps = T; t.tile_q = tq; t.tile_y = ty; t.graph = 1;
+                const size_t sm = smem_of(g.model, g.storage, T, tq, ty);
+                if (check_tuning(g, (t.zchunk = 1, t)) != RD_OK) continue;
+                const int occ = occupancy(g.model, g.storage, T, sm);
+                if (occ < 1) continue;
+                for (int waves : {1, 2, 4}) {
+                    t.zchunk = auto_zchunk(g, t, occ, waves);
+                    bool dup = false;
+                    for (auto& o : cands)
+                        dup |= (o.tsteps == t.tsteps && o.tile_q == t.tile_q &&
+                                o.tile_y == t.tile_y && o.zchunk == t.zchunk);
+                    if (!dup) cands.push_back(t);
+                }
+            }
+    cudaEvent_t e0, e1;
+    RD_CUDA(c, cudaEventCreate(&e0));
+    RD_CUDA(c, cudaEventCreate(&e1));
+    double best = -1.0;
+    rd_tuning bt = saved;
+    const double cells = (double)g.nx * g.ny * g.nz;
+    for (const rd_tuning& t : cands) {
+        c->tun = t;
+        c->desc_dirty = true;
+        rd_status st = upload_desc(c);
+        if (st != RD_OK) break;
+        // warm-up, then time launches that all read the current level
+        st = launch_ctx(c, t.tsteps, c->cur, c->stream);
+        if (st != RD_OK) { cudaGetLastError(); continue; }
+        const int reps = 4;
+        cudaEventRecord(e0, c->stream);
+        for (int i = 0; i < reps && st == RD_OK; ++i) st = launch_ctx(c, t.tsteps, c->cur, c->stream);
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess || st != RD_OK) { cudaGetLastError(); continue; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double rate = cells * t.tsteps * reps / (ms * 1e-3) / 1e9;
+        if (rate > best) { best = rate; bt = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tun = best > 0 ? bt : saved;
+    c->desc_dirty = true;
+    if (best > 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = c->tun;
+        save_tune(key, c->tun, best);
+    }
+    if (best_out) *best_out = c->tun;
+    return upload_desc(c);
+}
+
+const char* rd_status_str(rd_status st) {
+    switch (st) {
+    case RD_OK: return "ok";
+    case RD_EINVAL: return "invalid argument";
+    case RD_ENOMEM: return "out of memory";
+    case RD_ECUDA: return "CUDA error";
+    case RD_EUNSTABLE: return "time step above the stability bound";
+    case RD_ENONFINITE: return "non-finite values in the state";
+    case RD_ETIMEOUT: return "timed out";
+    case RD_EBUDGET: return "memory budget exceeded";
+    case RD_EUNSUPPORTED: return "not supported by this build";
+    }
+    return "unknown status";
+}
+
+const char* rd_last_error(const rd_ctx* c) { return c ? c->err : g_err; }
+
+// ================================================================ batches
+rd_status rd_batch_create(int32_t model, int32_t storage, rd_batch** out) {
+    if (!out) return RD_EINVAL;
+    *out = nullptr;
+    if (model < RD_MODEL_DIFFUSION || model > RD_MODEL_AIR) return fail(nullptr, RD_EINVAL, "bad model");
+    if (storage != RD_STORE_F32 && storage != RD_STORE_BF16) return fail(nullptr, RD_EINVAL, "bad storage");
+    rd_batch* b = new (std::nothrow) rd_batch();
+    if (!b) return RD_ENOMEM;
+    b->model = model;
+    b->storage = storage;
+    if (cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->upload_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(nullptr, RD_ECUDA, "batch stream/event creation failed");
+    }
+    b->stream = b->own_stream;
+    *out = b;
+    return RD_OK;
+}
+
+rd_status rd_batch_add(rd_batch* b, rd_ctx* c) {
+    if (!b || !c) return RD_EINVAL;
+    if (c->batch) return fail(c, RD_EINVAL, "context already in a batch");
+    if (c->cfg.model != b->model || c->cfg.storage != b->storage)
+        return fail(c, RD_EINVAL, "model/storage differ from the batch");
+    if (!c->state) return fail(c, RD_EINVAL, "no memory attached");
+    cudaStreamSynchronize(c->stream);
+    b->members.push_back(c);
+    c->batch = b;
+    b->members_version++;
+    return RD_OK;
+}
+
+rd_status rd_batch_remove(rd_batch* b, rd_ctx* c) {
+    if (!b || !c) return RD_EINVAL;
+    auto it = std::find(b->members.begin(), b->members.end(), c);
+    if (it == b->members.end()) return fail(c, RD_EINVAL, "not a member");
+    cudaStreamSynchronize(b->stream);
+    b->members.erase(it);
+    c->batch = nullptr;
+    c->desc_dirty = true;
+    b->members_version++;
+    return RD_OK;
+}
+
+int32_t rd_batch_size(const rd_batch* b) { return b ? (int32_t)b->members.size() : -1; }
+
+rd_status rd_batch_set_stream(rd_batch* b, void* stream) {
+    if (!b) return RD_EINVAL;
+    cudaStreamSynchronize(b->stream);
+    b->stream = static_cast<cudaStream_t>(stream);
+    return RD_OK;
+}
+
+rd_status rd_batch_set_tuning(rd_batch* b, const rd_tuning* t) {
+    if (!b || !t) return RD_EINVAL;
+    b->tun = *t;
+    b->tun_set = true;
+    b->graph.reset();
+    return RD_OK;
+}
+
+namespace {
+
+rd_tuning batch_tuning(rd_batch* b) {
+    if (b->tun_set) return b->tun;
+    rd_tuning t{};
+    t.tsteps = 1;
+    t.tile_q = 16;
+    t.tile_y = 8;
+    t.graph = 1;
+    t.zchunk = 32;
+    return t;
+}
+
+// Rebuild and upload the descriptor array: member i reads level cur_i at
+// parity 0.
+rd_status batch_upload(rd_batch* b, const rd_tuning& t, long long* nitems) {
+    const size_t n = b->members.size();
+    if (n > b->desc_cap) {
+        if (b->desc_dev) cudaFree(b->desc_dev);
+        if (b->desc_host) cudaFreeHost(b->desc_host);
+        b->desc_dev = nullptr;
+        b->desc_host = nullptr;
+        size_t cap = std::max<size_t>(16, n * 2);
+        if (cudaMalloc(&b->desc_dev, cap * sizeof(InstDesc)) != cudaSuccess ||
+            cudaMallocHost(&b->desc_host, cap * sizeof(InstDesc)) != cudaSuccess) {
+            cudaGetLastError();
+            b->desc_cap = 0;
+            return fail(nullptr, RD_ENOMEM, "batch descriptor allocation failed");
+        }
+        b->desc_cap = cap;
+        b->graph.reset();
+    }
+    // the previous upload must have left the pinned buffer
+    cudaEventSynchronize(b->upload_done);
+    long long begin = 0;
+    for (size_t i = 0; i < n; ++i) {
+        rd_ctx* c = b->members[i];
+        rd_tuning ti = t;
+        ti.zchunk = std::min(t.zchunk, c->cfg.nz);
+        fill_desc(c, b->desc_host[i], ti);
+        b->desc_host[i].par = c->cur;
+        b->desc_host[i].item_begin = begin;
+        begin += items_of(b->desc_host[i]);
+    }
+    *nitems = begin;
+    if (n) {
+        cudaError_t e = cudaMemcpyAsync(b->desc_dev, b->desc_host, n * sizeof(InstDesc),
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch descriptor upload");
+        cudaEventRecord(b->upload_done, b->stream);
+    }
+    return RD_OK;
+}
+
+rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long long nitems,
+                       cudaStream_t st) {
+    LaunchArgs a{};
+    a.desc = b->desc_dev;
+    a.ninst = (int)b->members.size();
+    a.parity = parity;
+    a.nitems = nitems;
+    a.tq = t.tile_q;
+    a.ty = t.tile_y;
+    const size_t sm = smem_of(b->model, b->storage, T, a.tq, a.ty);
+    const int occ = std::max(1, occupancy(b->model, b->storage, T, sm));
+    const long long grid = std::min<long long>(nitems, (long long)occ * num_sms());
+    cudaError_t e = launch_model(b->model, b->storage, T, a, (int)grid, sm, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch step launch");
+    b->launches++;
+    return RD_OK;
+}
+
+}  // namespace
+
+rd_status rd_batch_step(rd_batch* b, int64_t nsteps) {
+    if (!b || nsteps < 0) return RD_EINVAL;
+    if (b->members.empty() || nsteps == 0) return RD_OK;
+    const rd_tuning t = batch_tuning(b);
+    rd_status st = check_tuning(b->members[0]->cfg, t);
+    if (st != RD_OK) return st;
+    long long nitems = 0;
+    if ((st = batch_upload(b, t, &nitems)) != RD_OK) return st;
+    const int T = t.tsteps;
+    int64_t full = nsteps / T;
+    const int rem = (int)(nsteps % T);
+    int parity = 0;
+    const long long key = b->members_version * 1000003LL + nitems;
+    if (t.graph && full >= 2) {
+        if (!b->graph.exec || b->graph.key != key) {
+            b->graph.reset();
+            if (!b->capture_stream &&
+                cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+                return fail(nullptr, RD_ECUDA, "capture stream");
+            cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(nullptr, e, "begin capture");
+            st = batch_launch(b, t, T, 0, nitems, b->capture_stream);
+            if (st == RD_OK) st = batch_launch(b, t, T, 1, nitems, b->capture_stream);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(b->capture_stream, &g);
+            if (st != RD_OK) { if (g) cudaGraphDestroy(g); return st; }
+            if (e != cudaSuccess) return cuda_fail(nullptr, e, "end capture");
+            e = cudaGraphInstantiate(&b->graph.exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(nullptr, e, "instantiate");
+            b->launches -= 2;
+            b->graph.key = key;
+        }
+        while (full >= 2) {
+            cudaError_t e = cudaGraphLaunch(b->graph.exec, b->stream);
+            if (e != cudaSuccess) return cuda_fail(nullptr, e, "graph launch");
+            b->launches += 2;
+            full -= 2;
+        }
+    }
+    for (int64_t i = 0; i < full; ++i) {
+        if ((st = batch_launch(b, t, T, parity, nitems, b->stream)) != RD_OK) return st;
+        parity ^= 1;
+    }
+    if (rem) {
+        if ((st = batch_launch(b, t, rem, parity, nitems, b->stream)) != RD_OK) return st;
+        parity ^= 1;
+    }
+    const int64_t launches = nsteps / T + (rem ? 1 : 0);
+    for (rd_ctx* c : b->members) {
+        c->cur ^= (int)(launches & 1);
+        c->steps += nsteps;
+    }
+    return RD_OK;
+}
+
+rd_status rd_batch_sync(rd_batch* b) {
+    if (!b) return RD_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch sync");
+    return RD_OK;
+}
+
+rd_status rd_batch_destroy(rd_batch* b) {
+    if (!b) return RD_EINVAL;
+    cudaStreamSynchronize(b->stream);
+    for (rd_ctx* c : b->members) { c->batch = nullptr; c->desc_dirty = true; }
+    b->graph.reset();
+    if (b->desc_dev) cudaFree(b->desc_dev);
+    if (b->desc_host) cudaFreeHost(b->desc_host);
+    if (b->upload_done) cudaEventDestroy(b->upload_done);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->own_stream) cudaStreamDestroy(b->own_stream);
+    delete b;
+    return RD_OK;
+}
+
+int64_t rd_batch_launch_count(const rd_batch* b) { return b ? b->launches : -1; }
+
+}  // extern "C"

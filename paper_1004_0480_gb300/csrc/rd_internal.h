@@ -1,0 +1,74 @@
+// rd_internal.h -- device-side descriptors shared by the step kernels and
+// the host runtime of the GB300 reaction-diffusion library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rd.h"
+
+namespace rdk {
+
+constexpr int kThreads = 256;        // threads per CTA of every step kernel
+constexpr int kMaxS = RD_MAX_SPECIES;
+constexpr int kPrefetch = 2;         // level-0 planes in flight per CTA
+
+// One instance (context) as the step kernels see it.  Written by the host,
+// read by every CTA that works on the instance.
+struct InstDesc {
+    char* base[2][kMaxS];      // field of species s at time level l
+    int nx, ny, nz;
+    int pitch;                 // elements per row (multiple of 16 bytes)
+    long long plane;           // elements per plane (pitch * ny)
+    int par;                   // level read when the launch parity is 0
+    int per_x, per_y, per_z;   // periodic axes
+    unsigned held_mask[kMaxS]; // bit f: face f of species s is a held layer
+    float held_val[kMaxS][6];
+    float kx[kMaxS], ky[kMaxS], kz[kMaxS];   // D[s][axis] * dt / h^2
+    float dt;
+    float p[8];                // model constants, see the model structs
+    const float* courant;      // u_x(z) * dt / h per plane, or nullptr
+    int src_x, src_y, src_z, src_s;          // src_s < 0: no source
+    float src_amt;             // emission per step: rate * dt
+    int ntx, nty, nzc, zchunk; // work items: ntx * nty * nzc
+    long long item_begin;      // first global item index of this instance
+};
+
+struct LaunchArgs {
+    const InstDesc* desc;      // device array of ninst descriptors
+    int ninst;
+    int parity;                // launch parity (0/1): level read = par ^ parity
+    long long nitems;          // total work items over all instances
+    int tq;                    // tile width in 16-byte vectors
+    int ty;                    // tile height in rows
+};
+
+// Per-model launchers (one translation unit each).  With occ != nullptr
+// they only report the CTAs per SM for that shared-memory size.
+cudaError_t launch_diffusion(int storage, int tsteps, const LaunchArgs& a, int grid,
+                             size_t smem, cudaStream_t st, int* occ);
+cudaError_t launch_brusselator(int storage, int tsteps, const LaunchArgs& a, int grid,
+                               size_t smem, cudaStream_t st, int* occ);
+cudaError_t launch_ch_front(int storage, int tsteps, const LaunchArgs& a, int grid,
+                            size_t smem, cudaStream_t st, int* occ);
+cudaError_t launch_air(int storage, int tsteps, const LaunchArgs& a, int grid,
+                       size_t smem, cudaStream_t st, int* occ);
+// Dynamic shared memory of one step kernel variant, in bytes.
+size_t smem_diffusion(int storage, int tsteps, int tq, int ty);
+size_t smem_brusselator(int storage, int tsteps, int tq, int ty);
+size_t smem_ch_front(int storage, int tsteps, int tq, int ty);
+size_t smem_air(int storage, int tsteps, int tq, int ty);
+
+// Auxiliary kernels (rd_aux.cu).
+cudaError_t launch_pack(const float* dense, char* field, int storage, int nx, int ny,
+                        int nz, int pitch, unsigned held_mask, const float* held_val,
+                        cudaStream_t st);
+cudaError_t launch_unpack(const char* field, float* dense, int storage, int nx, int ny,
+                          int nz, int pitch, cudaStream_t st);
+// Deterministic two-pass FP64 reduction: out[0]=sum, out[1]=sum of squares,
+// out[2]=non-finite count.  partials holds reduce_blocks() * 3 doubles.
+int reduce_blocks();
+cudaError_t launch_reduce(const char* field, int storage, int nx, int ny, int nz,
+                          int pitch, double* partials, double* out, cudaStream_t st);
+
+}  // namespace rdk

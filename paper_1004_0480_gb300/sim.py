@@ -1,0 +1,270 @@
+"""Python binding over the C ABI: ``Sim`` (one problem) and ``Batch``.
+
+Argument marshalling only: every step, conversion and reduction runs in the
+CUDA library.  PyTorch is used, when available, for device memory (contexts
+created with ``torch_memory=True`` live in torch-allocated buffers attached
+through ``rd_attach``) and for streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+_PARAM_ORDER = {
+    "diffusion": (),
+    "brusselator": ("a", "b"),
+    "ch_front": ("k", "M", "kappa"),
+    "air": ("j", "k"),
+}
+
+
+def make_config(cfg, storage="f32", force=False, no_alloc=False) -> L.RdConfig:
+    """rd_config for a problem dictionary (``workloads`` format)."""
+    lib = L.load()
+    c = L.RdConfig()
+    lib.rd_config_init(ctypes.byref(c))
+    c.nx, c.ny, c.nz = cfg["shape"]
+    c.nspecies = cfg["nspecies"]
+    c.model = L.MODEL[cfg["model"]]
+    c.storage = L.STORAGE[storage]
+    c.h = cfg["h"]
+    c.dt = cfg["dt"]
+    for s in range(c.nspecies):
+        for a in range(3):
+            c.D[s][a] = cfg["D"][s][a]
+        for f in range(6):
+            c.bc[s][f] = L.BC[cfg["bc"][s][f]]
+            c.bc_value[s][f] = cfg["bc_value"][s][f]
+    for i, name in enumerate(_PARAM_ORDER[cfg["model"]]):
+        c.params[i] = cfg["params"][name]
+    w = cfg.get("wind")
+    c.wind_kind = L.WIND[w["kind"] if w else None]
+    c.wind_u0 = w["u0"] if w else 0.0
+    src = cfg.get("source")
+    if src:
+        c.src_x, c.src_y, c.src_z = src["x"], src["y"], src["z"]
+        c.src_species = src["species"]
+        c.src_rate = src["rate"]
+    else:
+        c.src_species = -1
+    c.flags = (L.FLAG_FORCE if force else 0) | (L.FLAG_NO_ALLOC if no_alloc else 0)
+    return c
+
+
+def query_sizes(cfg, storage="f32"):
+    lib = L.load()
+    c = make_config(cfg, storage)
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    L.check(lib.rd_query_sizes(ctypes.byref(c), ctypes.byref(a), ctypes.byref(b)),
+            None, "rd_query_sizes")
+    return a.value, b.value
+
+
+def _ptr(buf):
+    """(address, keep-alive) of a float32 buffer: numpy array or torch tensor."""
+    if isinstance(buf, np.ndarray):
+        arr = np.ascontiguousarray(buf, dtype=np.float32)
+        return arr.ctypes.data, arr
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(buf, torch.Tensor):
+        if buf.dtype != torch.float32 or not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous float32")
+        return buf.data_ptr(), buf
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+class Sim:
+    """One reaction-diffusion problem on the GPU.
+
+    ``cfg``     problem dictionary (see ``workloads``)
+    ``storage`` "f32" or "bf16"
+    ``stream``  a torch.cuda.Stream, a raw cudaStream_t int, or None (the
+                context's own stream)
+    ``torch_memory``  allocate state and scratch with torch and attach them
+    """
+
+    def __init__(self, cfg, storage="f32", stream=None, torch_memory=False, force=False,
+                 tuning=None):
+        self.lib = L.load()
+        self.cfg = cfg
+        self.storage = storage
+        self.shape = tuple(cfg["shape"])
+        self.nspecies = cfg["nspecies"]
+        self._keep = []
+        conf = make_config(cfg, storage, force=force, no_alloc=torch_memory)
+        ctx = ctypes.c_void_p()
+        L.check(self.lib.rd_create(ctypes.byref(conf), ctypes.byref(ctx)), None, "rd_create")
+        self.ctx = ctx
+        if stream is not None:
+            self.set_stream(stream)
+        if torch_memory:
+            import torch
+            sb, xb = query_sizes(cfg, storage)
+            st = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
+            sc = torch.empty(xb + 256, dtype=torch.uint8, device="cuda")
+            self._keep += [st, sc]
+            a0 = (st.data_ptr() + 255) // 256 * 256
+            a1 = (sc.data_ptr() + 255) // 256 * 256
+            self._check(self.lib.rd_attach(self.ctx, ctypes.c_void_p(a0), ctypes.c_void_p(a1)),
+                        "rd_attach")
+        if tuning is not None:
+            self.set_tuning(**tuning)
+
+    # -- helpers
+    def _check(self, st, what):
+        L.check(st, self.ctx, what)
+
+    @property
+    def ncell(self):
+        nx, ny, nz = self.shape
+        return nx * ny * nz
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.rd_set_stream(self.ctx, ctypes.c_void_p(handle)), "rd_set_stream")
+
+    # -- fields
+    def set_field(self, s, values):
+        addr, keep = _ptr(values)
+        n = self.ncell
+        if getattr(keep, "size", None) is not None and keep.size != n:
+            raise ValueError("wrong field size")
+        self._check(self.lib.rd_set_field(self.ctx, s, ctypes.c_void_p(addr), n), "rd_set_field")
+
+    def set_fields(self, fields):
+        for s in range(self.nspecies):
+            self.set_field(s, fields[s])
+
+    def get_field(self, s, out=None):
+        nx, ny, nz = self.shape
+        if out is None:
+            out = np.empty((nz, ny, nx), dtype=np.float32)
+        addr, keep = _ptr(out)
+        self._check(self.lib.rd_get_field(self.ctx, s, ctypes.c_void_p(addr), self.ncell),
+                    "rd_get_field")
+        return out
+
+    def get_fields(self):
+        return np.stack([self.get_field(s) for s in range(self.nspecies)])
+
+    # -- stepping
+    def step(self, n):
+        self._check(self.lib.rd_step(self.ctx, int(n)), "rd_step")
+
+    def sync(self):
+        self._check(self.lib.rd_sync(self.ctx), "rd_sync")
+
+    def wait(self, timeout_ms):
+        return self.lib.rd_wait(self.ctx, int(timeout_ms))
+
+    def mass(self, s):
+        out = (ctypes.c_double * 3)()
+        st = self.lib.rd_mass(self.ctx, s, out)
+        if st not in (L.RD_OK, L.RD_ENONFINITE):
+            self._check(st, "rd_mass")
+        return out[0], out[1], int(out[2])
+
+    @property
+    def steps_done(self):
+        return self.lib.rd_step_count(self.ctx)
+
+    @property
+    def launches(self):
+        return self.lib.rd_launch_count(self.ctx)
+
+    # -- tuning
+    def tuning(self):
+        t = L.RdTuning()
+        self._check(self.lib.rd_get_tuning(self.ctx, ctypes.byref(t)), "rd_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        cur = self.tuning()
+        cur.update(kw)
+        t = L.RdTuning(cur["tsteps"], cur["tile_q"], cur["tile_y"], cur["zchunk"],
+                       cur["graph"], 0)
+        self._check(self.lib.rd_set_tuning(self.ctx, ctypes.byref(t)), "rd_set_tuning")
+
+    def autotune(self):
+        t = L.RdTuning()
+        self._check(self.lib.rd_autotune(self.ctx, ctypes.byref(t)), "rd_autotune")
+        return t.as_dict()
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.rd_destroy(self.ctx)
+            self.ctx = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Contexts of one model and storage stepped by shared persistent launches."""
+
+    def __init__(self, model, storage="f32", stream=None):
+        self.lib = L.load()
+        b = ctypes.c_void_p()
+        L.check(self.lib.rd_batch_create(L.MODEL[model], L.STORAGE[storage], ctypes.byref(b)),
+                None, "rd_batch_create")
+        self.b = b
+        self.members = []
+        if stream is not None:
+            handle = getattr(stream, "cuda_stream", stream)
+            L.check(self.lib.rd_batch_set_stream(self.b, ctypes.c_void_p(handle)), None,
+                    "rd_batch_set_stream")
+
+    def add(self, sim: Sim):
+        L.check(self.lib.rd_batch_add(self.b, sim.ctx), sim.ctx, "rd_batch_add")
+        self.members.append(sim)
+
+    def remove(self, sim: Sim):
+        L.check(self.lib.rd_batch_remove(self.b, sim.ctx), sim.ctx, "rd_batch_remove")
+        self.members.remove(sim)
+
+    def set_tuning(self, tsteps=1, tile_q=16, tile_y=8, zchunk=32, graph=1):
+        t = L.RdTuning(tsteps, tile_q, tile_y, zchunk, graph, 0)
+        L.check(self.lib.rd_batch_set_tuning(self.b, ctypes.byref(t)), None,
+                "rd_batch_set_tuning")
+
+    def step(self, n):
+        L.check(self.lib.rd_batch_step(self.b, int(n)), None, "rd_batch_step")
+
+    def sync(self):
+        L.check(self.lib.rd_batch_sync(self.b), None, "rd_batch_sync")
+
+    @property
+    def launches(self):
+        return self.lib.rd_batch_launch_count(self.b)
+
+    def __len__(self):
+        return self.lib.rd_batch_size(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.rd_batch_destroy(self.b)
+            self.b = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

@@ -1,0 +1,116 @@
+"""The C ABI library loads on a machine without a GPU, exports every function
+``include/rd.h`` declares, and the ctypes binding agrees with the C layout.
+Only host-side validation is called here (no device work)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1004_0480_gb300 import _lib as L
+from paper_1004_0480_gb300 import build as B
+from paper_1004_0480_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rd.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rd_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in rd.h but not exported"
+    assert set(names) == set(L.SIGNATURES), "ctypes table out of sync with rd.h"
+
+
+def test_struct_layout_matches_c(tmp_path):
+    probe = tmp_path / "probe.c"
+    probe.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "rd.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rd_config), offsetof(rd_config, D),
+         offsetof(rd_config, bc), offsetof(rd_config, bc_value), offsetof(rd_config, params),
+         offsetof(rd_config, wind_u0), offsetof(rd_config, src_rate), sizeof(rd_tuning));
+  return 0;
+}''')
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", f"-I{os.path.join(ROOT, 'include')}", str(probe), "-o", str(exe)],
+                   check=True)
+    vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                        check=True).stdout.split()))
+    C = L.RdConfig
+    assert vals == [ctypes.sizeof(C), C.D.offset, C.bc.offset, C.bc_value.offset,
+                    C.params.offset, C.wind_u0.offset, C.src_rate.offset,
+                    ctypes.sizeof(L.RdTuning)]
+
+
+def test_status_strings(lib):
+    for st in range(9):
+        assert lib.rd_status_str(st)
+    assert lib.rd_status_str(99) == b"unknown status"
+
+
+def _cfg(cfg, **kw):
+    from paper_1004_0480_gb300.sim import make_config
+    c = make_config(cfg)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def test_validation_host_only(lib):
+    sz = ctypes.c_size_t()
+    sc = ctypes.c_size_t()
+    q = lambda c: lib.rd_query_sizes(ctypes.byref(c), ctypes.byref(sz), ctypes.byref(sc))
+    assert q(_cfg(W.cfg_brusselator_256())) == L.RD_OK
+    # two levels of two species, rows padded to 128 bytes
+    assert sz.value == 2 * 2 * 256 * 256 * 256 * 4
+    # stability: dt <= h^2 / (6 D) for isotropic diffusion
+    ok = W.diffusion_blob(8, dt=1.0 / 6.0)
+    bad = W.diffusion_blob(8, dt=1.0 / 6.0 * 1.001)
+    assert q(_cfg(ok)) == L.RD_OK
+    assert q(_cfg(bad)) == L.RD_EUNSTABLE
+    c = _cfg(bad)
+    c.flags = L.FLAG_FORCE
+    assert q(c) == L.RD_OK
+    # the air problem's Courant number enters the bound
+    air = W.air((16, 16, 8), src=(1, 1, 1), dt=0.2)
+    assert q(_cfg(air)) == L.RD_OK
+    assert q(_cfg(W.with_(air, dt=0.8))) == L.RD_EUNSTABLE
+    # grid and species checks
+    assert q(_cfg(W.diffusion_blob(8), nx=1)) == L.RD_EINVAL
+    assert q(_cfg(W.brusselator(8), nspecies=3)) == L.RD_EINVAL
+    c = _cfg(W.brusselator(8))
+    c.bc[0][0] = L.BC["neumann"]          # unpaired periodic face
+    assert q(c) == L.RD_EINVAL
+    c = _cfg(W.ch_front(8))
+    c.bc[2][4] = L.BC["dirichlet"]        # no held layer on the CH species
+    assert q(c) == L.RD_EUNSUPPORTED
+    c = _cfg(W.air((8, 8, 8), src=(1, 1, 1)))
+    c.src_x = 8                           # source outside the grid
+    assert q(c) == L.RD_EINVAL
+    assert b"source" in lib.rd_last_error(None)
+
+
+def test_bf16_rows_are_128_bytes(lib):
+    from paper_1004_0480_gb300.sim import make_config
+    c = make_config(W.diffusion_blob(shape=(70, 3, 2)), storage="bf16")
+    sz = ctypes.c_size_t()
+    assert lib.rd_query_sizes(ctypes.byref(c), ctypes.byref(sz), None) == L.RD_OK
+    # 70 cells pad to 128 bf16 per row: 2 levels * 1 species * 128*3*2 * 2 bytes
+    assert sz.value == 2 * ((128 * 3 * 2 * 2 + 255) // 256 * 256)
