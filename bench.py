@@ -1,0 +1,455 @@
+#!/usr/bin/env python3
+"""Benchmark of the reaction-diffusion stepper on GB300.
+
+One bench step = one complete job of the 256^3 periodic Brusselator
+(2 species, FP32 state, a=3, b=9, Du=2, Dv=16, dt=0.005): load the seeded
+initial fields, then 10 000 forward-Euler steps through the fused kernel
+(7-point Laplacian + reaction + Euler update, temporal blocking, CUDA-graph
+replay).  Metric: GLUPS = cells x time steps / s / 1e9 (the paper's
+Mpoints/s, scaled), aggregated over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--no-extras] [--serve]
+
+Under torchrun each rank runs its own replica of the job (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1004_0480_gb300 import workloads as W  # noqa: E402
+
+METRIC = "GLUPS (cell updates per second / 1e9), brusselator 256^3 FP32"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_FILE = os.path.join(ROOT, "profiles", "rd_step_brusselator_256.md")
+KERNEL_SOURCES = ["paper_1004_0480_gb300/csrc/rd_step_kernel.cuh",
+                  "paper_1004_0480_gb300/csrc/rd_k_brusselator.cu",
+                  "paper_1004_0480_gb300/csrc/rd_internal.h"]
+
+
+# ------------------------------------------------------------------ helpers
+def dist_setup(n_gpus):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(tsteps, tile_q, tile_y):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source and the same tuning; else None."""
+    try:
+        text = open(PROFILE_FILE).read()
+    except OSError:
+        return None
+    fields = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    try:
+        if fields.get("kernel_sha") != kernel_sha():
+            return None
+        if (int(fields["tsteps"]), int(fields["tile_q"]), int(fields["tile_y"])) != \
+                (tsteps, tile_q, tile_y):
+            return None
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                     hw=parts[5], hwt=parts[6], swt=parts[7], cap=parts[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        smax = max(r["smax"] for r in rows)
+        loaded = [r for r in rows if r["sm"] > 0.5 * smax] or rows
+        reasons = set()
+        for r in rows:
+            if r["hw"].lower().startswith("active"):
+                reasons.add("hw_slowdown")
+            if r["hwt"].lower().startswith("active"):
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"].lower().startswith("active"):
+                reasons.add("sw_thermal_slowdown")
+            if r["cap"].lower().startswith("active"):
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": statistics.median(r["sm"] for r in loaded), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_sample(cfg, nsteps, fields=None):
+    """Time the FP64 oracle (single thread) on ``nsteps`` steps of ``cfg``."""
+    import oracle
+    oracle.build()
+    f = W.initial_fields(cfg) if fields is None else fields
+    t0 = time.perf_counter()
+    oracle.run(cfg, f, nsteps)
+    dt = time.perf_counter() - t0
+    return W.cell_count(cfg) * nsteps / dt / 1e9, dt
+
+
+def reference_arm(args, ws, rank):
+    """Reference arm: the FP64 oracle on the host cores, bounded samples."""
+    if rank != 0:
+        return 0
+    cfg = W.cfg_brusselator_256()
+    f = W.initial_fields(cfg)
+    sample_steps = 1
+    for _ in range(args.warmup):
+        oracle_sample(cfg, sample_steps, f)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sample(cfg, sample_steps, f)
+        times.append(dt)
+    tot = sum(times)
+    glups = W.cell_count(cfg) * sample_steps * args.steps / tot / 1e9
+    sample = (f"{sample_steps} forward-Euler step of the 256^3 Brusselator per bench step "
+              f"(FP64 C oracle, single thread)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "brusselator_256^3_periodic", "cells": W.cell_count(cfg),
+                   "species": 2, "sample": sample},
+        "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_1004_0480_gb300 import build as B
+    B.build()
+    from paper_1004_0480_gb300.sim import Batch, Sim
+
+    torch.cuda.set_device(local)
+    cfg = W.cfg_brusselator_256()
+    steps_per_job = args.job_steps or cfg["steps"]
+    cells = W.cell_count(cfg)
+    f = W.initial_fields(cfg)
+    stream = torch.cuda.Stream()
+    sim = Sim(cfg, stream=stream)
+    sim.set_fields(f)
+    if args.tuning:
+        T_, ty_, zc_ = (int(x) for x in args.tuning.split(","))
+        sim.set_tuning(tsteps=T_, tile_y=ty_, zchunk=zc_)
+        tun = sim.tuning()
+    else:
+        tun = sim.autotune()
+    if args.profile:
+        # a few single launches of the step kernel for an ncu capture
+        for _ in range(args.profile):
+            sim.step(tun["tsteps"])
+        sim.sync()
+        sim.close()
+        return 0
+    dev_ic = torch.from_numpy(f).cuda()
+    host_ic = torch.from_numpy(f).pin_memory()
+    host_out = torch.empty_like(host_ic).pin_memory()
+
+    def job_device():
+        for s in range(2):
+            sim.set_field(s, dev_ic[s])
+        sim.step(steps_per_job)
+
+    for _ in range(args.warmup):
+        job_device()
+    sim.sync()
+
+    # ---------------- timed region: device-resident inputs
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    step_kernel_ms = 0.0
+    step_kernel_launches = 0
+    with ClockSampler(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        launches0 = sim.launches
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for i in range(args.steps):
+            for s in range(2):
+                sim.set_field(s, dev_ic[s])
+            l0 = sim.launches
+            ev[i][0].record(stream)
+            sim.step(steps_per_job)
+            ev[i][1].record(stream)
+            step_kernel_launches += sim.launches - l0
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        launches = sim.launches - launches0
+    elapsed_ms = start.elapsed_time(end)
+    step_kernel_ms = sum(a.elapsed_time(b) for a, b in ev)
+    elapsed_ms = max_over_ranks(elapsed_ms, ws)
+    clocks = clk.summary()
+    total_cell_steps = cells * steps_per_job * args.steps * ws
+    value = total_cell_steps / (elapsed_ms * 1e-3) / 1e9
+
+    # roofline of the step kernel: 2 species x (read + write) x 4 B per cell-step
+    T = tun["tsteps"]
+    per_launch_ms = step_kernel_ms / step_kernel_launches
+    bytes_per_launch = 16.0 * cells * T
+    achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": profiled_traffic(T, tun["tile_q"], tun["tile_y"]),
+                "peak_source": peak_src,
+                "kernel": f"rd_step_kernel<MBrusselator,float,{T}>",
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "launch_ms": per_launch_ms,
+                "compulsory_frac": (16.0 * cells) / (per_launch_ms * 1e-3) / 1e9 / peak}
+
+    # ---------------- end to end through the C ABI with host buffers
+    def job_host():
+        for s in range(2):
+            sim.set_field(s, host_ic[s])
+        sim.step(steps_per_job)
+        for s in range(2):
+            sim.get_field(s, host_out[s])
+
+    job_host()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        job_host()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    barrier(ws)
+    e2e = {"value": total_cell_steps / e2e_s / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": int(host_ic.numel() * 4),
+           "d2h_bytes_per_step": int(host_out.numel() * 4)}
+    assert np.isfinite(host_out.numpy()).all()
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = run_extras(args, Sim, Batch, torch)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        glups_cpu, dt = oracle_sample(cfg, args.cpu_steps, f)
+        cpu = {"value": glups_cpu, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_steps} steps of the 256^3 Brusselator, FP64 C oracle, "
+                         f"single thread ({dt:.1f} s)"}
+
+    sim.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"brusselator_256^3_periodic_{steps_per_job}_steps", "cells": cells,
+                   "species": 2, "steps_per_job": steps_per_job,
+                   "l2": "state 2 x 128 MiB per level > 129 MB L2 (no flush needed)",
+                   "tuning": tun, "parallelism": f"replicas x{ws}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    if extras:
+        line["extras"] = extras
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_extras(args, Sim, Batch, torch):
+    """BF16-storage variant, and the batched front workload vs the plain
+    one-launch-per-instance stepper."""
+    out = {}
+    # BF16 storage, same job
+    cfg = W.cfg_brusselator_256()
+    cells = W.cell_count(cfg)
+    f = W.initial_fields(cfg)
+    with Sim(cfg, storage="bf16") as sim:
+        sim.set_fields(f)
+        tun = sim.autotune()
+        sim.step(200)
+        sim.sync()
+        t0 = time.perf_counter()
+        sim.step(cfg["steps"])
+        sim.sync()
+        ms = (time.perf_counter() - t0) * 1e3
+        out["bf16_storage"] = {"glups": cells * cfg["steps"] / (ms * 1e-3) / 1e9,
+                               "tuning": tun}
+    # batched front instances vs plain per-instance stepping
+    cfgs = W.cfg_ch_front_batch(steps=args.batch_steps)
+    cells_b = sum(W.cell_count(c) for c in cfgs)
+    sims = [Sim(c) for c in cfgs]
+    for c, s in zip(cfgs, sims):
+        s.set_fields(W.initial_fields(c))
+    b = Batch("ch_front")
+    b.set_tuning(tsteps=1, tile_q=16, tile_y=8, zchunk=32, graph=1)
+    for s in sims:
+        b.add(s)
+    b.step(20)
+    b.sync()
+    t0 = time.perf_counter()
+    b.step(args.batch_steps)
+    b.sync()
+    bt = time.perf_counter() - t0
+    for s in sims:
+        b.remove(s)
+    b.close()
+    # plain stepper: the fused kernel at T=1, one launch per instance and
+    # step, no graph, instances serialised in arrival order on one stream
+    common = torch.cuda.Stream()
+    for s in sims:
+        s.set_tuning(tsteps=1, graph=0)
+        s.set_stream(common)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in sims:
+        s.step(args.batch_steps)
+    common.synchronize()
+    pt = time.perf_counter() - t0
+    for s in sims:
+        s.close()
+    out["ch_front_batch_32"] = {
+        "instances": len(cfgs), "cells": cells_b, "steps": args.batch_steps,
+        "batched_glups": cells_b * args.batch_steps / bt / 1e9,
+        "plain_glups": cells_b * args.batch_steps / pt / 1e9,
+        "speedup": pt / bt}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--job-steps", type=int, default=0,
+                    help="time steps per job (default: the workload's 10 000)")
+    ap.add_argument("--tuning", default="",
+                    help="fixed tuning 'tsteps,tile_y,zchunk' instead of the autotuner")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="only run this many single step-kernel launches (for ncu)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        rc = reference_arm(args, ws, rank)
+    else:
+        rc = run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -197,13 +197,15 @@ rd_status rd_set_step_count(rd_ctx* ctx, int64_t n);
 /* Kernel tuning of a context.
  *   tsteps  steps per launch (temporal blocking depth), 1..3 (1..2 for
  *           the Cahn-Hilliard model)
- *   tile_q  tile width in vectors of 16 bytes (x extent = tile_q * 4 float32
- *           or tile_q * 8 bfloat16 cells), 8..32
- *   tile_y  tile height in rows, 4..32
+ *   tile_q  tile width in 4-cell vectors; this build fixes it at 16 (a tile
+ *           is 64 cells wide)
+ *   tile_y  tile height in rows, >= 1; the CTA has (tile_q + 2) x
+ *           (tile_y + 2 L) threads (L = tsteps, 2 tsteps for Cahn-Hilliard),
+ *           at most 512
  *   zchunk  z planes per work item, >= 1
  *   graph   1: replay rd_step launches from a captured CUDA graph
- * rd_set_tuning validates; RD_EINVAL if the shared-memory footprint does not
- * fit one SM. */
+ * rd_set_tuning validates; RD_EINVAL if the CTA or its shared memory does
+ * not fit one SM. */
 typedef struct rd_tuning {
     int32_t tsteps, tile_q, tile_y, zchunk, graph, reserved;
 } rd_tuning;

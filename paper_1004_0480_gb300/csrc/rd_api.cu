@@ -65,17 +65,25 @@ int max_smem_optin() {
     return n;
 }
 
-int vec_of(int storage) { return storage == RD_STORE_BF16 ? 8 : 4; }
+int vec_of(int) { return 4; }
 int elem_bytes(int storage) { return storage == RD_STORE_BF16 ? 2 : 4; }
 
-size_t smem_of(int model, int storage, int T, int tq, int ty) {
+size_t smem_of(int model, int storage, int T, int ty) {
     switch (model) {
-    case RD_MODEL_DIFFUSION: return smem_diffusion(storage, T, tq, ty);
-    case RD_MODEL_BRUSSELATOR: return smem_brusselator(storage, T, tq, ty);
-    case RD_MODEL_CH_FRONT: return smem_ch_front(storage, T, tq, ty);
-    case RD_MODEL_AIR: return smem_air(storage, T, tq, ty);
+    case RD_MODEL_DIFFUSION: return smem_diffusion(storage, T, ty);
+    case RD_MODEL_BRUSSELATOR: return smem_brusselator(storage, T, ty);
+    case RD_MODEL_CH_FRONT: return smem_ch_front(storage, T, ty);
+    case RD_MODEL_AIR: return smem_air(storage, T, ty);
     }
     return 0;
+}
+
+// CTA size of a step kernel: the one-step kernel has a thread per tile
+// vector; the multi-level kernel (tile vectors + 2 halo) x (rows + 2 L)
+int threads_of(int model, int T, int ty) {
+    if (T == 1 && model != RD_MODEL_CH_FRONT) return kTileQ * ty;
+    const int L = (model == RD_MODEL_CH_FRONT ? 2 : 1) * T;
+    return (kTileQ + 2) * (ty + 2 * L);
 }
 
 cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int grid,
@@ -92,15 +100,18 @@ cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int
 int max_tsteps(int model) { return model == RD_MODEL_CH_FRONT ? 2 : 3; }
 
 // CTAs per SM for a variant (cached).
-int occupancy(int model, int storage, int T, size_t smem) {
+int occupancy(int model, int storage, int T, size_t smem, int threads) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, size_t>, int> cache;
+    static std::map<std::tuple<int, int, int, size_t, int>, int> cache;
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_tuple(model, storage, T, smem);
+    auto key = std::make_tuple(model, storage, T, smem, threads);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int occ = 0;
     LaunchArgs dummy{};
+    dummy.ty = (T == 1 && model != RD_MODEL_CH_FRONT)
+                   ? threads / kTileQ
+                   : threads / (kTileQ + 2) - 2 * (model == RD_MODEL_CH_FRONT ? 2 : 1) * T;
     if (launch_model(model, storage, T, dummy, 0, smem, nullptr, &occ) != cudaSuccess) occ = 0;
     cudaGetLastError();
     cache[key] = occ;
@@ -294,13 +305,6 @@ char* field_ptr(rd_ctx* c, int level, int s) {
     return c->state + ((size_t)level * c->S + s) * c->field_bytes;
 }
 
-// default tile width: as wide as a warp of 16-byte vectors, split evenly
-int default_tq(int nx, int vec) {
-    const int nxv = (nx + vec - 1) / vec;
-    const int ntx = (nxv + 31) / 32;
-    int tq = (nxv + ntx - 1) / ntx;
-    return std::max(2, std::min(32, tq));
-}
 
 int tiles(int n, int t) { return (n + t - 1) / t; }
 
@@ -319,9 +323,13 @@ int auto_zchunk(const rd_config& g, const rd_tuning& t, int occ, int waves) {
 rd_status check_tuning(const rd_config& g, const rd_tuning& t) {
     if (t.tsteps < 1 || t.tsteps > max_tsteps(g.model))
         return fail(nullptr, RD_EINVAL, "tsteps out of range");
-    if (t.tile_q < 2 || t.tile_q > 64 || t.tile_y < 1 || t.tile_y > 64 || t.zchunk < 1)
-        return fail(nullptr, RD_EINVAL, "tile out of range");
-    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_q, t.tile_y);
+    if (t.tile_q != kTileQ)
+        return fail(nullptr, RD_EINVAL, "tile_q must be %d in this build", kTileQ);
+    if (t.tile_y < 1 || t.zchunk < 1) return fail(nullptr, RD_EINVAL, "tile out of range");
+    if (threads_of(g.model, t.tsteps, t.tile_y) > kMaxThreads)
+        return fail(nullptr, RD_EINVAL, "tile_y %d too tall for %d steps per launch", t.tile_y,
+                    t.tsteps);
+    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_y);
     if (sm + sizeof(InstDesc) + 64 > (size_t)max_smem_optin())
         return fail(nullptr, RD_EINVAL, "tile needs %zu bytes of shared memory", sm);
     return RD_OK;
@@ -330,11 +338,11 @@ rd_status check_tuning(const rd_config& g, const rd_tuning& t) {
 rd_tuning default_tuning(const rd_config& g) {
     rd_tuning t{};
     t.tsteps = 1;
-    t.tile_q = default_tq(g.nx, vec_of(g.storage));
-    t.tile_y = 8;
+    t.tile_q = kTileQ;
+    t.tile_y = 16;
     t.graph = 1;
-    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_q, t.tile_y);
-    const int occ = occupancy(g.model, g.storage, t.tsteps, sm);
+    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_y);
+    const int occ = occupancy(g.model, g.storage, t.tsteps, sm, threads_of(g.model, t.tsteps, t.tile_y));
     t.zchunk = auto_zchunk(g, t, occ, 1);
     return t;
 }
@@ -436,10 +444,9 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     a.ninst = 1;
     a.parity = parity;
     a.nitems = items_of(c->desc);
-    a.tq = c->tun.tile_q;
     a.ty = c->tun.tile_y;
-    const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.tq, a.ty);
-    const int occ = std::max(1, occupancy(c->cfg.model, c->cfg.storage, T, sm));
+    const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty);
+    const int occ = std::max(1, occupancy(c->cfg.model, c->cfg.storage, T, sm, threads_of(c->cfg.model, T, a.ty)));
     const long long grid = std::min<long long>(a.nitems, (long long)occ * num_sms());
     cudaError_t e = launch_model(c->cfg.model, c->cfg.storage, T, a, (int)grid, sm, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
@@ -790,29 +797,23 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
         }
     }
     const rd_tuning saved = c->tun;
-    const int vec = c->vec;
-    const int tq0 = default_tq(g.nx, vec);
-    std::vector<int> tqs = {tq0};
-    if (tq0 > 16) tqs.push_back((tq0 + 1) / 2);
     std::vector<rd_tuning> cands;
     for (int T = 1; T <= max_tsteps(g.model); ++T)
-        for (int tq : tqs)
-            for (int ty : {4, 8, 16, 32}) {
-                rd_tuning t{};
-                t.tsteps = T; t.tile_q = tq; t.tile_y = ty; t.graph = 1;
-                const size_t sm = smem_of(g.model, g.storage, T, tq, ty);
-                if (check_tuning(g, (t.zchunk = 1, t)) != RD_OK) continue;
-                const int occ = occupancy(g.model, g.storage, T, sm);
-                if (occ < 1) continue;
-                for (int waves : {1, 2, 4}) {
-                    t.zchunk = auto_zchunk(g, t, occ, waves);
-                    bool dup = false;
-                    for (auto& o : cands)
-                        dup |= (o.tsteps == t.tsteps && o.tile_q == t.tile_q &&
-                                o.tile_y == t.tile_y && o.zchunk == t.zchunk);
-                    if (!dup) cands.push_back(t);
-                }
+        for (int ty : {4, 8, 12, 16, 20, 24, 32}) {
+            rd_tuning t{};
+            t.tsteps = T; t.tile_q = kTileQ; t.tile_y = ty; t.graph = 1; t.zchunk = 1;
+            if (check_tuning(g, t) != RD_OK) continue;
+            const size_t sm = smem_of(g.model, g.storage, T, ty);
+            const int occ = occupancy(g.model, g.storage, T, sm, threads_of(g.model, T, ty));
+            if (occ < 1) continue;
+            for (int waves : {1, 2, 4, 8}) {
+                t.zchunk = auto_zchunk(g, t, occ, waves);
+                bool dup = false;
+                for (auto& o : cands)
+                    dup |= (o.tsteps == t.tsteps && o.tile_y == t.tile_y && o.zchunk == t.zchunk);
+                if (!dup) cands.push_back(t);
             }
+        }
     cudaEvent_t e0, e1;
     RD_CUDA(c, cudaEventCreate(&e0));
     RD_CUDA(c, cudaEventCreate(&e1));
@@ -835,6 +836,9 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
         const double rate = cells * t.tsteps * reps / (ms * 1e-3) / 1e9;
+        if (std::getenv("RD_AUTOTUNE_VERBOSE"))
+            std::fprintf(stderr, "rd_autotune %s T=%d tile_y=%d zchunk=%d: %.2f GLUPS (%.4f ms/launch)\n",
+                         key.c_str(), t.tsteps, t.tile_y, t.zchunk, rate, ms / reps);
         if (rate > best) { best = rate; bt = t; }
     }
     cudaEventDestroy(e0);
@@ -936,7 +940,7 @@ rd_tuning batch_tuning(rd_batch* b) {
     if (b->tun_set) return b->tun;
     rd_tuning t{};
     t.tsteps = 1;
-    t.tile_q = 16;
+    t.tile_q = kTileQ;
     t.tile_y = 8;
     t.graph = 1;
     t.zchunk = 32;
@@ -991,10 +995,9 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
     a.ninst = (int)b->members.size();
     a.parity = parity;
     a.nitems = nitems;
-    a.tq = t.tile_q;
     a.ty = t.tile_y;
-    const size_t sm = smem_of(b->model, b->storage, T, a.tq, a.ty);
-    const int occ = std::max(1, occupancy(b->model, b->storage, T, sm));
+    const size_t sm = smem_of(b->model, b->storage, T, a.ty);
+    const int occ = std::max(1, occupancy(b->model, b->storage, T, sm, threads_of(b->model, T, a.ty)));
     const long long grid = std::min<long long>(nitems, (long long)occ * num_sms());
     cudaError_t e = launch_model(b->model, b->storage, T, a, (int)grid, sm, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch step launch");

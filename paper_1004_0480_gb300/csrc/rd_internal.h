@@ -9,9 +9,9 @@
 
 namespace rdk {
 
-constexpr int kThreads = 256;        // threads per CTA of every step kernel
+constexpr int kMaxThreads = 512;     // upper bound of step-kernel CTA size
+constexpr int kTileQ = 16;           // tile width in 4-cell vectors (64 cells)
 constexpr int kMaxS = RD_MAX_SPECIES;
-constexpr int kPrefetch = 2;         // level-0 planes in flight per CTA
 
 // One instance (context) as the step kernels see it.  Written by the host,
 // read by every CTA that works on the instance.
@@ -39,8 +39,7 @@ struct LaunchArgs {
     int ninst;
     int parity;                // launch parity (0/1): level read = par ^ parity
     long long nitems;          // total work items over all instances
-    int tq;                    // tile width in 16-byte vectors
-    int ty;                    // tile height in rows
+    int ty;                    // tile height in rows (width is kTileQ vectors)
 };
 
 // Per-model launchers (one translation unit each).  With occ != nullptr
@@ -53,11 +52,12 @@ cudaError_t launch_ch_front(int storage, int tsteps, const LaunchArgs& a, int gr
                             size_t smem, cudaStream_t st, int* occ);
 cudaError_t launch_air(int storage, int tsteps, const LaunchArgs& a, int grid,
                        size_t smem, cudaStream_t st, int* occ);
-// Dynamic shared memory of one step kernel variant, in bytes.
-size_t smem_diffusion(int storage, int tsteps, int tq, int ty);
-size_t smem_brusselator(int storage, int tsteps, int tq, int ty);
-size_t smem_ch_front(int storage, int tsteps, int tq, int ty);
-size_t smem_air(int storage, int tsteps, int tq, int ty);
+// Dynamic shared memory (bytes) and CTA size of one step kernel variant.
+size_t smem_diffusion(int storage, int tsteps, int ty);
+size_t smem_brusselator(int storage, int tsteps, int ty);
+size_t smem_ch_front(int storage, int tsteps, int ty);
+size_t smem_air(int storage, int tsteps, int ty);
+int step_threads(int model, int tsteps, int ty);
 
 // Auxiliary kernels (rd_aux.cu).
 cudaError_t launch_pack(const float* dense, char* field, int storage, int nx, int ny,

@@ -10,8 +10,8 @@ cudaError_t launch_diffusion(int storage, int tsteps, const LaunchArgs& a, int g
     return launch_model<MDiffusion>(storage, tsteps, a, grid, smem, st, occ);
 }
 
-size_t smem_diffusion(int storage, int tsteps, int tq, int ty) {
-    return smem_for<MDiffusion>(storage, tsteps, tq, ty);
+size_t smem_diffusion(int storage, int tsteps, int ty) {
+    return smem_for<MDiffusion>(storage, tsteps, ty);
 }
 
 }  // namespace rdk

@@ -1,162 +1,95 @@
 // rd_step_kernel.cuh -- the fused forward-Euler step kernel (sm_103a).
 //
-// One kernel advances T steps of eq. (5) for every species of a work item.
-// A work item is an x-y tile of TX x TY cells and a chunk of z planes of one
-// instance.  The CTA marches up the chunk (the z-march of the paper's
-// Shared method, Section 4.1 / Table 4, restated for this hardware):
+// One launch advances T steps of eq. (5) for every species of every work
+// item.  A work item is an x-y tile of 64 x TY cells and a chunk of z planes
+// of one instance.  The CTA marches up the chunk, as the paper's Shared
+// method does (Section 4.1, Table 4), restated for this hardware:
 //
-//   level 0   planes of the current state arrive in a shared-memory ring by
-//             16-byte cp.async copies, kPrefetch planes ahead, with the tile
-//             widened by a halo of L cells in y and one 16-byte vector in x;
-//   level l   1 <= l <= L: each new plane of level l is computed from three
-//             planes (q-1, q, q+1) of level l-1 as soon as they exist;
-//             level L is written to global memory with 16-byte stores.
+//  * thread layout: one thread per 4-cell vector position of the tile
+//    widened by a halo (one vector each side in x, L rows each side in y),
+//    i.e. (16 + 2) x (TY + 2L) threads.  As in the paper's overlapped
+//    blocks, halo threads load (and at inner levels compute) but never
+//    store.  A thread keeps its position for the whole march, so all index
+//    and boundary arithmetic is done once per work item.
+//  * level 0: planes of the current state arrive in a shared-memory ring by
+//    per-thread cp.async copies, several planes ahead.
+//  * level l = 1..L: as soon as level l-1 has planes q-1, q, q+1, plane q of
+//    level l is computed from them; every level keeps a few planes in shared
+//    memory.  Level L goes to global memory.  All levels advance once per
+//    plane, with a single barrier per plane.
+//  * Without Cahn-Hilliard L = T and level l is the state after l steps.
+//    With it L = 2T: odd levels hold mu = f'(c) - kappa Lap c, even levels
+//    the state -- the paper's "Laplacian, boundary rule, Laplacian"
+//    biharmonic (Section 4.1), fused into the march.
 //
-// Without Cahn-Hilliard, L = T and level l is the state after l steps.
-// With it, L = 2T: odd levels hold mu = f'(c) - kappa Lap c, even levels the
-// state, so the biharmonic term is the paper's "Laplacian, boundary rule,
-// Laplacian" (Section 4.1) fused into one pass.
-//
-// Boundary rules are applied where neighbours are read, at every level:
-//   periodic axis  halo cells are real cells at wrapped coordinates, loaded
-//                  and updated like any other cell;
-//   zero-flux axis a neighbour outside the domain is replaced by the cell
-//                  itself (ghost = face cell), so out-of-domain halo cells
-//                  are never read and never loaded;
+// Boundary rules, applied at every level:
+//   periodic axis  halo cells are real cells at wrapped coordinates;
+//   zero flux      a neighbour outside the domain is the cell itself (the
+//                  ghost equals the face cell), so outside cells are never
+//                  read or loaded;
 //   held layer     (Dirichlet) the cell's new value is its bc value.
-// Every cell value, at every level, comes from the same per-cell update with
-// explicitly rounded operations, so a T-step launch gives bit-for-bit the
-// same state as T one-step launches.
+// Every value at every level comes from the same per-cell update with
+// explicitly rounded operations, and inner levels are rounded to the storage
+// type, so a T-step launch reproduces T one-step launches bit for bit.
 #pragma once
 
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+
 #include "rd_internal.h"
 
 namespace rdk {
+
+constexpr int kVEC = 4;               // cells per thread position (x)
+constexpr int kNQ = kTileQ + 2;       // vector positions per row incl. halo
+constexpr int kRW = kNQ * kVEC;       // elements per shared-memory row
 
 // ---------------------------------------------------------------- storage
 template <class ST> struct Store;
 
 template <> struct Store<float> {
-    static constexpr int VEC = 4;
     __device__ __forceinline__ static void load(const float* p, float (&v)[4]) {
-        float4 t = *reinterpret_cast<const float4*>(p);
+        const float4 t = *reinterpret_cast<const float4*>(p);
         v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     }
     __device__ __forceinline__ static void store(float* p, const float (&v)[4]) {
         *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
     __device__ __forceinline__ static float get(const float* p) { return *p; }
+    __device__ __forceinline__ static float round(float x) { return x; }
+    __device__ __forceinline__ static void cp_async(float* smem, const float* g) {
+        const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
+    }
 };
 
 template <> struct Store<__nv_bfloat16> {
-    static constexpr int VEC = 8;
-    __device__ __forceinline__ static void load(const __nv_bfloat16* p, float (&v)[8]) {
-        uint4 t = *reinterpret_cast<const uint4*>(p);
-        const unsigned w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            v[2 * i] = __uint_as_float(w[i] << 16);
-            v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
-        }
+    __device__ __forceinline__ static void load(const __nv_bfloat16* p, float (&v)[4]) {
+        const uint2 t = *reinterpret_cast<const uint2*>(p);
+        v[0] = __uint_as_float(t.x << 16);
+        v[1] = __uint_as_float(t.x & 0xffff0000u);
+        v[2] = __uint_as_float(t.y << 16);
+        v[3] = __uint_as_float(t.y & 0xffff0000u);
     }
-    __device__ __forceinline__ static void store(__nv_bfloat16* p, const float (&v)[8]) {
-        unsigned w[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-            w[i] = *reinterpret_cast<unsigned*>(&h);
-        }
-        *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    __device__ __forceinline__ static void store(__nv_bfloat16* p, const float (&v)[4]) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+        *reinterpret_cast<uint2*>(p) =
+            make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b));
     }
     __device__ __forceinline__ static float get(const __nv_bfloat16* p) {
         return __bfloat162float(*p);
     }
-};
-
-// N consecutive elements of type E (float or bfloat16) as floats, moved with
-// 16-byte shared-memory accesses.
-template <class E, int N> struct Vec;
-template <int N> struct Vec<float, N> {
-    __device__ __forceinline__ static void load(const float* p, float (&v)[N]) {
-#pragma unroll
-        for (int i = 0; i < N / 4; ++i) {
-            float4 t = reinterpret_cast<const float4*>(p)[i];
-            v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
-        }
+    __device__ __forceinline__ static float round(float x) {
+        return __bfloat162float(__float2bfloat16_rn(x));
     }
-    __device__ __forceinline__ static void store(float* p, const float (&v)[N]) {
-#pragma unroll
-        for (int i = 0; i < N / 4; ++i)
-            reinterpret_cast<float4*>(p)[i] =
-                make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-    }
-    __device__ __forceinline__ static float get(const float* p) { return *p; }
-};
-template <int N> struct Vec<__nv_bfloat16, N> {
-    static_assert(N % 8 == 0, "bf16 vectors are 8 wide");
-    __device__ __forceinline__ static void load(const __nv_bfloat16* p, float (&v)[N]) {
-#pragma unroll
-        for (int i = 0; i < N / 8; ++i) {
-            float t[8];
-            Store<__nv_bfloat16>::load(p + 8 * i, t);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[8 * i + e] = t[e];
-        }
-    }
-    __device__ __forceinline__ static void store(__nv_bfloat16* p, const float (&v)[N]) {
-#pragma unroll
-        for (int i = 0; i < N / 8; ++i) {
-            float t[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) t[e] = v[8 * i + e];
-            Store<__nv_bfloat16>::store(p + 8 * i, t);
-        }
-    }
-    __device__ __forceinline__ static float get(const __nv_bfloat16* p) {
-        return __bfloat162float(*p);
+    __device__ __forceinline__ static void cp_async(__nv_bfloat16* smem, const __nv_bfloat16* g) {
+        const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
     }
 };
 
-// 7-point neighbourhood of N cells of one row: centre plus the two
-// neighbours along each axis.  Planes P0 (this z), Pm (z-1), Pp (z+1) are
-// already chosen by the z rule; rows off/offm/offp by the y rule; the x rule
-// for zero-flux faces replaces an outside neighbour by the cell itself.
-template <class E, int N>
-__device__ __forceinline__ void gather7(const E* P0, const E* Pm, const E* Pp, int off,
-                                        int offm, int offp, bool xb, int xs, int nx,
-                                        float (&c)[N], float (&xm)[N], float (&xp)[N],
-                                        float (&ym)[N], float (&yp)[N], float (&zm)[N],
-                                        float (&zp)[N]) {
-    Vec<E, N>::load(P0 + off, c);
-    Vec<E, N>::load(P0 + offm, ym);
-    Vec<E, N>::load(P0 + offp, yp);
-    Vec<E, N>::load(Pm + off, zm);
-    Vec<E, N>::load(Pp + off, zp);
-    const float left = Vec<E, N>::get(P0 + off - 1);
-    const float right = Vec<E, N>::get(P0 + off + N);
-#pragma unroll
-    for (int e = 0; e < N; ++e) {
-        xm[e] = e ? c[e - 1] : left;
-        xp[e] = (e < N - 1) ? c[e + 1] : right;
-    }
-    if (xb) {
-#pragma unroll
-        for (int e = 0; e < N; ++e) {
-            if (xs + e == 0) xm[e] = c[e];
-            if (xs + e == nx - 1) xp[e] = c[e];
-        }
-    }
-}
-
-// ------------------------------------------------------------ async copies
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem)
-                 : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -170,8 +103,7 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 }
 
 // ----------------------------------------------------------------- models
-// Per-cell pieces of eq. (1).  ``react`` returns dt * R_s(c) for every
-// species (the increment before transport terms).
+// Per-cell pieces of eq. (1).  ``react`` returns dt * R_s(c) per species.
 struct MDiffusion {
     static constexpr int S = 1;
     static constexpr bool CH = false;
@@ -233,8 +165,8 @@ struct MChFront {
     }
 };
 
-// One cell of eq. (5) for a species with Fickian transport: c + inc +
-// sum_a k_a (c[-1] + c[+1] - 2c) with k_a = D_a dt / h^2.
+// One cell of eq. (5) for a species with Fickian transport:
+// c + inc + sum_a k_a (c[-1] + c[+1] - 2c), k_a = D_a dt / h^2.
 __device__ __forceinline__ float euler_cell(float c, float xm, float xp, float ym, float yp,
                                             float zm, float zp, float kx, float ky, float kz,
                                             float inc) {
@@ -254,80 +186,157 @@ __device__ __forceinline__ float upwind(float inc, float cx, float c, float xm, 
                       : __fmaf_rn(-cx, __fsub_rn(xp, c), inc);
 }
 
-// Held (Dirichlet) layer test, faces in order -x,+x,-y,+y,-z,+z.
-__device__ __forceinline__ bool held_value(const InstDesc& d, int s, int x, int y, int z,
-                                           float& v) {
-    const unsigned m = d.held_mask[s];
-    if (!m) return false;
-    if ((m & 1u) && x == 0) { v = d.held_val[s][0]; return true; }
-    if ((m & 2u) && x == d.nx - 1) { v = d.held_val[s][1]; return true; }
-    if ((m & 4u) && y == 0) { v = d.held_val[s][2]; return true; }
-    if ((m & 8u) && y == d.ny - 1) { v = d.held_val[s][3]; return true; }
-    if ((m & 16u) && z == 0) { v = d.held_val[s][4]; return true; }
-    if ((m & 32u) && z == d.nz - 1) { v = d.held_val[s][5]; return true; }
-    return false;
-}
-
 // ------------------------------------------------------- shared-memory map
-// Plane buffers: NR rows of RS elements plus a VEC-element guard at each
-// end; ring slots per level as described above.
+// Every level keeps its planes in shared memory; slots are the low bits of
+// the plane index.  Level 0 is a ring of 8 planes per species, P of them in
+// flight ahead of the plane being consumed; an inner level has 4 plane
+// buffers (a mu level holds one field).  The z neighbours a thread needs
+// are its own position in planes q-1 and q+1, which it wrote (or copied)
+// itself; only the x/y neighbours in plane q come from other threads, and
+// that plane was completed before the last barrier.  Hence one barrier per
+// plane suffices when
+//   level 0:  P <= 8 - 3 (read up to two planes after arrival; the
+//             Cahn-Hilliard state level reads it three planes after: P <= 4)
+//   inner:    4 buffers (read up to three planes after it is written).
+// Each plane is rows(ty) rows of kRW elements plus a kVEC guard at both ends.
 template <class M, class ST, int T> struct Layout {
-    static constexpr int VEC = Store<ST>::VEC;
     static constexpr int S = M::S;
     static constexpr bool CH = M::CH;
     static constexpr int L = CH ? 2 * T : T;
-    static constexpr int RING_STATE = CH ? 4 : 3;
-    static constexpr int RING0 = RING_STATE + kPrefetch;
-    static constexpr int RING_MU = 3;
-
-    __host__ __device__ static bool is_mu(int l) { return CH && (l & 1); }
-    __host__ __device__ static int plane_elems(int tq, int ty) {
-        return (ty + 2 * L) * (tq + 2) * VEC + 2 * VEC;
+    static constexpr int RING0 = 8;
+    static constexpr int P = CH ? 4 : 5;     // level-0 planes in flight
+    static constexpr int NBUF = 4;           // planes of an inner level
+    __host__ __device__ static constexpr bool is_mu(int l) { return CH && (l & 1); }
+    __host__ __device__ static int rows(int ty) { return ty + 2 * L; }
+    __host__ __device__ static int plane_elems(int ty) { return rows(ty) * kRW + 2 * kVEC; }
+    __host__ __device__ static size_t level_bytes(int l, int ty) {
+        const size_t pe = plane_elems(ty);
+        if (l == 0) return (size_t)RING0 * S * pe * sizeof(ST);
+        if (is_mu(l)) return (size_t)NBUF * pe * sizeof(float);
+        return (size_t)NBUF * S * pe * sizeof(ST);
     }
-    // bytes of level l's ring (l = 0 .. L-1)
-    __host__ __device__ static size_t level_bytes(int l, int tq, int ty) {
-        const size_t pe = plane_elems(tq, ty);
-        if (l == 0) return RING0 * S * pe * sizeof(ST);
-        if (is_mu(l)) return RING_MU * pe * sizeof(float);
-        return RING_STATE * S * pe * sizeof(ST);
-    }
-    __host__ __device__ static size_t level_offset(int l, int tq, int ty) {
+    __host__ __device__ static size_t level_offset(int l, int ty) {
         size_t o = 0;
-        for (int i = 0; i < l; ++i) o += level_bytes(i, tq, ty);
+        for (int i = 0; i < l; ++i) o += level_bytes(i, ty);
         return o;
     }
-    __host__ __device__ static size_t total(int tq, int ty) { return level_offset(L, tq, ty); }
+    __host__ __device__ static size_t total(int ty) { return level_offset(L, ty); }
+    __host__ __device__ static int threads(int ty) { return kNQ * rows(ty); }
 };
+
+// Per-thread geometry of a work item (fixed for the whole march).
+struct Pos {
+    int own;          // shared-memory element offset of the thread's vector
+    int offm, offp;   // vector above / below (own vector at a zero-flux y face)
+    int offl;         // element left of the vector (own element 0 at x = 0)
+    int xs, y;        // global x of element 0 and global y (unwrapped)
+    int xhi;          // element holding x = nx-1 at a zero-flux face, else -1
+};
+
+// 7-point neighbourhood of the thread's vector in one level: centre and the
+// z neighbours from planes Pc / Pm / Pp at the thread's own position, x and
+// y neighbours from plane Pc.
+template <class E>
+__device__ __forceinline__ void gather7(const E* Pc, const E* Pm, const E* Pp, const Pos& ps,
+                                        float (&c)[kVEC], float (&xm)[kVEC], float (&xp)[kVEC],
+                                        float (&ym)[kVEC], float (&yp)[kVEC],
+                                        float (&zm)[kVEC], float (&zp)[kVEC]) {
+    Store<E>::load(Pc + ps.own, c);
+    Store<E>::load(Pm + ps.own, zm);
+    Store<E>::load(Pp + ps.own, zp);
+    Store<E>::load(Pc + ps.offm, ym);
+    Store<E>::load(Pc + ps.offp, yp);
+    const float left = Store<E>::get(Pc + ps.offl);
+    const float right = Store<E>::get(Pc + ps.own + kVEC);
+#pragma unroll
+    for (int e = 0; e < kVEC; ++e) {
+        xm[e] = e ? c[e - 1] : left;
+        xp[e] = (e < kVEC - 1) ? c[e + 1] : right;
+    }
+    if (ps.xhi >= 0) {
+#pragma unroll
+        for (int e = 0; e < kVEC; ++e)
+            if (e == ps.xhi) xp[e] = c[e];
+    }
+}
+
+// Held (Dirichlet) layers: the first face in -x,+x,-y,+y,-z,+z wins.
+__device__ __forceinline__ void held_layers(const InstDesc& sd, int s, int xs, int y, int q,
+                                            float (&o)[kVEC]) {
+    const unsigned hm = sd.held_mask[s];
+    if (!hm) return;
+#pragma unroll
+    for (int e = 0; e < kVEC; ++e) {
+        const int x = xs + e;
+        float hv = o[e];
+        if ((hm & 32u) && q == sd.nz - 1) hv = sd.held_val[s][5];
+        if ((hm & 16u) && q == 0) hv = sd.held_val[s][4];
+        if ((hm & 8u) && y == sd.ny - 1) hv = sd.held_val[s][3];
+        if ((hm & 4u) && y == 0) hv = sd.held_val[s][2];
+        if ((hm & 2u) && x == sd.nx - 1) hv = sd.held_val[s][1];
+        if ((hm & 1u) && x == 0) hv = sd.held_val[s][0];
+        o[e] = hv;
+    }
+}
+
+// New value of one species on the thread's 4 cells (eq. (5)): reaction
+// increment ``inc`` (dt R), point source, upwind advection, Fickian
+// transport, then held layers.  Shared by every kernel so that all launch
+// shapes give identical bits.
+__device__ __forceinline__ void species_update(const InstDesc& sd, int s, const float (&c)[kVEC],
+                                               const float (&xm)[kVEC], const float (&xp)[kVEC],
+                                               const float (&ym)[kVEC], const float (&yp)[kVEC],
+                                               const float (&zm)[kVEC], const float (&zp)[kVEC],
+                                               const float (&inc)[kVEC], float cx, bool src_here,
+                                               bool px, int xs, int y, int q, float (&o)[kVEC]) {
+    const float kx = sd.kx[s], ky = sd.ky[s], kz = sd.kz[s];
+#pragma unroll
+    for (int e = 0; e < kVEC; ++e) {
+        float in = inc[e];
+        if (src_here && s == sd.src_s && (px ? wrapi(xs + e, sd.nx) : xs + e) == sd.src_x)
+            in = __fadd_rn(in, sd.src_amt);
+        if (cx != 0.0f) in = upwind(in, cx, c[e], xm[e], xp[e]);
+        o[e] = euler_cell(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, ky, kz, in);
+    }
+    held_layers(sd, s, xs, y, q, o);
+}
 
 // ------------------------------------------------------------------ kernel
 template <class M, class ST, int T>
-__global__ void __launch_bounds__(kThreads) rd_step_kernel(const LaunchArgs a) {
-    using SX = Store<ST>;
+__global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const LaunchArgs a) {
     using LY = Layout<M, ST, T>;
-    constexpr int VEC = SX::VEC;
     constexpr int S = M::S;
     constexpr bool CH = M::CH;
     constexpr int L = LY::L;
+    constexpr int P = LY::P;
 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ InstDesc sd;
     __shared__ int s_inst;
 
     const int tid = threadIdx.x;
-    const int tq = a.tq, TY = a.ty;
-    const int nq = tq + 2;
-    const int RS = nq * VEC;
-    const int NR = TY + 2 * L;
-    const int PE = LY::plane_elems(tq, TY);
+    const int TY = a.ty;
+    const int NR = LY::rows(TY);
+    const int PE = LY::plane_elems(TY);
+    const int r = tid / kNQ;             // row of the thread's position
+    const int v = tid - r * kNQ;         // vector of the thread's position
+
+    // plane X of state level m, species s; plane X of mu level m
+    auto state_plane = [&](int m, int s, int X) -> ST* {
+        const int slot = (m == 0) ? (X & (LY::RING0 - 1)) : (X & (LY::NBUF - 1));
+        return reinterpret_cast<ST*>(smem + LY::level_offset(m, TY)) + (size_t)(slot * S + s) * PE +
+               kVEC;
+    };
+    auto mu_plane = [&](int m, int X) -> float* {
+        return reinterpret_cast<float*>(smem + LY::level_offset(m, TY)) +
+               (size_t)(X & (LY::NBUF - 1)) * PE + kVEC;
+    };
 
     int cur_inst = -1;
     if (tid == 0) s_inst = 0;
     for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-        // ---- which instance owns this item
-        if (a.ninst == 1) {
-            if (tid == 0) s_inst = 0;
-        } else {
-            for (int i = tid; i < a.ninst; i += kThreads) {
+        if (a.ninst > 1) {
+            for (int i = tid; i < a.ninst; i += blockDim.x) {
                 const long long b0 = a.desc[i].item_begin;
                 const long long b1 = (i + 1 < a.ninst) ? a.desc[i + 1].item_begin : a.nitems;
                 if (item >= b0 && item < b1) s_inst = i;
@@ -338,203 +347,382 @@ __global__ void __launch_bounds__(kThreads) rd_step_kernel(const LaunchArgs a) {
             cur_inst = s_inst;
             const int* src = reinterpret_cast<const int*>(a.desc + cur_inst);
             int* dst = reinterpret_cast<int*>(&sd);
-            for (int i = tid; i < (int)(sizeof(InstDesc) / sizeof(int)); i += kThreads)
+            for (int i = tid; i < (int)(sizeof(InstDesc) / sizeof(int)); i += blockDim.x)
                 dst[i] = src[i];
         }
         __syncthreads();
 
-        const int nx = sd.nx, ny = sd.ny, nz = sd.nz, pitch = sd.pitch;
-        const long long plane = sd.plane;
+        const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
         const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;
         const long long local = item - sd.item_begin;
-        const int tx = (int)(local % sd.ntx);
+        const int txi = (int)(local % sd.ntx);
         const int tyi = (int)((local / sd.ntx) % sd.nty);
         const int zc = (int)(local / ((long long)sd.ntx * sd.nty));
-        const int x0 = tx * tq * VEC, y0 = tyi * TY;
+        const int x0 = txi * kTileQ * kVEC, y0 = tyi * TY;
         const int z0 = zc * sd.zchunk;
         const int z1 = min(z0 + sd.zchunk, nz);
         const int lin = sd.par ^ a.parity;
 
-        // -------------------------------------------------------- loader
-        auto ring0 = [&](int s, int slot) -> ST* {
-            return reinterpret_cast<ST*>(smem) + (size_t)(slot * S + s) * PE + VEC;
-        };
-        auto load_plane = [&](int q) {
-            if (!pz && (q < 0 || q >= nz)) return;
-            const int zw = pz ? wrapi(q, nz) : q;
-            const int slot = wrapi(q, LY::RING0);
-            const int per_s = NR * nq;
-            for (int u = tid; u < S * per_s; u += kThreads) {
-                const int s = u / per_s;
-                const int rem = u - s * per_s;
-                const int r = rem / nq;
-                const int v = rem - r * nq;
-                const int y = y0 - L + r;
-                int yw = y;
-                if (py) yw = wrapi(y, ny);
-                else if (y < 0 || y >= ny) continue;
-                const int xs = x0 - VEC + v * VEC;
-                ST* dst = ring0(s, slot) + r * RS + v * VEC;
-                const ST* row = reinterpret_cast<const ST*>(sd.base[lin][s]) +
-                                (size_t)zw * plane + (size_t)yw * pitch;
-                if (xs >= 0 && xs < nx) {
-                    if (!px || xs + VEC <= nx) { cp_async16(dst, row + xs); continue; }
-                } else if (!px) {
-                    continue;                         // zero-flux halo: never read
-                } else {
-                    // a wrapped vector is copied whole only from a 16-byte
-                    // aligned start that does not cross the wrap point
-                    const int xw = wrapi(xs, nx);
-                    if (xw % VEC == 0 && xw + VEC <= nx) { cp_async16(dst, row + xw); continue; }
-                }
-                // periodic vector straddling the wrap point: element-wise
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) dst[e] = row[wrapi(xs + e, nx)];
+        // ---- per-thread geometry
+        Pos ps;
+        ps.y = y0 - L + r;
+        ps.xs = x0 - kVEC + v * kVEC;
+        const bool yin = py || (ps.y >= 0 && ps.y < ny);
+        const bool xin = px || (ps.xs + kVEC > 0 && ps.xs < nx);
+        const bool in_dom = r < NR && yin && xin;
+        ps.own = r * kRW + v * kVEC;
+        ps.offm = (!py && ps.y == 0) ? ps.own : ps.own - kRW;
+        ps.offp = (!py && ps.y == ny - 1) ? ps.own : ps.own + kRW;
+        ps.offl = (!px && ps.xs == 0) ? ps.own : ps.own - 1;
+        ps.xhi = (!px && ps.xs <= nx - 1 && nx - 1 < ps.xs + kVEC) ? nx - 1 - ps.xs : -1;
+        const int yw = py ? wrapi(ps.y, ny) : ps.y;
+        // global load of the thread's vector: 1 = one copy, 2 = wrapped
+        // element by element, 0 = none
+        int ld_mode = 0;
+        long long ld_off = 0;
+        if (in_dom) {
+            const long long row = (long long)yw * sd.pitch;
+            if (ps.xs >= 0 && ps.xs < nx && (!px || ps.xs + kVEC <= nx)) {
+                ld_mode = 1;
+                ld_off = row + ps.xs;
+            } else if (px) {
+                const int xw = wrapi(ps.xs, nx);
+                if (xw % kVEC == 0 && xw + kVEC <= nx) { ld_mode = 1; ld_off = row + xw; }
+                else { ld_mode = 2; ld_off = row; }
             }
-        };
-
-        // ---------------------------------------------- per-level compute
-        // level l: q = plane, reads level l-1 (and l-2 for the CH state)
-        auto level_ptr = [&](int l, int s, int q) -> void* {
-            if (l == 0) return ring0(s, wrapi(q, LY::RING0));
-            unsigned char* b = smem + LY::level_offset(l, tq, TY);
-            if (LY::is_mu(l)) return reinterpret_cast<float*>(b) + (size_t)wrapi(q, LY::RING_MU) * PE + VEC;
-            return reinterpret_cast<ST*>(b) +
-                   (size_t)(wrapi(q, LY::RING_STATE) * S + s) * PE + VEC;
-        };
-
-        const int pbeg = z0 - L, pend = z1 + L;
-#pragma unroll 1
-        for (int j = 0; j < kPrefetch; ++j) {
-            if (pbeg + j < pend) load_plane(pbeg + j);
-            cp_async_commit();
         }
+        // levels this position computes: bit l (l = L: the stored tile)
+        unsigned lbits = 0;
+        if (in_dom) {
+#pragma unroll
+            for (int l = 1; l < L; ++l)
+                if (r >= l && r < NR - l) lbits |= 1u << l;
+            if (r >= L && r < L + TY && v >= 1 && v <= kTileQ && ps.y >= 0 && ps.y < ny &&
+                ps.xs < nx)
+                lbits |= 1u << L;
+        }
+        const long long st_off = (long long)ps.y * sd.pitch + ps.xs;
+        const bool src_col = sd.src_s >= 0 && yw == sd.src_y;
+
+        // ---- loads: plane ``nld`` (wrapped index zld) into the level-0 ring
+        const int pbeg = z0 - L, pend = z1 + L;
+        int nld = pbeg;
+        int zld = pz ? wrapi(nld, nz) : nld;
+        auto issue = [&]() {
+            if (nld < pend && ld_mode != 0 && (pz || (nld >= 0 && nld < nz))) {
+                const long long zoff = (long long)zld * sd.plane + ld_off;
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const ST* g = reinterpret_cast<const ST*>(sd.base[lin][s]) + zoff;
+                    ST* dst = state_plane(0, s, nld) + ps.own;
+                    if (ld_mode == 1) {
+                        Store<ST>::cp_async(dst, g);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < kVEC; ++e) dst[e] = g[wrapi(ps.xs + e, nx)];
+                    }
+                }
+            }
+            ++nld;
+            if (!pz) zld = nld;
+            else if (++zld == nz) zld = 0;
+            cp_async_commit();
+        };
+
+#pragma unroll 1
+        for (int j = 0; j < P; ++j) issue();
+        int zcur = pz ? wrapi(pbeg, nz) : pbeg;   // wrapped index of plane p
 #pragma unroll 1
         for (int p = pbeg; p < pend; ++p) {
-            if (p + kPrefetch < pend) load_plane(p + kPrefetch);
-            cp_async_commit();
-            cp_async_wait<kPrefetch>();
+            issue();
+            cp_async_wait<P>();
             __syncthreads();
 #pragma unroll
             for (int l = 1; l <= L; ++l) {
                 const int q = p - l;
                 const bool valid = q >= z0 - L + l && q < z1 + L - l && (pz || (q >= 0 && q < nz));
-                if (valid) {
-                    const bool fin = (l == L);
-                    const bool mu_lvl = LY::is_mu(l);
-                    // state source level for Fickian terms and centres
-                    const int ls = (CH && !mu_lvl) ? l - 2 : l - 1;
-                    int qm = q - 1, qp = q + 1;
-                    if (!pz) { if (q == 0) qm = q; if (q == nz - 1) qp = q; }
-                    const int zw = pz ? wrapi(q, nz) : q;
-                    const float cx = sd.courant ? sd.courant[zw] : 0.0f;
-                    const int r_lo = l, r_hi = NR - l;
-                    const int v_lo = fin ? 1 : 0, v_hi = fin ? nq - 1 : nq;
-                    const int nv = v_hi - v_lo;
-                    const int nunits = (r_hi - r_lo) * nv;
-                    for (int u = tid; u < nunits; u += kThreads) {
-                        const int rr = u / nv;
-                        const int r = r_lo + rr;
-                        const int v = v_lo + (u - rr * nv);
-                        const int y = y0 - L + r;
-                        if (!py && (y < 0 || y >= ny)) continue;
-                        const int xs = x0 - VEC + v * VEC;
-                        if (!px && (xs + VEC <= 0 || xs >= nx)) continue;
-                        if (fin && (y >= ny || xs >= nx)) continue;
-                        const int yw = py ? wrapi(y, ny) : y;
-                        int rm = r - 1, rp = r + 1;
-                        if (!py) { if (y == 0) rm = r; if (y == ny - 1) rp = r; }
-                        const bool xb = !px && (xs <= 0 || xs + VEC >= nx);
-                        const int off = r * RS + v * VEC;
-                        const int offm = rm * RS + v * VEC;
-                        const int offp = rp * RS + v * VEC;
-
-                        if (mu_lvl) {
-                            // mu of the Cahn-Hilliard species from level l-1
-                            const ST* P0 = (const ST*)level_ptr(l - 1, 2, q);
-                            const ST* Pm = (const ST*)level_ptr(l - 1, 2, qm);
-                            const ST* Pp = (const ST*)level_ptr(l - 1, 2, qp);
-                            float c[VEC], xm[VEC], xp[VEC], ym[VEC], yp[VEC], zm[VEC], zp[VEC];
-                            gather7<ST, VEC>(P0, Pm, Pp, off, offm, offp, xb, xs, nx, c, xm, xp, ym, yp, zm, zp);
-                            float mo[VEC];
+                if (!valid || !(lbits & (1u << l))) continue;
+                const bool fin = (l == L);
+                int zw = q;
+                if (pz) { zw = zcur - l; while (zw < 0) zw += nz; }
+                // z neighbours: the face plane itself at a zero-flux z face
+                const int qm = (!pz && q == 0) ? q : q - 1;
+                const int qp = (!pz && q == nz - 1) ? q : q + 1;
+                if (LY::is_mu(l)) {
+                    // mu of the Cahn-Hilliard species from state level l-1
+                    float c[kVEC], xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC];
+                    gather7<ST>(state_plane(l - 1, 2, q), state_plane(l - 1, 2, qm),
+                                state_plane(l - 1, 2, qp), ps, c, xm, xp, ym, yp, zm, zp);
+                    float mo[kVEC];
 #pragma unroll
-                            for (int e = 0; e < VEC; ++e)
-                                mo[e] = MChFront::mu(sd, c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e]);
-                            Vec<float, VEC>::store((float*)level_ptr(l, 0, q) + off, mo);
-                            continue;
-                        }
-
-                        // centres of all species, then the reaction increments
-                        float cen[S][VEC], inc[S][VEC];
+                    for (int e = 0; e < kVEC; ++e)
+                        mo[e] = MChFront::mu(sd, c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e]);
+                    Store<float>::store(mu_plane(l, q) + ps.own, mo);
+                    continue;
+                }
+                // state update from level ls (and, for Cahn-Hilliard, mu at l-1)
+                const int ls = CH ? l - 2 : l - 1;
+                float inc[S][kVEC];
+                {
+                    float cen[S][kVEC];
 #pragma unroll
-                        for (int s = 0; s < S; ++s)
-                            SX::load((const ST*)level_ptr(ls, s, q) + off, cen[s]);
+                    for (int s = 0; s < S; ++s) Store<ST>::load(state_plane(ls, s, q) + ps.own, cen[s]);
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e) {
-                            float cv[S], iv[S];
+                    for (int e = 0; e < kVEC; ++e) {
+                        float cv[S], iv[S];
 #pragma unroll
-                            for (int s = 0; s < S; ++s) cv[s] = cen[s][e];
-                            M::react(sd, cv, iv);
+                        for (int s = 0; s < S; ++s) cv[s] = cen[s][e];
+                        M::react(sd, cv, iv);
 #pragma unroll
-                            for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
-                        }
-                        const bool src_here = sd.src_s >= 0 && zw == sd.src_z && yw == sd.src_y;
-#pragma unroll
-                        for (int s = 0; s < S; ++s) {
-                            float o[VEC];
-                            if (CH && s == 2) {
-                                const float* U0 = (const float*)level_ptr(l - 1, 0, q);
-                                const float* Um = (const float*)level_ptr(l - 1, 0, qm);
-                                const float* Up = (const float*)level_ptr(l - 1, 0, qp);
-                                float m0[VEC], mxm[VEC], mxp[VEC], mym[VEC], myp[VEC], mzm[VEC], mzp[VEC];
-                                gather7<float, VEC>(U0, Um, Up, off, offm, offp, xb, xs, nx, m0, mxm, mxp, mym, myp, mzm, mzp);
-#pragma unroll
-                                for (int e = 0; e < VEC; ++e) {
-                                    const float s6 = __fadd_rn(__fadd_rn(__fadd_rn(mxm[e], mxp[e]),
-                                                                         __fadd_rn(mym[e], myp[e])),
-                                                               __fadd_rn(mzm[e], mzp[e]));
-                                    const float lap = __fmaf_rn(-6.0f, m0[e], s6);
-                                    const float in = __fmaf_rn(sd.p[1], lap, inc[s][e]);
-                                    o[e] = __fadd_rn(cen[s][e], in);
-                                }
-                            } else {
-                                const ST* P0 = (const ST*)level_ptr(ls, s, q);
-                                const ST* Pm = (const ST*)level_ptr(ls, s, qm);
-                                const ST* Pp = (const ST*)level_ptr(ls, s, qp);
-                                float c[VEC], xm[VEC], xp[VEC], ym[VEC], yp[VEC], zm[VEC], zp[VEC];
-                                gather7<ST, VEC>(P0, Pm, Pp, off, offm, offp, xb, xs, nx, c, xm, xp, ym, yp, zm, zp);
-                                const float kx = sd.kx[s], ky = sd.ky[s], kz = sd.kz[s];
-#pragma unroll
-                                for (int e = 0; e < VEC; ++e) {
-                                    float in = inc[s][e];
-                                    if (src_here && s == sd.src_s) {
-                                        const int xw = px ? wrapi(xs + e, nx) : xs + e;
-                                        if (xw == sd.src_x) in = __fadd_rn(in, sd.src_amt);
-                                    }
-                                    if (cx != 0.0f) in = upwind(in, cx, c[e], xm[e], xp[e]);
-                                    o[e] = euler_cell(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e],
-                                                      kx, ky, kz, in);
-                                }
-                            }
-                            if (sd.held_mask[s]) {
-#pragma unroll
-                                for (int e = 0; e < VEC; ++e) {
-                                    float hv;
-                                    if (held_value(sd, s, xs + e, y, q, hv)) o[e] = hv;
-                                }
-                            }
-                            if (fin) {
-                                ST* g = reinterpret_cast<ST*>(sd.base[lin ^ 1][s]) +
-                                        (size_t)q * plane + (size_t)y * pitch + xs;
-                                SX::store(g, o);
-                            } else {
-                                SX::store((ST*)level_ptr(l, s, q) + off, o);
-                            }
-                        }
+                        for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
                     }
                 }
-                __syncthreads();
+                const float cx = sd.courant ? sd.courant[zw] : 0.0f;
+                const bool src_here = src_col && zw == sd.src_z;
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    float o[kVEC];
+                    if (CH && s == 2) {
+                        // c += dt M / h^2 * (7-point Laplacian of mu)
+                        float m0[kVEC], mxm[kVEC], mxp[kVEC], mym[kVEC], myp[kVEC], mzm[kVEC],
+                            mzp[kVEC], c[kVEC];
+                        gather7<float>(mu_plane(l - 1, q), mu_plane(l - 1, qm), mu_plane(l - 1, qp),
+                                       ps, m0, mxm, mxp, mym, myp, mzm, mzp);
+                        Store<ST>::load(state_plane(ls, 2, q) + ps.own, c);
+#pragma unroll
+                        for (int e = 0; e < kVEC; ++e) {
+                            const float s6 = __fadd_rn(
+                                __fadd_rn(__fadd_rn(mxm[e], mxp[e]), __fadd_rn(mym[e], myp[e])),
+                                __fadd_rn(mzm[e], mzp[e]));
+                            const float lap = __fmaf_rn(-6.0f, m0[e], s6);
+                            o[e] = __fadd_rn(c[e], __fmaf_rn(sd.p[1], lap, inc[s][e]));
+                        }
+                    } else {
+                        float c[kVEC], xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC];
+                        gather7<ST>(state_plane(ls, s, q), state_plane(ls, s, qm),
+                                    state_plane(ls, s, qp), ps, c, xm, xp, ym, yp, zm, zp);
+                        species_update(sd, s, c, xm, xp, ym, yp, zm, zp, inc[s], cx, src_here, px,
+                                       ps.xs, ps.y, q, o);
+                    }
+                    if (CH && s == 2) held_layers(sd, s, ps.xs, ps.y, q, o);
+                    if (fin) {
+                        ST* g = reinterpret_cast<ST*>(sd.base[lin ^ 1][s]);
+                        Store<ST>::store(g + (long long)q * sd.plane + st_off, o);
+                    } else {
+                        // inner level, rounded exactly as a stored state
+                        Store<ST>::store(state_plane(l, s, q) + ps.own, o);
+                    }
+                }
             }
+            if (pz && ++zcur == nz) zcur = 0;
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ one-step kernel
+// The T = 1 path of the models without Cahn-Hilliard: one thread per
+// 4-cell vector of a 64 x TY tile, no idle halo threads.  Threads on the
+// tile edge also fetch the halo vectors (one row above/below, one vector
+// left/right; the 7-point stencil needs no corners).  Planes arrive in an
+// 8-slot shared-memory ring.  While plane q is computed, planes q-1..q+1
+// are resident and q+2..q+6 are in flight (P = 7 copy groups ahead of q-1).
+// A thread reads its own vector in planes q-1, q, q+1 and its neighbours in
+// plane q; the slot refilled at step q held plane q-2, whose neighbour
+// reads ended two barriers earlier and whose own-vector reads precede the
+// refill in the thread's program order, so one barrier per plane suffices.
+template <class M, class ST> struct Layout1 {
+    static constexpr int S = M::S;
+    static constexpr int RING = 8;
+    static constexpr int P = 7;
+    __host__ __device__ static int plane_elems(int ty) { return (ty + 2) * kRW + 2 * kVEC; }
+    __host__ __device__ static size_t total(int ty) {
+        return (size_t)RING * S * plane_elems(ty) * sizeof(ST);
+    }
+    __host__ __device__ static int threads(int ty) { return kTileQ * ty; }
+};
+
+// How a thread fetches one vector: 1 = one async copy, 2 = element by
+// element with wrapped x, 0 = nothing (outside a zero-flux face).
+struct Fetch {
+    int mode;
+    int goff;    // element offset of row + x within a plane
+    int soff;    // element offset of the position within a plane buffer
+};
+
+__device__ __forceinline__ Fetch make_fetch(int yrow, int xs, int nx, int ny, int pitch, bool px,
+                                            bool py, int soff) {
+    Fetch f{0, 0, soff};
+    if (!py && (yrow < 0 || yrow >= ny)) return f;
+    const int yw = py ? wrapi(yrow, ny) : yrow;
+    const int row = yw * pitch;
+    if (xs >= 0 && xs < nx && (!px || xs + kVEC <= nx)) {
+        f.mode = 1;
+        f.goff = row + xs;
+    } else if (px) {
+        const int xw = wrapi(xs, nx);
+        if (xw % kVEC == 0 && xw + kVEC <= nx) { f.mode = 1; f.goff = row + xw; }
+        else { f.mode = 2; f.goff = row; }
+    }
+    return f;
+}
+
+template <class ST>
+__device__ __forceinline__ void fetch(const Fetch& f, ST* plane_buf, const ST* gplane, int xs,
+                                      int nx) {
+    if (f.mode == 1) {
+        Store<ST>::cp_async(plane_buf + f.soff, gplane + f.goff);
+    } else if (f.mode == 2) {
+#pragma unroll
+        for (int e = 0; e < kVEC; ++e) plane_buf[f.soff + e] = gplane[f.goff + wrapi(xs + e, nx)];
+    }
+}
+
+template <class M, class ST>
+__global__ void __launch_bounds__(kMaxThreads, 1) rd_step1_kernel(const LaunchArgs a) {
+    using LY = Layout1<M, ST>;
+    constexpr int S = M::S;
+    constexpr int P = LY::P;
+    constexpr int RING = LY::RING;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ InstDesc sd;
+    __shared__ int s_inst;
+
+    ST* const ring = reinterpret_cast<ST*>(smem) + kVEC;   // slot 0, species 0
+    const int tid = threadIdx.x;
+    const int TY = a.ty;
+    const int PE = LY::plane_elems(TY);
+    const int r = tid / kTileQ;
+    const int v = tid - r * kTileQ;
+    const int own = (r + 1) * kRW + (v + 1) * kVEC;
+
+    int cur_inst = -1;
+    if (tid == 0) s_inst = 0;
+    for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+        if (a.ninst > 1) {
+            for (int i = tid; i < a.ninst; i += blockDim.x) {
+                const long long b0 = a.desc[i].item_begin;
+                const long long b1 = (i + 1 < a.ninst) ? a.desc[i + 1].item_begin : a.nitems;
+                if (item >= b0 && item < b1) s_inst = i;
+            }
+        }
+        __syncthreads();
+        if (s_inst != cur_inst) {
+            cur_inst = s_inst;
+            const int* src = reinterpret_cast<const int*>(a.desc + cur_inst);
+            int* dst = reinterpret_cast<int*>(&sd);
+            for (int i = tid; i < (int)(sizeof(InstDesc) / sizeof(int)); i += blockDim.x)
+                dst[i] = src[i];
+        }
+        __syncthreads();
+
+        const int nx = sd.nx, ny = sd.ny, nz = sd.nz, pitch = sd.pitch;
+        const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;
+        const long long local = item - sd.item_begin;
+        const int txi = (int)(local % sd.ntx);
+        const int tyi = (int)((local / sd.ntx) % sd.nty);
+        const int zc = (int)(local / ((long long)sd.ntx * sd.nty));
+        const int x0 = txi * kTileQ * kVEC, y0 = tyi * TY;
+        const int z0 = zc * sd.zchunk;
+        const int z1 = min(z0 + sd.zchunk, nz);
+        const int lin = sd.par ^ a.parity;
+
+        // ---- per-thread geometry
+        Pos ps;
+        ps.y = y0 + r;
+        ps.xs = x0 + v * kVEC;
+        ps.own = own;
+        ps.offm = (!py && ps.y == 0) ? own : own - kRW;
+        ps.offp = (!py && ps.y == ny - 1) ? own : own + kRW;
+        ps.offl = (!px && ps.xs == 0) ? own : own - 1;
+        ps.xhi = (!px && ps.xs <= nx - 1 && nx - 1 < ps.xs + kVEC) ? nx - 1 - ps.xs : -1;
+        const bool computes = ps.y < ny && ps.xs < nx;
+        const bool src_col = sd.src_s >= 0 && (py ? wrapi(ps.y, ny) : ps.y) == sd.src_y;
+        const long long st_off = (long long)ps.y * pitch + ps.xs;
+        // the thread's own vector, and the halo vectors it is responsible for
+        const Fetch f_own = make_fetch(ps.y, ps.xs, nx, ny, pitch, px, py, own);
+        Fetch f_y{0, 0, 0}, f_x{0, 0, 0};
+        if (r == 0) f_y = make_fetch(y0 - 1, ps.xs, nx, ny, pitch, px, py, own - kRW);
+        else if (r == TY - 1) f_y = make_fetch(y0 + TY, ps.xs, nx, ny, pitch, px, py, own + kRW);
+        const int xhalo = (v == 0) ? x0 - kVEC : x0 + kTileQ * kVEC;
+        if (v == 0 || v == kTileQ - 1) {
+            const int sh = (v == 0) ? own - kVEC : own + kVEC;
+            f_x = make_fetch(ps.y, xhalo, nx, ny, pitch, px, py, sh);
+        }
+        // the y-halo rows of the last tile row may lie past ny: then they
+        // belong to no thread's own load, as intended
+
+        // ---- the march: plane nld is fetched P planes ahead of plane p
+        int nld = z0 - 1;
+        int zld = pz ? wrapi(nld, nz) : nld;
+        auto issue = [&]() {
+            if (nld <= z1 && (pz || (nld >= 0 && nld < nz))) {
+                const long long zoff = (long long)zld * sd.plane;
+                ST* buf = ring + (size_t)(nld & (RING - 1)) * S * PE;
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const ST* g = reinterpret_cast<const ST*>(sd.base[lin][s]) + zoff;
+                    ST* b = buf + (size_t)s * PE;
+                    fetch(f_own, b, g, ps.xs, nx);
+                    fetch(f_y, b, g, ps.xs, nx);
+                    fetch(f_x, b, g, xhalo, nx);
+                }
+            }
+            ++nld;
+            if (!pz) zld = nld;
+            else if (++zld == nz) zld = 0;
+            cp_async_commit();
+        };
+
+#pragma unroll 1
+        for (int j = 0; j < P; ++j) issue();
+        int zq = pz ? wrapi(z0, nz) : z0;     // wrapped index of plane q
+        const float* courant = sd.courant;
+#pragma unroll 1
+        for (int q = z0; q < z1; ++q) {
+            // planes up to q + 1 must have landed: of the P + (q - z0 + 1)
+            // groups issued so far, all but the newest P - 2
+            issue();
+            cp_async_wait<P - 2>();
+            __syncthreads();
+            if (computes) {
+                const int qm = (!pz && q == 0) ? q : q - 1;
+                const int qp = (!pz && q == nz - 1) ? q : q + 1;
+                const ST* Pc = ring + (size_t)(q & (RING - 1)) * S * PE;
+                const ST* Pm = ring + (size_t)(qm & (RING - 1)) * S * PE;
+                const ST* Pp = ring + (size_t)(qp & (RING - 1)) * S * PE;
+                float inc[S][kVEC];
+                {
+                    float cen[S][kVEC];
+#pragma unroll
+                    for (int s = 0; s < S; ++s) Store<ST>::load(Pc + (size_t)s * PE + own, cen[s]);
+#pragma unroll
+                    for (int e = 0; e < kVEC; ++e) {
+                        float cv[S], iv[S];
+#pragma unroll
+                        for (int s = 0; s < S; ++s) cv[s] = cen[s][e];
+                        M::react(sd, cv, iv);
+#pragma unroll
+                        for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
+                    }
+                }
+                const float cx = courant ? courant[zq] : 0.0f;
+                const bool src_here = src_col && zq == sd.src_z;
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    float c[kVEC], xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], o[kVEC];
+                    gather7<ST>(Pc + (size_t)s * PE, Pm + (size_t)s * PE, Pp + (size_t)s * PE, ps, c,
+                                xm, xp, ym, yp, zm, zp);
+                    species_update(sd, s, c, xm, xp, ym, yp, zm, zp, inc[s], cx, src_here, px,
+                                   ps.xs, ps.y, q, o);
+                    ST* g = reinterpret_cast<ST*>(sd.base[lin ^ 1][s]);
+                    Store<ST>::store(g + (long long)q * sd.plane + st_off, o);
+                }
+            }
+            if (!pz) zq = q + 1;
+            else if (++zq == nz) zq = 0;
         }
         cp_async_wait<0>();
         __syncthreads();
@@ -544,7 +732,10 @@ __global__ void __launch_bounds__(kThreads) rd_step_kernel(const LaunchArgs a) {
 // Launch helper used by the per-model translation units.
 template <class M, class ST, int T>
 cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t st, int* occ) {
-    auto k = rd_step_kernel<M, ST, T>;
+    constexpr bool lean = (T == 1 && !M::CH);
+    void (*k)(const LaunchArgs);
+    if constexpr (lean) k = rd_step1_kernel<M, ST>;
+    else k = rd_step_kernel<M, ST, T>;
     static size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -552,10 +743,10 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    if (occ) {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, kThreads, smem);
-    }
-    k<<<grid, kThreads, smem, st>>>(a);
+    const int threads = lean ? Layout1<M, ST>::threads(a.ty) : Layout<M, ST, T>::threads(a.ty);
+    if (threads > kMaxThreads) return cudaErrorInvalidConfiguration;
+    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, threads, smem);
+    k<<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -583,18 +774,19 @@ cudaError_t launch_model(int storage, int tsteps, const LaunchArgs& a, int grid,
 }
 
 template <class M>
-size_t smem_for(int storage, int tsteps, int tq, int ty) {
+size_t smem_for(int storage, int tsteps, int ty) {
     if (storage == RD_STORE_F32) {
         switch (tsteps) {
-        case 1: return Layout<M, float, 1>::total(tq, ty);
-        case 2: return Layout<M, float, 2>::total(tq, ty);
-        case 3: return Layout<M, float, 3>::total(tq, ty);
+        case 1: return M::CH ? Layout<M, float, 1>::total(ty) : Layout1<M, float>::total(ty);
+        case 2: return Layout<M, float, 2>::total(ty);
+        case 3: return Layout<M, float, 3>::total(ty);
         }
     } else {
         switch (tsteps) {
-        case 1: return Layout<M, __nv_bfloat16, 1>::total(tq, ty);
-        case 2: return Layout<M, __nv_bfloat16, 2>::total(tq, ty);
-        case 3: return Layout<M, __nv_bfloat16, 3>::total(tq, ty);
+        case 1: return M::CH ? Layout<M, __nv_bfloat16, 1>::total(ty)
+                             : Layout1<M, __nv_bfloat16>::total(ty);
+        case 2: return Layout<M, __nv_bfloat16, 2>::total(ty);
+        case 3: return Layout<M, __nv_bfloat16, 3>::total(ty);
         }
     }
     return 0;

@@ -133,8 +133,9 @@ class Sim:
     def set_field(self, s, values):
         addr, keep = _ptr(values)
         n = self.ncell
-        if getattr(keep, "size", None) is not None and keep.size != n:
-            raise ValueError("wrong field size")
+        count = keep.size if isinstance(keep, np.ndarray) else keep.numel()
+        if count != n:
+            raise ValueError(f"field has {count} values, the grid {n}")
         self._check(self.lib.rd_set_field(self.ctx, s, ctypes.c_void_p(addr), n), "rd_set_field")
 
     def set_fields(self, fields):

@@ -44,7 +44,7 @@ def run_gpu(rd, cfg, steps, storage="f32", tuning=None, fields=None):
         return sim.get_fields()
 
 
-SHAPE = (41, 22, 18)
+SHAPE = (141, 23, 19)   # 3 x tiles of 64 (ragged 13), ragged y tiles and z chunks
 
 
 def family_cases():
@@ -75,10 +75,11 @@ def family_cases():
 
 CASES = family_cases()
 TILINGS = [
-    dict(tsteps=1, tile_q=4, tile_y=4, zchunk=5, graph=0),
-    dict(tsteps=2, tile_q=3, tile_y=5, zchunk=7, graph=0),
-    dict(tsteps=3, tile_q=5, tile_y=3, zchunk=4, graph=1),
-    dict(tsteps=2, tile_q=32, tile_y=16, zchunk=18, graph=1),
+    dict(tsteps=1, tile_q=16, tile_y=4, zchunk=5, graph=0),
+    dict(tsteps=2, tile_q=16, tile_y=5, zchunk=7, graph=0),
+    dict(tsteps=3, tile_q=16, tile_y=3, zchunk=4, graph=1),
+    dict(tsteps=2, tile_q=16, tile_y=8, zchunk=19, graph=1),
+    dict(tsteps=1, tile_q=16, tile_y=16, zchunk=8, graph=1),
 ]
 
 
@@ -123,7 +124,7 @@ def test_bf16_storage_is_close_and_depth_invariant(rd, orc, name):
 def test_graph_replay_matches_plain_launches(rd):
     cfg = W.brusselator(shape=(48, 40, 36))
     f = W.initial_fields(cfg)
-    t = dict(tsteps=1, tile_q=8, tile_y=8, zchunk=12)
+    t = dict(tsteps=1, tile_q=16, tile_y=8, zchunk=12)
     a = run_gpu(rd, cfg, 70, tuning=dict(t, graph=1), fields=f)
     b = run_gpu(rd, cfg, 70, tuning=dict(t, graph=0), fields=f)
     assert np.array_equal(a, b)
@@ -132,13 +133,13 @@ def test_graph_replay_matches_plain_launches(rd):
 def test_steps_split_across_calls_match_one_call(rd):
     cfg = W.air((40, 24, 16), src=(3, 4, 5))
     f = W.initial_fields(cfg)
-    with rd.Sim(cfg, tuning=dict(tsteps=2)) as sim:
+    with rd.Sim(cfg, tuning=dict(tsteps=2, tile_y=8)) as sim:
         sim.set_fields(f)
         for n in (1, 5, 2, 17, 0, 3):
             sim.step(n)
         a = sim.get_fields()
         assert sim.steps_done == 28
-    b = run_gpu(rd, cfg, 28, tuning=dict(tsteps=3), fields=f)
+    b = run_gpu(rd, cfg, 28, tuning=dict(tsteps=3, tile_y=4), fields=f)
     assert np.array_equal(a, b)
 
 
@@ -160,14 +161,14 @@ def test_checkpoint_resume_is_bitwise(rd):
 
 @pytest.mark.parametrize("model", ["diffusion", "brusselator", "ch_front", "air"])
 def test_batch_matches_standalone_bitwise(rd, model):
-    sizes = [(23, 17, 11), (40, 9, 14), (16, 33, 25), (50, 20, 8)]
+    sizes = [(23, 17, 11), (140, 9, 14), (16, 33, 25), (70, 20, 8)]
     mk = {"diffusion": lambda s, i: W.diffusion_blob(shape=s, seed=i),
           "brusselator": lambda s, i: W.brusselator(shape=s, seed=i),
           "ch_front": lambda s, i: W.ch_front(shape=s, seed=i),
           "air": lambda s, i: W.air(s, src=(1, 2, 3), seed=i)}[model]
     cfgs = [mk(s, i) for i, s in enumerate(sizes)]
     steps = 15
-    tun = dict(tsteps=1, tile_q=4, tile_y=4, zchunk=6, graph=1)
+    tun = dict(tsteps=1, tile_q=16, tile_y=4, zchunk=6, graph=1)
     ref = [run_gpu(rd, c, steps, tuning=tun) for c in cfgs]
     sims = [rd.Sim(c) for c in cfgs]
     for c, s in zip(cfgs, sims):
@@ -281,7 +282,7 @@ def test_oversized_tile_rejected(rd):
     from paper_1004_0480_gb300 import _lib as L
     with rd.Sim(W.ch_front(shape=(300, 300, 8))) as sim:
         with pytest.raises(L.RdError):
-            sim.set_tuning(tsteps=2, tile_q=64, tile_y=64)
+            sim.set_tuning(tsteps=2, tile_q=16, tile_y=64)
 
 
 def test_wait_times_out_without_harm(rd):
@@ -309,7 +310,7 @@ def test_brusselator_200_steps(rd, orc):
     cfg = W.brusselator(64, steps=200)
     f = W.initial_fields(cfg)
     ref = orc.run(cfg, f, 200)
-    for t in (dict(tsteps=1), dict(tsteps=2), dict(tsteps=3)):
+    for t in (dict(tsteps=1), dict(tsteps=2, tile_y=8), dict(tsteps=3, tile_y=4)):
         assert rel_err(run_gpu(rd, cfg, 200, tuning=t, fields=f), ref) <= TOL_NONLIN
 
 
@@ -317,7 +318,7 @@ def test_ch_front_200_steps(rd, orc):
     cfg = W.ch_front(48, steps=200)
     f = W.initial_fields(cfg)
     ref = orc.run(cfg, f, 200)
-    for t in (dict(tsteps=1), dict(tsteps=2)):
+    for t in (dict(tsteps=1, tile_y=8), dict(tsteps=2, tile_y=8)):
         assert rel_err(run_gpu(rd, cfg, 200, tuning=t, fields=f), ref) <= TOL_NONLIN
 
 
