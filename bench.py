@@ -235,8 +235,9 @@ def run_ours(args, ws, rank, local):
     sim = Sim(cfg, stream=stream)
     sim.set_fields(f)
     if args.tuning:
-        T_, ty_, zc_ = (int(x) for x in args.tuning.split(","))
-        sim.set_tuning(tsteps=T_, tile_y=ty_, zchunk=zc_)
+        vals = [int(x) for x in args.tuning.split(",")]
+        sim.set_tuning(tsteps=vals[0], tile_y=vals[1], zchunk=vals[2],
+                       regcap=vals[3] if len(vals) > 3 else 0)
         tun = sim.tuning()
     else:
         tun = sim.autotune()
@@ -435,7 +436,7 @@ def main():
     ap.add_argument("--job-steps", type=int, default=0,
                     help="time steps per job (default: the workload's 10 000)")
     ap.add_argument("--tuning", default="",
-                    help="fixed tuning 'tsteps,tile_y,zchunk' instead of the autotuner")
+                    help="fixed tuning 'tsteps,tile_y,zchunk[,regcap]' instead of the autotuner")
     ap.add_argument("--profile", type=int, default=0,
                     help="only run this many single step-kernel launches (for ncu)")
     args = ap.parse_args()

@@ -199,15 +199,19 @@ rd_status rd_set_step_count(rd_ctx* ctx, int64_t n);
  *           the Cahn-Hilliard model)
  *   tile_q  tile width in 4-cell vectors; this build fixes it at 16 (a tile
  *           is 64 cells wide)
- *   tile_y  tile height in rows, >= 1; the CTA has (tile_q + 2) x
- *           (tile_y + 2 L) threads (L = tsteps, 2 tsteps for Cahn-Hilliard),
- *           at most 512
+ *   tile_y  tile height in rows, >= 1 (even for tsteps = 1 without
+ *           Cahn-Hilliard, where the CTA is 16 tile_y compute threads plus
+ *           one halo warp); otherwise the CTA has (tile_q + 2) x
+ *           (tile_y + 2 L) threads (L = tsteps, 2 tsteps for Cahn-Hilliard);
+ *           at most 512 threads
  *   zchunk  z planes per work item, >= 1
  *   graph   1: replay rd_step launches from a captured CUDA graph
  * rd_set_tuning validates; RD_EINVAL if the CTA or its shared memory does
  * not fit one SM. */
 typedef struct rd_tuning {
-    int32_t tsteps, tile_q, tile_y, zchunk, graph, reserved;
+    int32_t tsteps, tile_q, tile_y, zchunk, graph;
+    int32_t regcap;   /* 1: cap the one-step kernel at 64 registers per thread
+                         (more resident warps), 0: let it use up to 128      */
 } rd_tuning;
 rd_status rd_get_tuning(const rd_ctx* ctx, rd_tuning* out);
 rd_status rd_set_tuning(rd_ctx* ctx, const rd_tuning* t);

@@ -38,11 +38,11 @@ class RdConfig(ctypes.Structure):
 class RdTuning(ctypes.Structure):
     _fields_ = [("tsteps", ctypes.c_int32), ("tile_q", ctypes.c_int32),
                 ("tile_y", ctypes.c_int32), ("zchunk", ctypes.c_int32),
-                ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("regcap", ctypes.c_int32)]
 
     def as_dict(self):
         return dict(tsteps=self.tsteps, tile_q=self.tile_q, tile_y=self.tile_y,
-                    zchunk=self.zchunk, graph=self.graph)
+                    zchunk=self.zchunk, graph=self.graph, regcap=self.regcap)
 
 
 _P = ctypes.c_void_p

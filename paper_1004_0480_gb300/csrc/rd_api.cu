@@ -81,7 +81,7 @@ size_t smem_of(int model, int storage, int T, int ty) {
 // CTA size of a step kernel: the one-step kernel has a thread per tile
 // vector; the multi-level kernel (tile vectors + 2 halo) x (rows + 2 L)
 int threads_of(int model, int T, int ty) {
-    if (T == 1 && model != RD_MODEL_CH_FRONT) return kTileQ * ty;
+    if (T == 1 && model != RD_MODEL_CH_FRONT) return kTileQ * ty + 32;
     const int L = (model == RD_MODEL_CH_FRONT ? 2 : 1) * T;
     return (kTileQ + 2) * (ty + 2 * L);
 }
@@ -100,17 +100,19 @@ cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int
 int max_tsteps(int model) { return model == RD_MODEL_CH_FRONT ? 2 : 3; }
 
 // CTAs per SM for a variant (cached).
-int occupancy(int model, int storage, int T, size_t smem, int threads) {
+int occupancy(int model, int storage, int T, size_t smem, int threads, int regcap = 0) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, size_t, int>, int> cache;
+    static std::map<std::tuple<int, int, int, size_t, int, int>, int> cache;
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_tuple(model, storage, T, smem, threads);
+    auto key = std::make_tuple(model, storage, T, smem, threads, regcap);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int occ = 0;
     LaunchArgs dummy{};
+    dummy.use_one = 1;
+    dummy.regcap = regcap;
     dummy.ty = (T == 1 && model != RD_MODEL_CH_FRONT)
-                   ? threads / kTileQ
+                   ? (threads - 32) / kTileQ
                    : threads / (kTileQ + 2) - 2 * (model == RD_MODEL_CH_FRONT ? 2 : 1) * T;
     if (launch_model(model, storage, T, dummy, 0, smem, nullptr, &occ) != cudaSuccess) occ = 0;
     cudaGetLastError();
@@ -326,6 +328,9 @@ rd_status check_tuning(const rd_config& g, const rd_tuning& t) {
     if (t.tile_q != kTileQ)
         return fail(nullptr, RD_EINVAL, "tile_q must be %d in this build", kTileQ);
     if (t.tile_y < 1 || t.zchunk < 1) return fail(nullptr, RD_EINVAL, "tile out of range");
+    if (t.regcap != 0 && t.regcap != 1) return fail(nullptr, RD_EINVAL, "regcap must be 0 or 1");
+    if (t.tsteps == 1 && g.model != RD_MODEL_CH_FRONT && (t.tile_y & 1))
+        return fail(nullptr, RD_EINVAL, "tile_y must be even for one step per launch");
     if (threads_of(g.model, t.tsteps, t.tile_y) > kMaxThreads)
         return fail(nullptr, RD_EINVAL, "tile_y %d too tall for %d steps per launch", t.tile_y,
                     t.tsteps);
@@ -395,6 +400,7 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
     d.src_amt = (float)(g.src_rate * g.dt);
     const int vec = c->vec;
     d.ntx = tiles(g.nx, t.tile_q * vec);
+    d.wrap_elems = d.per_x && (g.nx % 4 != 0);
     d.nty = tiles(g.ny, t.tile_y);
     d.zchunk = std::max(1, std::min(t.zchunk, g.nz));
     d.nzc = tiles(g.nz, d.zchunk);
@@ -444,9 +450,12 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     a.ninst = 1;
     a.parity = parity;
     a.nitems = items_of(c->desc);
+    a.use_one = 1;
+    a.one = c->desc;
+    a.regcap = c->tun.regcap;
     a.ty = c->tun.tile_y;
     const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty);
-    const int occ = std::max(1, occupancy(c->cfg.model, c->cfg.storage, T, sm, threads_of(c->cfg.model, T, a.ty)));
+    const int occ = std::max(1, occupancy(c->cfg.model, c->cfg.storage, T, sm, threads_of(c->cfg.model, T, a.ty), a.regcap));
     const long long grid = std::min<long long>(a.nitems, (long long)occ * num_sms());
     cudaError_t e = launch_model(c->cfg.model, c->cfg.storage, T, a, (int)grid, sm, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
@@ -456,7 +465,8 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
 
 long long ctx_graph_key(const rd_ctx* c) {
     const rd_tuning& t = c->tun;
-    return ((((long long)t.tsteps * 64 + t.tile_q) * 64 + t.tile_y) * 100000 + t.zchunk);
+    return (((((long long)t.tsteps * 64 + t.tile_q) * 64 + t.tile_y) * 100000 + t.zchunk) * 2 +
+            t.regcap);
 }
 
 constexpr int kGraphLaunches = 16;
@@ -557,8 +567,8 @@ void load_tune_file() {
         rd_tuning t{};
         if (std::sscanf(line,
                         " {\"key\": \"%255[^\"]\", \"tsteps\": %d, \"tile_q\": %d, \"tile_y\": %d, "
-                        "\"zchunk\": %d, \"graph\": %d",
-                        key, &t.tsteps, &t.tile_q, &t.tile_y, &t.zchunk, &t.graph) == 6)
+                        "\"zchunk\": %d, \"graph\": %d, \"regcap\": %d",
+                        key, &t.tsteps, &t.tile_q, &t.tile_y, &t.zchunk, &t.graph, &t.regcap) == 7)
             g_tune_cache[key] = t;
     }
     std::fclose(f);
@@ -571,8 +581,8 @@ void save_tune(const std::string& key, const rd_tuning& t, double gcups) {
     if (!f) return;
     std::fprintf(f,
                  "{\"key\": \"%s\", \"tsteps\": %d, \"tile_q\": %d, \"tile_y\": %d, \"zchunk\": %d, "
-                 "\"graph\": %d, \"gcups\": %.3f}\n",
-                 key.c_str(), t.tsteps, t.tile_q, t.tile_y, t.zchunk, t.graph, gcups);
+                 "\"graph\": %d, \"regcap\": %d, \"gcups\": %.3f}\n",
+                 key.c_str(), t.tsteps, t.tile_q, t.tile_y, t.zchunk, t.graph, t.regcap, gcups);
     std::fclose(f);
 }
 
@@ -800,19 +810,23 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
     std::vector<rd_tuning> cands;
     for (int T = 1; T <= max_tsteps(g.model); ++T)
         for (int ty : {4, 8, 12, 16, 20, 24, 32}) {
+          for (int rc = 0; rc <= ((T == 1 && g.model != RD_MODEL_CH_FRONT) ? 1 : 0); ++rc) {
             rd_tuning t{};
             t.tsteps = T; t.tile_q = kTileQ; t.tile_y = ty; t.graph = 1; t.zchunk = 1;
+            t.regcap = rc;
             if (check_tuning(g, t) != RD_OK) continue;
             const size_t sm = smem_of(g.model, g.storage, T, ty);
-            const int occ = occupancy(g.model, g.storage, T, sm, threads_of(g.model, T, ty));
+            const int occ = occupancy(g.model, g.storage, T, sm, threads_of(g.model, T, ty), rc);
             if (occ < 1) continue;
             for (int waves : {1, 2, 4, 8}) {
                 t.zchunk = auto_zchunk(g, t, occ, waves);
                 bool dup = false;
                 for (auto& o : cands)
-                    dup |= (o.tsteps == t.tsteps && o.tile_y == t.tile_y && o.zchunk == t.zchunk);
+                    dup |= (o.tsteps == t.tsteps && o.tile_y == t.tile_y && o.zchunk == t.zchunk &&
+                            o.regcap == t.regcap);
                 if (!dup) cands.push_back(t);
             }
+          }
         }
     cudaEvent_t e0, e1;
     RD_CUDA(c, cudaEventCreate(&e0));
@@ -837,8 +851,8 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
         cudaEventElapsedTime(&ms, e0, e1);
         const double rate = cells * t.tsteps * reps / (ms * 1e-3) / 1e9;
         if (std::getenv("RD_AUTOTUNE_VERBOSE"))
-            std::fprintf(stderr, "rd_autotune %s T=%d tile_y=%d zchunk=%d: %.2f GLUPS (%.4f ms/launch)\n",
-                         key.c_str(), t.tsteps, t.tile_y, t.zchunk, rate, ms / reps);
+            std::fprintf(stderr, "rd_autotune %s T=%d tile_y=%d zchunk=%d regcap=%d: %.2f GLUPS (%.4f ms/launch)\n",
+                         key.c_str(), t.tsteps, t.tile_y, t.zchunk, t.regcap, rate, ms / reps);
         if (rate > best) { best = rate; bt = t; }
     }
     cudaEventDestroy(e0);
@@ -995,9 +1009,10 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
     a.ninst = (int)b->members.size();
     a.parity = parity;
     a.nitems = nitems;
+    a.regcap = t.regcap;
     a.ty = t.tile_y;
     const size_t sm = smem_of(b->model, b->storage, T, a.ty);
-    const int occ = std::max(1, occupancy(b->model, b->storage, T, sm, threads_of(b->model, T, a.ty)));
+    const int occ = std::max(1, occupancy(b->model, b->storage, T, sm, threads_of(b->model, T, a.ty), a.regcap));
     const long long grid = std::min<long long>(nitems, (long long)occ * num_sms());
     cudaError_t e = launch_model(b->model, b->storage, T, a, (int)grid, sm, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch step launch");

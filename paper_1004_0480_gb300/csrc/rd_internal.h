@@ -31,15 +31,20 @@ struct InstDesc {
     int src_x, src_y, src_z, src_s;          // src_s < 0: no source
     float src_amt;             // emission per step: rate * dt
     int ntx, nty, nzc, zchunk; // work items: ntx * nty * nzc
+    int wrap_elems;            // periodic x with nx % 4 != 0: some halo
+                               // vectors straddle the wrap point
     long long item_begin;      // first global item index of this instance
 };
 
 struct LaunchArgs {
-    const InstDesc* desc;      // device array of ninst descriptors
+    const InstDesc* desc;      // device array of ninst descriptors (batches)
     int ninst;
     int parity;                // launch parity (0/1): level read = par ^ parity
     long long nitems;          // total work items over all instances
     int ty;                    // tile height in rows (width is kTileQ vectors)
+    int use_one;               // 1: a single instance, described by ``one``
+    int regcap;                // one-step kernel: 1 = at most 64 registers
+    InstDesc one;              // the instance of a single-instance launch
 };
 
 // Per-model launchers (one translation unit each).  With occ != nullptr

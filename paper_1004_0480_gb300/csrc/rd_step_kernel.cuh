@@ -62,6 +62,14 @@ template <> struct Store<float> {
         const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
     }
+    // copy only where ``pred`` holds (no branch)
+    __device__ __forceinline__ static void cp_async_if(float* smem, const float* g, int pred) {
+        const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n"
+                     " @p cp.async.cg.shared.global [%0], [%1], 16;\n}\n" ::"r"(s), "l"(g),
+                     "r"(pred)
+                     : "memory");
+    }
 };
 
 template <> struct Store<__nv_bfloat16> {
@@ -87,6 +95,14 @@ template <> struct Store<__nv_bfloat16> {
     __device__ __forceinline__ static void cp_async(__nv_bfloat16* smem, const __nv_bfloat16* g) {
         const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
+    }
+    __device__ __forceinline__ static void cp_async_if(__nv_bfloat16* smem,
+                                                       const __nv_bfloat16* g, int pred) {
+        const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n"
+                     " @p cp.async.ca.shared.global [%0], [%1], 8;\n}\n" ::"r"(s), "l"(g),
+                     "r"(pred)
+                     : "memory");
     }
 };
 
@@ -180,6 +196,15 @@ __device__ __forceinline__ float euler_cell(float c, float xm, float xp, float y
     return __fadd_rn(c, inc);
 }
 
+// Same for equal diffusivities on the three axes (k = D dt / h^2):
+// c + inc + k (sum of the 6 neighbours - 6 c).
+__device__ __forceinline__ float euler_cell_iso(float c, float xm, float xp, float ym, float yp,
+                                                float zm, float zp, float k, float inc) {
+    const float s6 = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
+    const float lap = __fmaf_rn(-6.0f, c, s6);
+    return __fadd_rn(c, __fmaf_rn(k, lap, inc));
+}
+
 // First-order upwind advection increment for Courant number cx = u dt / h.
 __device__ __forceinline__ float upwind(float inc, float cx, float c, float xm, float xp) {
     return cx >= 0.0f ? __fmaf_rn(-cx, __fsub_rn(c, xm), inc)
@@ -260,6 +285,35 @@ __device__ __forceinline__ void gather7(const E* Pc, const E* Pm, const E* Pp, c
     }
 }
 
+// The instance a work item belongs to: the launch's own descriptor (kernel
+// parameter space, read as constants) for single-instance launches, else a
+// shared-memory copy of the batch entry.
+template <bool ONE>
+__device__ __forceinline__ const InstDesc& desc_of(const LaunchArgs& a, const InstDesc& copy) {
+    if constexpr (ONE) return a.one;
+    else return copy;
+}
+
+// Fetch the descriptor of the instance owning ``item`` into ``copy`` (batch
+// launches); one barrier-separated pass per change of instance.
+__device__ __forceinline__ void load_desc(const LaunchArgs& a, long long item, InstDesc& copy,
+                                          int& s_inst, int& cur_inst) {
+    const int tid = threadIdx.x;
+    for (int i = tid; i < a.ninst; i += blockDim.x) {
+        const long long b0 = a.desc[i].item_begin;
+        const long long b1 = (i + 1 < a.ninst) ? a.desc[i + 1].item_begin : a.nitems;
+        if (item >= b0 && item < b1) s_inst = i;
+    }
+    __syncthreads();
+    if (s_inst != cur_inst) {
+        cur_inst = s_inst;
+        const int* src = reinterpret_cast<const int*>(a.desc + cur_inst);
+        int* dst = reinterpret_cast<int*>(&copy);
+        for (int i = tid; i < (int)(sizeof(InstDesc) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+}
+
 // Held (Dirichlet) layers: the first face in -x,+x,-y,+y,-z,+z wins.
 __device__ __forceinline__ void held_layers(const InstDesc& sd, int s, int xs, int y, int q,
                                             float (&o)[kVEC]) {
@@ -290,20 +344,35 @@ __device__ __forceinline__ void species_update(const InstDesc& sd, int s, const 
                                                const float (&inc)[kVEC], float cx, bool src_here,
                                                bool px, int xs, int y, int q, float (&o)[kVEC]) {
     const float kx = sd.kx[s], ky = sd.ky[s], kz = sd.kz[s];
+    const bool src_s = src_here && s == sd.src_s;
+    if (cx == 0.0f && !src_s) {
+        if (kx == ky && kx == kz) {
 #pragma unroll
-    for (int e = 0; e < kVEC; ++e) {
-        float in = inc[e];
-        if (src_here && s == sd.src_s && (px ? wrapi(xs + e, sd.nx) : xs + e) == sd.src_x)
-            in = __fadd_rn(in, sd.src_amt);
-        if (cx != 0.0f) in = upwind(in, cx, c[e], xm[e], xp[e]);
-        o[e] = euler_cell(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, ky, kz, in);
+            for (int e = 0; e < kVEC; ++e)
+                o[e] = euler_cell_iso(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, inc[e]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < kVEC; ++e)
+                o[e] = euler_cell(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, ky, kz, inc[e]);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < kVEC; ++e) {
+            float in = inc[e];
+            if (src_s && (px ? wrapi(xs + e, sd.nx) : xs + e) == sd.src_x)
+                in = __fadd_rn(in, sd.src_amt);
+            if (cx != 0.0f) in = upwind(in, cx, c[e], xm[e], xp[e]);
+            o[e] = (kx == ky && kx == kz)
+                       ? euler_cell_iso(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, in)
+                       : euler_cell(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, ky, kz, in);
+        }
     }
     held_layers(sd, s, xs, y, q, o);
 }
 
 // ------------------------------------------------------------------ kernel
-template <class M, class ST, int T>
-__global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const LaunchArgs a) {
+template <class M, class ST, int T, bool ONE>
+__global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const __grid_constant__ LaunchArgs a) {
     using LY = Layout<M, ST, T>;
     constexpr int S = M::S;
     constexpr bool CH = M::CH;
@@ -311,7 +380,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const LaunchArg
     constexpr int P = LY::P;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ InstDesc sd;
+    __shared__ InstDesc sdm;
     __shared__ int s_inst;
 
     const int tid = threadIdx.x;
@@ -335,22 +404,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const LaunchArg
     int cur_inst = -1;
     if (tid == 0) s_inst = 0;
     for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-        if (a.ninst > 1) {
-            for (int i = tid; i < a.ninst; i += blockDim.x) {
-                const long long b0 = a.desc[i].item_begin;
-                const long long b1 = (i + 1 < a.ninst) ? a.desc[i + 1].item_begin : a.nitems;
-                if (item >= b0 && item < b1) s_inst = i;
-            }
-        }
-        __syncthreads();
-        if (s_inst != cur_inst) {
-            cur_inst = s_inst;
-            const int* src = reinterpret_cast<const int*>(a.desc + cur_inst);
-            int* dst = reinterpret_cast<int*>(&sd);
-            for (int i = tid; i < (int)(sizeof(InstDesc) / sizeof(int)); i += blockDim.x)
-                dst[i] = src[i];
-        }
-        __syncthreads();
+        if constexpr (!ONE) load_desc(a, item, sdm, s_inst, cur_inst);
+        const InstDesc& sd = desc_of<ONE>(a, sdm);
 
         const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
         const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;
@@ -522,38 +577,41 @@ __global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const LaunchArg
 }
 
 // ------------------------------------------------------ one-step kernel
-// The T = 1 path of the models without Cahn-Hilliard: one thread per
-// 4-cell vector of a 64 x TY tile, no idle halo threads.  Threads on the
-// tile edge also fetch the halo vectors (one row above/below, one vector
-// left/right; the 7-point stencil needs no corners).  Planes arrive in an
-// 8-slot shared-memory ring.  While plane q is computed, planes q-1..q+1
-// are resident and q+2..q+6 are in flight (P = 7 copy groups ahead of q-1).
-// A thread reads its own vector in planes q-1, q, q+1 and its neighbours in
-// plane q; the slot refilled at step q held plane q-2, whose neighbour
-// reads ended two barriers earlier and whose own-vector reads precede the
-// refill in the thread's program order, so one barrier per plane suffices.
+// The T = 1 path of the models without Cahn-Hilliard.  16 x TY compute
+// threads, one per 4-cell vector of a 64 x TY tile, plus one halo warp that
+// fetches the tile's halo (one row above and below, one vector left and
+// right; the 7-point stencil needs no corners).  Planes arrive in a 6-slot
+// shared-memory ring: while plane q is computed, planes q-1..q+1 are
+// resident and q+2..q+4 in flight (P = 5 copy groups ahead of q-1).  A
+// compute thread reads its own vector in planes q-1, q, q+1 and its four
+// neighbours in plane q.  The slot refilled at step q held plane q-2: its
+// neighbour reads ended two barriers earlier and its own-vector reads
+// precede the refill in the owner's program order, so one barrier per plane
+// suffices.  The halo warp runs its own copy loop with the same barriers.
 template <class M, class ST> struct Layout1 {
     static constexpr int S = M::S;
-    static constexpr int RING = 8;
-    static constexpr int P = 7;
+    static constexpr int RING = 6;
+    static constexpr int P = 5;
     __host__ __device__ static int plane_elems(int ty) { return (ty + 2) * kRW + 2 * kVEC; }
     __host__ __device__ static size_t total(int ty) {
-        return (size_t)RING * S * plane_elems(ty) * sizeof(ST);
+        return (size_t)RING * S * plane_elems(ty) * sizeof(ST) + 96 * sizeof(int4);
     }
-    __host__ __device__ static int threads(int ty) { return kTileQ * ty; }
+    __host__ __device__ static int threads(int ty) { return kTileQ * ty + 32; }
 };
 
-// How a thread fetches one vector: 1 = one async copy, 2 = element by
-// element with wrapped x, 0 = nothing (outside a zero-flux face).
+// How one vector is fetched: 1 = one async copy, 2 = element by element
+// with wrapped x, 0 = nothing (outside a zero-flux face).
 struct Fetch {
     int mode;
     int goff;    // element offset of row + x within a plane
-    int soff;    // element offset of the position within a plane buffer
+    int soff;    // byte offset of the position within a plane buffer
+    int xs;      // global x of the vector's first element (unwrapped)
 };
 
+template <class ST>
 __device__ __forceinline__ Fetch make_fetch(int yrow, int xs, int nx, int ny, int pitch, bool px,
-                                            bool py, int soff) {
-    Fetch f{0, 0, soff};
+                                            bool py, int soff_elems) {
+    Fetch f{0, 0, soff_elems * (int)sizeof(ST), xs};
     if (!py && (yrow < 0 || yrow >= ny)) return f;
     const int yw = py ? wrapi(yrow, ny) : yrow;
     const int row = yw * pitch;
@@ -568,58 +626,70 @@ __device__ __forceinline__ Fetch make_fetch(int yrow, int xs, int nx, int ny, in
     return f;
 }
 
-template <class ST>
-__device__ __forceinline__ void fetch(const Fetch& f, ST* plane_buf, const ST* gplane, int xs,
-                                      int nx) {
-    if (f.mode == 1) {
-        Store<ST>::cp_async(plane_buf + f.soff, gplane + f.goff);
-    } else if (f.mode == 2) {
+// one fetch of every species of a plane; ``wrap`` is true only for periodic
+// x with nx not a multiple of 4, the one case where mode 2 occurs
+template <class ST, int S>
+__device__ __forceinline__ void fetch_all(const Fetch& f, unsigned char* plane_buf, int pe_bytes,
+                                          const ST* gplane, long long fstride, int nx,
+                                          bool wrap) {
 #pragma unroll
-        for (int e = 0; e < kVEC; ++e) plane_buf[f.soff + e] = gplane[f.goff + wrapi(xs + e, nx)];
+    for (int s = 0; s < S; ++s)
+        Store<ST>::cp_async_if(reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff),
+                               gplane + s * fstride + f.goff, f.mode == 1);
+    if (wrap && f.mode == 2) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            ST* d = reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff);
+#pragma unroll
+            for (int e = 0; e < kVEC; ++e) d[e] = gplane[s * fstride + f.goff + wrapi(f.xs + e, nx)];
+        }
     }
 }
 
-template <class M, class ST>
-__global__ void __launch_bounds__(kMaxThreads, 1) rd_step1_kernel(const LaunchArgs a) {
+template <class ST>
+__device__ __forceinline__ void lds_vec(const unsigned char* p, float (&v)[kVEC]) {
+    Store<ST>::load(reinterpret_cast<const ST*>(p), v);
+}
+template <class ST>
+__device__ __forceinline__ float lds_one(const unsigned char* p) {
+    return Store<ST>::get(reinterpret_cast<const ST*>(p));
+}
+
+template <class M, class ST, bool ONE, int MINB>
+__global__ void __launch_bounds__(kMaxThreads, MINB)
+rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
     using LY = Layout1<M, ST>;
     constexpr int S = M::S;
     constexpr int P = LY::P;
     constexpr int RING = LY::RING;
+    constexpr int EB = (int)sizeof(ST);
+    constexpr int RWB = kRW * EB;                            // bytes per shared row
 
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ InstDesc sd;
+    __shared__ InstDesc sdm;
     __shared__ int s_inst;
 
-    ST* const ring = reinterpret_cast<ST*>(smem) + kVEC;   // slot 0, species 0
     const int tid = threadIdx.x;
     const int TY = a.ty;
-    const int PE = LY::plane_elems(TY);
+    const int PEB = LY::plane_elems(TY) * EB;                // bytes per species plane
+    const int SLOTB = S * PEB;                               // bytes per ring slot
+    unsigned char* const ring = smem + kVEC * EB;            // slot 0, species 0
+    int4* const hfetch = reinterpret_cast<int4*>(smem + RING * SLOTB);
+    const int ncomp = kTileQ * TY;
+    const bool halo_warp = tid >= ncomp;
     const int r = tid / kTileQ;
     const int v = tid - r * kTileQ;
-    const int own = (r + 1) * kRW + (v + 1) * kVEC;
+    const int own_b = ((r + 1) * kRW + (v + 1) * kVEC) * EB;
 
     int cur_inst = -1;
     if (tid == 0) s_inst = 0;
     for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-        if (a.ninst > 1) {
-            for (int i = tid; i < a.ninst; i += blockDim.x) {
-                const long long b0 = a.desc[i].item_begin;
-                const long long b1 = (i + 1 < a.ninst) ? a.desc[i + 1].item_begin : a.nitems;
-                if (item >= b0 && item < b1) s_inst = i;
-            }
-        }
-        __syncthreads();
-        if (s_inst != cur_inst) {
-            cur_inst = s_inst;
-            const int* src = reinterpret_cast<const int*>(a.desc + cur_inst);
-            int* dst = reinterpret_cast<int*>(&sd);
-            for (int i = tid; i < (int)(sizeof(InstDesc) / sizeof(int)); i += blockDim.x)
-                dst[i] = src[i];
-        }
-        __syncthreads();
+        if constexpr (!ONE) load_desc(a, item, sdm, s_inst, cur_inst);
+        const InstDesc& sd = desc_of<ONE>(a, sdm);
 
         const int nx = sd.nx, ny = sd.ny, nz = sd.nz, pitch = sd.pitch;
         const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;
+        const bool wrap = sd.wrap_elems;
         const long long local = item - sd.item_begin;
         const int txi = (int)(local % sd.ntx);
         const int tyi = (int)((local / sd.ntx) % sd.nty);
@@ -628,57 +698,78 @@ __global__ void __launch_bounds__(kMaxThreads, 1) rd_step1_kernel(const LaunchAr
         const int z0 = zc * sd.zchunk;
         const int z1 = min(z0 + sd.zchunk, nz);
         const int lin = sd.par ^ a.parity;
+        const ST* const gin = reinterpret_cast<const ST*>(sd.base[lin][0]);
+        ST* const gout = reinterpret_cast<ST*>(sd.base[lin ^ 1][0]);
+        // the fields of one instance and time level are evenly spaced
+        const long long fstride = S > 1 ? reinterpret_cast<const ST*>(sd.base[lin][1]) - gin : 0;
+        const long long plane = sd.plane;
 
-        // ---- per-thread geometry
-        Pos ps;
-        ps.y = y0 + r;
-        ps.xs = x0 + v * kVEC;
-        ps.own = own;
-        ps.offm = (!py && ps.y == 0) ? own : own - kRW;
-        ps.offp = (!py && ps.y == ny - 1) ? own : own + kRW;
-        ps.offl = (!px && ps.xs == 0) ? own : own - 1;
-        ps.xhi = (!px && ps.xs <= nx - 1 && nx - 1 < ps.xs + kVEC) ? nx - 1 - ps.xs : -1;
-        const bool computes = ps.y < ny && ps.xs < nx;
-        const bool src_col = sd.src_s >= 0 && (py ? wrapi(ps.y, ny) : ps.y) == sd.src_y;
-        const long long st_off = (long long)ps.y * pitch + ps.xs;
-        // the thread's own vector, and the halo vectors it is responsible for
-        const Fetch f_own = make_fetch(ps.y, ps.xs, nx, ny, pitch, px, py, own);
-        Fetch f_y{0, 0, 0}, f_x{0, 0, 0};
-        if (r == 0) f_y = make_fetch(y0 - 1, ps.xs, nx, ny, pitch, px, py, own - kRW);
-        else if (r == TY - 1) f_y = make_fetch(y0 + TY, ps.xs, nx, ny, pitch, px, py, own + kRW);
-        const int xhalo = (v == 0) ? x0 - kVEC : x0 + kTileQ * kVEC;
-        if (v == 0 || v == kTileQ - 1) {
-            const int sh = (v == 0) ? own - kVEC : own + kVEC;
-            f_x = make_fetch(ps.y, xhalo, nx, ny, pitch, px, py, sh);
+        // ---- halo lanes: up to three halo vectors each, described in shared
+        // memory (2 TY side vectors, then 2 x 16 row vectors)
+        if (halo_warp) {
+            const int hl = tid - ncomp;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int j = hl + 32 * k;
+                Fetch f{0, 0, 0, 0};
+                if (j < 2 * TY) {
+                    const int hr = j >> 1;
+                    const bool right = j & 1;
+                    const int xh = right ? x0 + kTileQ * kVEC : x0 - kVEC;
+                    f = make_fetch<ST>(y0 + hr, xh, nx, ny, pitch, px, py,
+                                       (hr + 1) * kRW + (right ? kNQ - 1 : 0) * kVEC);
+                } else if (j < 2 * TY + 2 * kTileQ) {
+                    const int jj = j - 2 * TY;
+                    const bool bottom = jj >= kTileQ;
+                    const int hv = jj - (bottom ? kTileQ : 0);
+                    f = make_fetch<ST>(bottom ? y0 + TY : y0 - 1, x0 + hv * kVEC, nx, ny, pitch, px,
+                                       py, (bottom ? TY + 1 : 0) * kRW + (hv + 1) * kVEC);
+                }
+                hfetch[j] = make_int4(f.mode, f.goff, f.soff, f.xs);
+            }
         }
-        // the y-halo rows of the last tile row may lie past ny: then they
-        // belong to no thread's own load, as intended
+        // ---- compute threads: own vector and its neighbours
+        const int y = y0 + r;
+        const int xs = x0 + v * kVEC;
+        const int offm_b = (!py && y == 0) ? own_b : own_b - RWB;
+        const int offp_b = (!py && y == ny - 1) ? own_b : own_b + RWB;
+        const int offl_b = (!px && xs == 0) ? own_b : own_b - EB;
+        const int offr_b = own_b + kVEC * EB;
+        const int xhi = (!px && xs <= nx - 1 && nx - 1 < xs + kVEC) ? nx - 1 - xs : -1;
+        const bool computes = !halo_warp && y < ny && xs < nx;
+        const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
+        const Fetch fo = halo_warp ? Fetch{0, 0, 0, 0}
+                                   : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB);
+        __syncthreads();   // halo descriptors written
 
-        // ---- the march: plane nld is fetched P planes ahead of plane p
-        int nld = z0 - 1;
+        // ---- the march: plane nld (ring slot sld) is fetched P planes ahead
+        int nld = z0 - 1, sld = 0;
         int zld = pz ? wrapi(nld, nz) : nld;
+        const ST* gld = gin + (long long)zld * plane;
         auto issue = [&]() {
             if (nld <= z1 && (pz || (nld >= 0 && nld < nz))) {
-                const long long zoff = (long long)zld * sd.plane;
-                ST* buf = ring + (size_t)(nld & (RING - 1)) * S * PE;
+                unsigned char* buf = ring + sld * SLOTB;
+                if (halo_warp) {
+                    const int hl = tid - ncomp;
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    const ST* g = reinterpret_cast<const ST*>(sd.base[lin][s]) + zoff;
-                    ST* b = buf + (size_t)s * PE;
-                    fetch(f_own, b, g, ps.xs, nx);
-                    fetch(f_y, b, g, ps.xs, nx);
-                    fetch(f_x, b, g, xhalo, nx);
+                    for (int k = 0; k < 3; ++k) {
+                        const int4 h = hfetch[hl + 32 * k];
+                        fetch_all<ST, S>(Fetch{h.x, h.y, h.z, h.w}, buf, PEB, gld, fstride, nx, wrap);
+                    }
+                } else {
+                    fetch_all<ST, S>(fo, buf, PEB, gld, fstride, nx, wrap);
                 }
             }
             ++nld;
-            if (!pz) zld = nld;
-            else if (++zld == nz) zld = 0;
+            sld = (sld == RING - 1) ? 0 : sld + 1;
+            if (pz && ++zld == nz) { zld = 0; gld = gin; } else { gld += plane; }
             cp_async_commit();
         };
-
 #pragma unroll 1
         for (int j = 0; j < P; ++j) issue();
-        int zq = pz ? wrapi(z0, nz) : z0;     // wrapped index of plane q
+        int zq = pz ? wrapi(z0, nz) : z0;       // wrapped index of plane q
+        int sc = 1;                             // ring slot of plane q (z0 - 1 is slot 0)
+        ST* gst = gout + (long long)z0 * plane + (long long)y * pitch + xs;
         const float* courant = sd.courant;
 #pragma unroll 1
         for (int q = z0; q < z1; ++q) {
@@ -687,40 +778,49 @@ __global__ void __launch_bounds__(kMaxThreads, 1) rd_step1_kernel(const LaunchAr
             issue();
             cp_async_wait<P - 2>();
             __syncthreads();
-            if (computes) {
-                const int qm = (!pz && q == 0) ? q : q - 1;
-                const int qp = (!pz && q == nz - 1) ? q : q + 1;
-                const ST* Pc = ring + (size_t)(q & (RING - 1)) * S * PE;
-                const ST* Pm = ring + (size_t)(qm & (RING - 1)) * S * PE;
-                const ST* Pp = ring + (size_t)(qp & (RING - 1)) * S * PE;
-                float inc[S][kVEC];
-                {
-                    float cen[S][kVEC];
+            if (!halo_warp) {
+                const int sm = (!pz && q == 0) ? sc : (sc == 0 ? RING - 1 : sc - 1);
+                const int sp = (!pz && q == nz - 1) ? sc : (sc == RING - 1 ? 0 : sc + 1);
+                const unsigned char* Pc = ring + sc * SLOTB;
+                const unsigned char* Pm = ring + sm * SLOTB;
+                const unsigned char* Pp = ring + sp * SLOTB;
+                float cen[S][kVEC], inc[S][kVEC];
 #pragma unroll
-                    for (int s = 0; s < S; ++s) Store<ST>::load(Pc + (size_t)s * PE + own, cen[s]);
+                for (int s = 0; s < S; ++s) lds_vec<ST>(Pc + s * PEB + own_b, cen[s]);
 #pragma unroll
-                    for (int e = 0; e < kVEC; ++e) {
-                        float cv[S], iv[S];
+                for (int e = 0; e < kVEC; ++e) {
+                    float cv[S], iv[S];
 #pragma unroll
-                        for (int s = 0; s < S; ++s) cv[s] = cen[s][e];
-                        M::react(sd, cv, iv);
+                    for (int s = 0; s < S; ++s) cv[s] = cen[s][e];
+                    M::react(sd, cv, iv);
 #pragma unroll
-                        for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
-                    }
+                    for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
                 }
                 const float cx = courant ? courant[zq] : 0.0f;
                 const bool src_here = src_col && zq == sd.src_z;
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
-                    float c[kVEC], xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], o[kVEC];
-                    gather7<ST>(Pc + (size_t)s * PE, Pm + (size_t)s * PE, Pp + (size_t)s * PE, ps, c,
-                                xm, xp, ym, yp, zm, zp);
-                    species_update(sd, s, c, xm, xp, ym, yp, zm, zp, inc[s], cx, src_here, px,
-                                   ps.xs, ps.y, q, o);
-                    ST* g = reinterpret_cast<ST*>(sd.base[lin ^ 1][s]);
-                    Store<ST>::store(g + (long long)q * sd.plane + st_off, o);
+                    const unsigned char* Ps = Pc + s * PEB;
+                    float xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], o[kVEC];
+                    lds_vec<ST>(Pm + s * PEB + own_b, zm);
+                    lds_vec<ST>(Pp + s * PEB + own_b, zp);
+                    lds_vec<ST>(Ps + offm_b, ym);
+                    lds_vec<ST>(Ps + offp_b, yp);
+                    const float left = lds_one<ST>(Ps + offl_b);
+                    const float right = lds_one<ST>(Ps + offr_b);
+#pragma unroll
+                    for (int e = 0; e < kVEC; ++e) {
+                        xm[e] = e ? cen[s][e - 1] : left;
+                        xp[e] = (e < kVEC - 1) ? cen[s][e + 1] : right;
+                        xp[e] = (e == xhi) ? cen[s][e] : xp[e];   // zero-flux +x face
+                    }
+                    species_update(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s], cx, src_here, px,
+                                   xs, y, q, o);
+                    if (computes) Store<ST>::store(gst + s * fstride, o);
                 }
             }
+            gst += plane;
+            sc = (sc == RING - 1) ? 0 : sc + 1;
             if (!pz) zq = q + 1;
             else if (++zq == nz) zq = 0;
         }
@@ -730,18 +830,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1) rd_step1_kernel(const LaunchAr
 }
 
 // Launch helper used by the per-model translation units.
-template <class M, class ST, int T>
+template <class M, class ST, int T, bool ONE>
 cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t st, int* occ) {
     constexpr bool lean = (T == 1 && !M::CH);
     void (*k)(const LaunchArgs);
-    if constexpr (lean) k = rd_step1_kernel<M, ST>;
-    else k = rd_step_kernel<M, ST, T>;
-    static size_t configured = 0;
-    if (smem > configured) {
+    if constexpr (lean) {
+        // register budget of the one-step kernel: 128 (regcap 0) or 64 (regcap 1)
+        k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2> : rd_step1_kernel<M, ST, ONE, 1>;
+    } else {
+        k = rd_step_kernel<M, ST, T, ONE>;
+    }
+    static size_t configured[2] = {0, 0};
+    size_t& conf = configured[lean && a.regcap ? 1 : 0];
+    if (smem > conf) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
+        conf = smem;
     }
     const int threads = lean ? Layout1<M, ST>::threads(a.ty) : Layout<M, ST, T>::threads(a.ty);
     if (threads > kMaxThreads) return cudaErrorInvalidConfiguration;
@@ -750,27 +855,35 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <class M>
-cudaError_t launch_model(int storage, int tsteps, const LaunchArgs& a, int grid, size_t smem,
-                         cudaStream_t st, int* occ) {
+template <class M, bool ONE>
+cudaError_t launch_var(int storage, int tsteps, const LaunchArgs& a, int grid, size_t smem,
+                       cudaStream_t st, int* occ) {
     if (storage == RD_STORE_F32) {
         switch (tsteps) {
-        case 1: return launch_one<M, float, 1>(a, grid, smem, st, occ);
-        case 2: return launch_one<M, float, 2>(a, grid, smem, st, occ);
-        case 3: if constexpr (!M::CH) return launch_one<M, float, 3>(a, grid, smem, st, occ);
+        case 1: return launch_one<M, float, 1, ONE>(a, grid, smem, st, occ);
+        case 2: return launch_one<M, float, 2, ONE>(a, grid, smem, st, occ);
+        case 3: if constexpr (!M::CH) return launch_one<M, float, 3, ONE>(a, grid, smem, st, occ);
                 break;
         default: break;
         }
     } else {
         switch (tsteps) {
-        case 1: return launch_one<M, __nv_bfloat16, 1>(a, grid, smem, st, occ);
-        case 2: return launch_one<M, __nv_bfloat16, 2>(a, grid, smem, st, occ);
-        case 3: if constexpr (!M::CH) return launch_one<M, __nv_bfloat16, 3>(a, grid, smem, st, occ);
-                break;
+        case 1: return launch_one<M, __nv_bfloat16, 1, ONE>(a, grid, smem, st, occ);
+        case 2: return launch_one<M, __nv_bfloat16, 2, ONE>(a, grid, smem, st, occ);
+        case 3:
+            if constexpr (!M::CH) return launch_one<M, __nv_bfloat16, 3, ONE>(a, grid, smem, st, occ);
+            break;
         default: break;
         }
     }
     return cudaErrorInvalidValue;
+}
+
+template <class M>
+cudaError_t launch_model(int storage, int tsteps, const LaunchArgs& a, int grid, size_t smem,
+                         cudaStream_t st, int* occ) {
+    return a.use_one ? launch_var<M, true>(storage, tsteps, a, grid, smem, st, occ)
+                     : launch_var<M, false>(storage, tsteps, a, grid, smem, st, occ);
 }
 
 template <class M>

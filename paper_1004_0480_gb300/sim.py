@@ -189,7 +189,7 @@ class Sim:
         cur = self.tuning()
         cur.update(kw)
         t = L.RdTuning(cur["tsteps"], cur["tile_q"], cur["tile_y"], cur["zchunk"],
-                       cur["graph"], 0)
+                       cur["graph"], cur.get("regcap", 0))
         self._check(self.lib.rd_set_tuning(self.ctx, ctypes.byref(t)), "rd_set_tuning")
 
     def autotune(self):
@@ -240,8 +240,8 @@ class Batch:
         L.check(self.lib.rd_batch_remove(self.b, sim.ctx), sim.ctx, "rd_batch_remove")
         self.members.remove(sim)
 
-    def set_tuning(self, tsteps=1, tile_q=16, tile_y=8, zchunk=32, graph=1):
-        t = L.RdTuning(tsteps, tile_q, tile_y, zchunk, graph, 0)
+    def set_tuning(self, tsteps=1, tile_q=16, tile_y=8, zchunk=32, graph=1, regcap=0):
+        t = L.RdTuning(tsteps, tile_q, tile_y, zchunk, graph, regcap)
         L.check(self.lib.rd_batch_set_tuning(self.b, ctypes.byref(t)), None,
                 "rd_batch_set_tuning")
 
