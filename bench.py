@@ -87,7 +87,7 @@ def kernel_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(tsteps, tile_q, tile_y):
+def profiled_traffic(tsteps, tile_q, tile_y, regcap=0):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source and the same tuning; else None."""
     try:
@@ -102,8 +102,8 @@ def profiled_traffic(tsteps, tile_q, tile_y):
     try:
         if fields.get("kernel_sha") != kernel_sha():
             return None
-        if (int(fields["tsteps"]), int(fields["tile_q"]), int(fields["tile_y"])) != \
-                (tsteps, tile_q, tile_y):
+        if (int(fields["tsteps"]), int(fields["tile_q"]), int(fields["tile_y"]),
+                int(fields.get("regcap", 0))) != (tsteps, tile_q, tile_y, regcap):
             return None
         return float(fields["dram_bytes_per_launch"])
     except (KeyError, ValueError):
@@ -302,9 +302,10 @@ def run_ours(args, ws, rank, local):
     peak, peak_src = measured_peak()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": profiled_traffic(T, tun["tile_q"], tun["tile_y"]),
+                "traffic": profiled_traffic(T, tun["tile_q"], tun["tile_y"], tun.get("regcap", 0)),
                 "peak_source": peak_src,
-                "kernel": f"rd_step_kernel<MBrusselator,float,{T}>",
+                "kernel": ("rd_step1_kernel<MBrusselator,float>" if T == 1
+                           else f"rd_step_kernel<MBrusselator,float,{T}>"),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "launch_ms": per_launch_ms,
                 "compulsory_frac": (16.0 * cells) / (per_launch_ms * 1e-3) / 1e9 / peak}
