@@ -150,7 +150,12 @@ rd_status rd_create(const rd_config* cfg, rd_ctx** out);
 /* Attach caller-owned device memory (RD_FLAG_NO_ALLOC contexts only):
  * ``state`` of state_bytes and ``scratch`` of scratch_bytes as reported by
  * rd_query_sizes, both 256-byte aligned.  The caller keeps ownership and
- * must keep both alive until rd_destroy. */
+ * must keep both alive until rd_destroy.
+ * State layout: species s of time level l starts at byte
+ * (l * nspecies + s) * (state_bytes / (2 * nspecies)); each field is nz
+ * planes of ny rows of ``pitch`` elements (float32 or bfloat16), pitch = nx
+ * rounded up to a multiple of 128 bytes, x fastest.  Level 0 is current
+ * after rd_set_field and after every even number of kernel launches. */
 rd_status rd_attach(rd_ctx* ctx, void* state, void* scratch);
 
 /* Free what the context owns (device memory, stream, graphs). */
@@ -229,6 +234,29 @@ int64_t rd_launch_count(const rd_ctx* ctx);
 /* Text of a status code, and of the last error seen by a context. */
 const char* rd_status_str(rd_status st);
 const char* rd_last_error(const rd_ctx* ctx);
+
+/* FP64 moments of one field held anywhere in device memory, for callers
+ * that must not allocate device memory at that point: code that is
+ * capturing a CUDA graph (cudaMalloc / cudaFree are not allowed during a
+ * stream capture), serving loops held to a memory budget fixed at start-up,
+ * and monitors that must not trigger the device-wide synchronisation that
+ * cudaMalloc / cudaFree can cause.  The paper has no counterpart; it is the
+ * reduction of rd_mass without a context.
+ *   field    device pointer to nz planes of ny rows of ``pitch`` elements of
+ *            the given storage kind (RD_STORE_F32 / RD_STORE_BF16), x fastest
+ *   out      device pointer to 3 doubles: sum, sum of squares, count of
+ *            non-finite values (same fixed-order FP64 sums as rd_mass)
+ *   stream   cudaStream_t to run on (NULL = legacy default stream)
+ * Limits: nx, ny, nz >= 1, nx <= pitch <= 2^31 - 1, ny * nz <= 2^31 - 1;
+ * RD_EINVAL beyond them.  Asynchronous; allocates nothing.  The partial
+ * sums live in one file-scope device array of 608 x 3 doubles (14,592
+ * bytes) that every GPU loading this library keeps until the process exits.
+ * The first call on a device looks up that array's address (with the device
+ * current), so make a first call before any stream capture.  Calls share
+ * the array: two calls that overlap on the GPU (unordered streams) race and
+ * may return wrong sums. */
+rd_status rd_moments_noalloc(const void* field, int32_t storage, int32_t nx, int32_t ny,
+                             int32_t nz, int64_t pitch, double* out, void* stream);
 
 /*
  * Batches: many independent instances (contexts) of the same model and

@@ -87,6 +87,7 @@ SIGNATURES = {
     "rd_batch_sync": (_I, [_P]),
     "rd_batch_destroy": (_I, [_P]),
     "rd_batch_launch_count": (_I64, [_P]),
+    "rd_moments_noalloc": (_I, [_P, _I32, _I32, _I32, _I32, _I64, _P, _P]),
 }
 
 _lib = None
