@@ -9,7 +9,8 @@ replay).  Metric: GLUPS = cells x time steps / s / 1e9 (the paper's
 Mpoints/s, scaled), aggregated over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--no-extras] [--serve]
+                  [--no-extras]
+  python bench.py --serve [--serve-requests 500]      (serving workload)
 
 Under torchrun each rank runs its own replica of the job (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
@@ -424,6 +425,63 @@ def run_extras(args, Sim, Batch, torch):
     return out
 
 
+def run_serving(args):
+    """Serving workload: seeded Poisson stream of mixed requests, served by
+    continuous batching and by the plain one-request-at-a-time stepper."""
+    import torch
+
+    from paper_1004_0480_gb300 import build as B
+    B.build()
+    from paper_1004_0480_gb300 import serving as SV
+
+    torch.cuda.set_device(0)
+    specs = W.serving_requests(count=args.serve_requests, rate_per_s=1.0, seed=4)
+    reqs = SV.requests_from_workload(specs)
+    mean_work = float(np.mean([r.cells * r.steps for r in reqs]))
+    # calibrate the plain stepper's capacity on a few requests of the mix
+    probe = reqs[: max(3, min(8, len(reqs)))]
+    eng = SV.CudaEngine()
+    t0 = time.perf_counter()
+    for r in probe:
+        eng.run_alone(r, False)
+    torch.cuda.synchronize()
+    cap = sum(r.cells * r.steps for r in probe) / (time.perf_counter() - t0)
+    rate = args.serve_load * cap / mean_work
+    reqs = SV.with_rate(reqs, rate, seed=4)
+    server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
+                       quantum=args.serve_quantum)
+    res_b, st_b = server.run(reqs)
+    server.engine.shutdown()
+    res_p, st_p = SV.serve_plain(SV.CudaEngine(), reqs)
+    # capacity: the first requests of the stream all arriving at once
+    sat = [SV.Request(r.id, 0.0, r.cfg) for r in reqs[: args.serve_sat_requests]]
+    server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
+                       quantum=args.serve_quantum)
+    _, sat_b = server.run(sat)
+    server.engine.shutdown()
+    _, sat_p = SV.serve_plain(SV.CudaEngine(), sat)
+
+    def pack(st):
+        return {"p50_s": st.p50, "p99_s": st.p99, "mean_s": st.mean, "glups": st.glups,
+                "makespan_s": st.makespan, "max_active": st.max_active,
+                "max_device_bytes": st.max_bytes, "gpu_launches": st.launches}
+    line = {
+        "metric": "serving latency p50/p99 (s) and aggregate GLUPS", "unit": "s",
+        "requests": len(reqs), "arrival_rate_per_s": rate, "offered_load": args.serve_load,
+        "plain_capacity_glups": cap / 1e9, "budget_gb": args.serve_budget_gb,
+        "quantum_steps": args.serve_quantum, "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals, diffusion/brusselator/ch_front "
+                               "kinetics, edges {32..384}^3, 100..5000 steps", "seed": 4},
+        "continuous_batching": pack(st_b), "plain": pack(st_p),
+        "p99_speedup": st_p.p99 / st_b.p99 if st_b.p99 > 0 else None,
+        "saturated": {"requests": len(sat), "continuous_batching": pack(sat_b),
+                      "plain": pack(sat_p),
+                      "glups_speedup": sat_b.glups / sat_p.glups if sat_p.glups > 0 else None},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -440,8 +498,19 @@ def main():
                     help="fixed tuning 'tsteps,tile_y,zchunk[,regcap]' instead of the autotuner")
     ap.add_argument("--profile", type=int, default=0,
                     help="only run this many single step-kernel launches (for ncu)")
+    ap.add_argument("--serve", action="store_true",
+                    help="run the serving workload instead of the step benchmark")
+    ap.add_argument("--serve-requests", type=int, default=500)
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="offered load as a fraction of the plain stepper's capacity")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-quantum", type=int, default=250)
+    ap.add_argument("--serve-sat-requests", type=int, default=100,
+                    help="requests of the saturated (all arrive at once) capacity run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.serve:
+        return run_serving(args)
     ws, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         rc = reference_arm(args, ws, rank)

@@ -1,0 +1,296 @@
+"""Continuous-batching server for reaction-diffusion requests.
+
+Requests (a problem, an arrival time, a step count) arrive over time.  The
+server admits them in arrival order as soon as their device memory fits a
+budget, keeps their state resident, and advances all admitted requests of
+one kinetics family together with one batched launch sequence per tick
+(``rd_batch_step``), each family on its own stream so the families' kernels
+overlap on the device.  A request is retired the moment its step count is
+reached; its memory is freed and the next arrivals can be admitted.  Reports
+per-request latency (finish - arrival), p50/p99 and aggregate GLUPS.
+
+``serve_plain`` is the baseline: one request at a time in arrival order,
+each stepped alone by the plain stepper (the fused kernel at one step per
+launch, no graph).
+
+The scheduling logic talks to an engine object, so it can run on the CPU
+with a fake engine and a fake clock (see the tests); ``CudaEngine`` is the
+real one, on the C ABI.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import workloads as W
+
+
+@dataclass
+class Request:
+    id: int
+    arrival: float          # seconds after the start of the run
+    cfg: dict               # problem (workloads format); cfg["steps"] steps
+
+    @property
+    def steps(self):
+        return int(self.cfg["steps"])
+
+    @property
+    def family(self):
+        return self.cfg["model"]
+
+    @property
+    def cells(self):
+        return W.cell_count(self.cfg)
+
+
+@dataclass
+class Result:
+    id: int
+    arrival: float
+    admitted: float
+    finished: float
+    steps: int
+    cells: int
+    fields: np.ndarray | None = None
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+
+@dataclass
+class Stats:
+    n: int
+    makespan: float
+    glups: float
+    p50: float
+    p99: float
+    mean: float
+    max_bytes: int
+    max_active: int
+    launches: int = 0
+    extra: dict = field(default_factory=dict)
+
+
+def percentile(xs, q):
+    """q-th percentile (0..100) with linear interpolation."""
+    if not xs:
+        return float("nan")
+    xs = sorted(xs)
+    k = (len(xs) - 1) * q / 100.0
+    lo = math.floor(k)
+    hi = min(lo + 1, len(xs) - 1)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def summarize(results, makespan, max_bytes, max_active, launches=0):
+    lat = [r.latency for r in results]
+    work = sum(r.cells * r.steps for r in results)
+    return Stats(n=len(results), makespan=makespan,
+                 glups=work / makespan / 1e9 if makespan > 0 else float("nan"),
+                 p50=percentile(lat, 50), p99=percentile(lat, 99),
+                 mean=float(np.mean(lat)) if lat else float("nan"),
+                 max_bytes=max_bytes, max_active=max_active, launches=launches)
+
+
+# --------------------------------------------------------------- engines
+class CudaEngine:
+    """Requests as contexts of the CUDA library; one batch per family."""
+
+    def __init__(self, storage="f32", batch_tuning=None):
+        import torch
+
+        from .sim import Batch, Sim, query_sizes
+        self._torch = torch
+        self._Sim = Sim
+        self._Batch = Batch
+        self._query = query_sizes
+        self.storage = storage
+        self.batch_tuning = batch_tuning or {}
+        self.batches = {}
+        self.streams = {}
+
+    def bytes_for(self, req):
+        st, sc = self._query(req.cfg, self.storage)
+        return st + sc
+
+    def _new_sim(self, req):
+        # torch-owned memory: retiring a request returns it to torch's cache
+        # instead of a device-synchronising cudaFree
+        sim = self._Sim(req.cfg, self.storage, torch_memory=True)
+        f = W.initial_fields_torch(req.cfg, "cuda")
+        sim.set_fields(f)
+        del f
+        return sim
+
+    def open(self, req):
+        sim = self._new_sim(req)
+        fam = req.family
+        if fam not in self.batches:
+            s = self._torch.cuda.Stream()
+            b = self._Batch(fam, self.storage, stream=s)
+            tun = self.batch_tuning.get(fam)
+            if tun:
+                b.set_tuning(**tun)
+            self.batches[fam] = b
+            self.streams[fam] = s
+        self.batches[fam].add(sim)
+        return sim
+
+    def step(self, family, n):
+        self.batches[family].step(n)
+
+    def sync(self, family=None):
+        fams = [family] if family else list(self.batches)
+        for f in fams:
+            self.batches[f].sync()
+
+    def result(self, handle):
+        return handle.get_fields()
+
+    def close(self, family, handle):
+        self.batches[family].remove(handle)
+        handle.close()
+
+    def launches(self):
+        return sum(b.launches for b in self.batches.values())
+
+    def shutdown(self):
+        for b in self.batches.values():
+            b.close()
+        self.batches.clear()
+
+    # plain stepper: one request alone, one launch per step, no graph
+    def run_alone(self, req, collect):
+        sim = self._new_sim(req)
+        sim.set_tuning(tsteps=1, graph=0)
+        sim.step(req.steps)
+        sim.sync()
+        out = sim.get_fields() if collect else None
+        launches = sim.launches
+        sim.close()
+        return out, launches
+
+
+# ---------------------------------------------------------------- server
+class Server:
+    """Continuous batching under a device-memory budget.
+
+    ``quantum``  steps per tick for a family batch (a tick never steps a
+                 request past its count: the batch advances by the smallest
+                 remaining count if that is smaller)
+    ``budget``   bytes of device memory the admitted requests may hold
+    ``clock``    seconds (monotonic); ``sleep`` waits for the next arrival
+    """
+
+    def __init__(self, engine, budget_bytes=120e9, quantum=200, clock=time.perf_counter,
+                 sleep=time.sleep):
+        self.engine = engine
+        self.budget = float(budget_bytes)
+        self.quantum = int(quantum)
+        self.clock = clock
+        self.sleep = sleep
+
+    def run(self, requests, collect_fields=False):
+        pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.id)))
+        for r in pending:
+            if self.engine.bytes_for(r) > self.budget:
+                raise ValueError(f"request {r.id} alone exceeds the memory budget")
+        active = collections.OrderedDict()       # family -> list of slots
+        results = []
+        used = 0
+        max_used = 0
+        max_active = 0
+        t0 = self.clock()
+        while pending or any(active.values()):
+            now = self.clock() - t0
+            # ---- admit arrivals, first come first served, while memory allows
+            while pending and pending[0].arrival <= now:
+                req = pending[0]
+                need = self.engine.bytes_for(req)
+                if used + need > self.budget:
+                    break
+                pending.popleft()
+                handle = self.engine.open(req)
+                used += need
+                max_used = max(max_used, used)
+                active.setdefault(req.family, []).append(
+                    dict(req=req, handle=handle, left=req.steps, bytes=need,
+                         admitted=self.clock() - t0))
+            n_active = sum(len(v) for v in active.values())
+            max_active = max(max_active, n_active)
+            if n_active == 0:
+                if pending:
+                    wait = pending[0].arrival - (self.clock() - t0)
+                    if wait > 0:
+                        self.sleep(wait)
+                continue
+            # ---- one tick: every family batch advances (asynchronously)
+            stepped = []
+            for fam, slots in active.items():
+                if not slots:
+                    continue
+                n = min(self.quantum, min(s["left"] for s in slots))
+                self.engine.step(fam, n)
+                for s in slots:
+                    s["left"] -= n
+                stepped.append(fam)
+            # ---- end of tick: wait for the device (the host admits the next
+            # arrivals between ticks), then retire what is done
+            self.engine.sync()
+            finished = self.clock() - t0
+            for fam in stepped:
+                slots = active[fam]
+                done = [s for s in slots if s["left"] == 0]
+                if not done:
+                    continue
+                for s in done:
+                    req = s["req"]
+                    fields = self.engine.result(s["handle"]) if collect_fields else None
+                    results.append(Result(req.id, req.arrival, s["admitted"], finished, req.steps,
+                                          req.cells, fields))
+                    self.engine.close(fam, s["handle"])
+                    used -= s["bytes"]
+                    slots.remove(s)
+        self.engine.sync()
+        makespan = self.clock() - t0
+        launches = self.engine.launches()
+        return results, summarize(results, makespan, max_used, max_active, launches)
+
+
+def serve_plain(engine, requests, collect_fields=False, clock=time.perf_counter,
+                sleep=time.sleep):
+    """Baseline: requests one at a time in arrival order, each alone."""
+    order = sorted(requests, key=lambda r: (r.arrival, r.id))
+    results = []
+    launches = 0
+    t0 = clock()
+    for req in order:
+        now = clock() - t0
+        if req.arrival > now:
+            sleep(req.arrival - now)
+        admitted = clock() - t0
+        fields, nl = engine.run_alone(req, collect_fields)
+        launches += nl
+        results.append(Result(req.id, req.arrival, admitted, clock() - t0, req.steps, req.cells,
+                               fields))
+    makespan = clock() - t0
+    return results, summarize(results, makespan, 0, 1, launches)
+
+
+def requests_from_workload(specs):
+    """Request objects from ``workloads.serving_requests`` entries."""
+    return [Request(s["id"], s["arrival"], s["cfg"]) for s in specs]
+
+
+def with_rate(requests, rate_per_s, seed=4):
+    """The same requests with Poisson arrivals of the given rate."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_per_s, size=len(requests))
+    t = np.cumsum(gaps) - gaps[0]
+    return [Request(r.id, float(t[i]), r.cfg) for i, r in enumerate(requests)]

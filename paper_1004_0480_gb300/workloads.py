@@ -260,3 +260,71 @@ def state_bytes(cfg, bytes_per_value=4):
 def serving_mean_cells(edges=SERVE_EDGES):
     return float(np.mean([e ** 3 for e in edges]))
 
+
+
+# --------------------------------------------------------------------------
+# the same draws on a torch device (for large requests generated where they
+# are used); bit patterns of uint64 arithmetic are carried in int64 tensors
+# --------------------------------------------------------------------------
+def _as_i64(u):
+    u = int(u) & 0xFFFFFFFFFFFFFFFF
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+def _lsr(z, k):
+    """Logical right shift of int64 bit patterns."""
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def uniform01_torch(seed, species, n, device, start=0):
+    """``uniform01`` computed with torch on ``device`` (same values)."""
+    import torch
+    base = _as_i64((int(seed) * 0x9E3779B97F4A7C15) ^ (int(species) * 0xC2B2AE3D27D4EB4F))
+    z = torch.arange(start, start + n, dtype=torch.int64, device=device) + base
+    z = z + _as_i64(0x9E3779B97F4A7C15)
+    z = (z ^ _lsr(z, 30)) * _as_i64(0xBF58476D1CE4E5B9)
+    z = (z ^ _lsr(z, 27)) * _as_i64(0x94D049BB133111EB)
+    z = z ^ _lsr(z, 31)
+    return _lsr(z, 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+
+
+def initial_fields_torch(cfg, device, seed=None):
+    """``initial_fields`` (float32) generated with torch on ``device``."""
+    import torch
+    nx, ny, nz = cfg["shape"]
+    ncell = nx * ny * nz
+    s = cfg["seed"] if seed is None else seed
+    S = cfg["nspecies"]
+    out = torch.empty((S, nz, ny, nx), dtype=torch.float64, device=device)
+    kind = cfg["init"]
+    if kind == "blob":
+        u = uniform01_torch(s, 0, ncell, device).reshape(nz, ny, nx)
+        z = torch.arange(nz, device=device, dtype=torch.float64).view(nz, 1, 1)
+        y = torch.arange(ny, device=device, dtype=torch.float64).view(1, ny, 1)
+        x = torch.arange(nx, device=device, dtype=torch.float64).view(1, 1, nx)
+        cx, cy, cz = (nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0
+        r2 = (x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2
+        out[0] = u + 10.0 * torch.exp(-r2 / (2.0 * 6.0 ** 2))
+    elif kind == "brusselator":
+        a, b = cfg["params"]["a"], cfg["params"]["b"]
+        base = (a, b / a)
+        for sp in range(2):
+            u = uniform01_torch(s, sp, ncell, device).reshape(nz, ny, nx)
+            out[sp] = base[sp] * (1.0 + 0.01 * (2.0 * u - 1.0))
+    elif kind == "ch_front":
+        out[0] = 0.0
+        out[0, 0, :, :] = cfg["bc_value"][0][4]
+        out[1] = 1.0
+        u = uniform01_torch(s, 2, ncell, device).reshape(nz, ny, nx)
+        out[2] = 0.005 * (2.0 * u - 1.0)
+    elif kind == "air":
+        base = (0.01, 0.01, 1.0)
+        for sp in range(3):
+            u = uniform01_torch(s, sp, ncell, device).reshape(nz, ny, nx)
+            out[sp] = base[sp] * (1.0 + 0.01 * (2.0 * u - 1.0))
+    elif kind == "uniform_noise":
+        for sp in range(S):
+            out[sp] = uniform01_torch(s, sp, ncell, device).reshape(nz, ny, nx)
+    else:
+        raise ValueError(f"unknown initial condition {kind!r}")
+    return out.to(torch.float32)
