@@ -44,14 +44,19 @@ KERNEL_SOURCES = ["paper_1004_0480_gb300/csrc/rd_step_kernel.cuh",
 
 # ------------------------------------------------------------------ helpers
 def dist_setup(n_gpus):
+    """Rank layout from the torchrun environment; one process per GPU.
+    NCCL where CUDA is present, else gloo (the CPU test of the N > 1 path)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return ws, rank, local
 
 
@@ -62,13 +67,21 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """The slowest rank's value (the job ends when every replica is done)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_glups(cell_steps_per_rank, ws, elapsed_s):
+    """Aggregate throughput: every rank's cell-steps over the slowest rank's
+    time (weak scaling: each rank runs its own replica of the job)."""
+    return cell_steps_per_rank * ws / elapsed_s / 1e9
 
 
 def measured_peak():
@@ -293,7 +306,7 @@ def run_ours(args, ws, rank, local):
     elapsed_ms = max_over_ranks(elapsed_ms, ws)
     clocks = clk.summary()
     total_cell_steps = cells * steps_per_job * args.steps * ws
-    value = total_cell_steps / (elapsed_ms * 1e-3) / 1e9
+    value = whole_job_glups(cells * steps_per_job * args.steps, ws, elapsed_ms * 1e-3)
 
     # roofline of the step kernel: 2 species x (read + write) x 4 B per cell-step
     T = tun["tsteps"]
