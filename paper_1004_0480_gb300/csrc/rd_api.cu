@@ -409,6 +409,18 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
 
 long long items_of(const InstDesc& d) { return (long long)d.ntx * d.nty * d.nzc; }
 
+// No held layers, point source or wind, and every species isotropic: the
+// one-step kernel may then use its fast variant.
+bool plain_problem(const rd_config& g) {
+    if (g.wind_kind != RD_WIND_NONE || g.src_species >= 0) return false;
+    for (int s = 0; s < g.nspecies; ++s) {
+        for (int f = 0; f < 6; ++f)
+            if (g.bc[s][f] == RD_BC_DIRICHLET) return false;
+        if (g.D[s][0] != g.D[s][1] || g.D[s][0] != g.D[s][2]) return false;
+    }
+    return true;
+}
+
 rd_status upload_desc(rd_ctx* c) {
     if (!c->desc_dirty) return RD_OK;
     fill_desc(c, c->desc, c->tun);
@@ -453,6 +465,7 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     a.use_one = 1;
     a.one = c->desc;
     a.regcap = c->tun.regcap;
+    a.fast = plain_problem(c->cfg);
     a.ty = c->tun.tile_y;
     const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty);
     const int occ = std::max(1, occupancy(c->cfg.model, c->cfg.storage, T, sm, threads_of(c->cfg.model, T, a.ty), a.regcap));
@@ -1010,6 +1023,8 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
     a.parity = parity;
     a.nitems = nitems;
     a.regcap = t.regcap;
+    a.fast = 1;
+    for (rd_ctx* m : b->members) a.fast = a.fast && plain_problem(m->cfg);
     a.ty = t.tile_y;
     const size_t sm = smem_of(b->model, b->storage, T, a.ty);
     const int occ = std::max(1, occupancy(b->model, b->storage, T, sm, threads_of(b->model, T, a.ty), a.regcap));

@@ -123,6 +123,7 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 struct MDiffusion {
     static constexpr int S = 1;
     static constexpr bool CH = false;
+    static constexpr bool FASTOK = true;    // fast one-step variant built
     __device__ __forceinline__ static void react(const InstDesc&, const float*, float* inc) {
         inc[0] = 0.0f;
     }
@@ -133,6 +134,7 @@ struct MDiffusion {
 struct MBrusselator {
     static constexpr int S = 2;
     static constexpr bool CH = false;
+    static constexpr bool FASTOK = true;
     __device__ __forceinline__ static void react(const InstDesc& d, const float* c, float* inc) {
         const float u = c[0], v = c[1];
         const float uuv = __fmul_rn(__fmul_rn(u, u), v);
@@ -148,6 +150,7 @@ struct MBrusselator {
 struct MAir {
     static constexpr int S = 3;
     static constexpr bool CH = false;
+    static constexpr bool FASTOK = false;   // always has wind and a source
     __device__ __forceinline__ static void react(const InstDesc& d, const float* c, float* inc) {
         const float ph = __fmul_rn(d.p[0], c[1]);
         const float ti = __fmul_rn(__fmul_rn(d.p[1], c[0]), c[2]);
@@ -163,6 +166,7 @@ struct MAir {
 struct MChFront {
     static constexpr int S = 3;
     static constexpr bool CH = true;
+    static constexpr bool FASTOK = false;
     __device__ __forceinline__ static void react(const InstDesc& d, const float* c, float* inc) {
         const float q = __fmul_rn(__fmul_rn(d.p[0], c[0]), c[1]);
         inc[0] = -q;
@@ -610,18 +614,29 @@ struct Fetch {
 
 template <class ST>
 __device__ __forceinline__ Fetch make_fetch(int yrow, int xs, int nx, int ny, int pitch, bool px,
-                                            bool py, int soff_elems) {
+                                            bool py, int soff_elems, bool clamp) {
     Fetch f{0, 0, soff_elems * (int)sizeof(ST), xs};
-    if (!py && (yrow < 0 || yrow >= ny)) return f;
-    const int yw = py ? wrapi(yrow, ny) : yrow;
+    int yw = yrow;
+    if (py) {
+        yw = wrapi(yrow, ny);
+    } else if (yrow < 0 || yrow >= ny) {
+        if (!clamp) return f;                     // never read
+        yw = yrow < 0 ? 0 : ny - 1;               // ghost row = face row
+    }
     const int row = yw * pitch;
-    if (xs >= 0 && xs < nx && (!px || xs + kVEC <= nx)) {
+    if (xs >= 0 && xs + kVEC <= nx) {
         f.mode = 1;
         f.goff = row + xs;
     } else if (px) {
         const int xw = wrapi(xs, nx);
         if (xw % kVEC == 0 && xw + kVEC <= nx) { f.mode = 1; f.goff = row + xw; }
         else { f.mode = 2; f.goff = row; }
+    } else if (clamp) {
+        f.mode = 2;                               // ghost cells = face cell
+        f.goff = row;
+    } else if (xs >= 0 && xs < nx) {
+        f.mode = 1;                               // last vector: tail in the row padding
+        f.goff = row + xs;
     }
     return f;
 }
@@ -631,17 +646,21 @@ __device__ __forceinline__ Fetch make_fetch(int yrow, int xs, int nx, int ny, in
 template <class ST, int S>
 __device__ __forceinline__ void fetch_all(const Fetch& f, unsigned char* plane_buf, int pe_bytes,
                                           const ST* gplane, long long fstride, int nx,
-                                          bool wrap) {
+                                          bool elems, bool px) {
 #pragma unroll
     for (int s = 0; s < S; ++s)
         Store<ST>::cp_async_if(reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff),
                                gplane + s * fstride + f.goff, f.mode == 1);
-    if (wrap && f.mode == 2) {
+    if (elems && f.mode == 2) {
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             ST* d = reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff);
 #pragma unroll
-            for (int e = 0; e < kVEC; ++e) d[e] = gplane[s * fstride + f.goff + wrapi(f.xs + e, nx)];
+            for (int e = 0; e < kVEC; ++e) {
+                const int x = f.xs + e;
+                const int xi = px ? wrapi(x, nx) : (x < 0 ? 0 : (x >= nx ? nx - 1 : x));
+                d[e] = gplane[s * fstride + f.goff + xi];
+            }
         }
     }
 }
@@ -655,7 +674,12 @@ __device__ __forceinline__ float lds_one(const unsigned char* p) {
     return Store<ST>::get(reinterpret_cast<const ST*>(p));
 }
 
-template <class M, class ST, bool ONE, int MINB>
+// FAST: no held layers, point source or wind, every species isotropic.
+// Then zero-flux ghosts are loaded as copies of the face cells (rows,
+// vectors and planes at distance one), every neighbour sits at a fixed
+// offset from the thread's own vector, and the update is the isotropic one;
+// the arithmetic per cell is the same as on the general path.
+template <class M, class ST, bool ONE, int MINB, bool FAST>
 __global__ void __launch_bounds__(kMaxThreads, MINB)
 rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
     using LY = Layout1<M, ST>;
@@ -689,7 +713,9 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
 
         const int nx = sd.nx, ny = sd.ny, nz = sd.nz, pitch = sd.pitch;
         const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;
-        const bool wrap = sd.wrap_elems;
+        // element-wise copies happen for periodic x with nx % 4 != 0, and on
+        // the fast path at zero-flux x faces
+        const bool elems = sd.wrap_elems || (FAST && !sd.per_x);
         const long long local = item - sd.item_begin;
         const int txi = (int)(local % sd.ntx);
         const int tyi = (int)((local / sd.ntx) % sd.nty);
@@ -717,13 +743,13 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                     const bool right = j & 1;
                     const int xh = right ? x0 + kTileQ * kVEC : x0 - kVEC;
                     f = make_fetch<ST>(y0 + hr, xh, nx, ny, pitch, px, py,
-                                       (hr + 1) * kRW + (right ? kNQ - 1 : 0) * kVEC);
+                                       (hr + 1) * kRW + (right ? kNQ - 1 : 0) * kVEC, FAST);
                 } else if (j < 2 * TY + 2 * kTileQ) {
                     const int jj = j - 2 * TY;
                     const bool bottom = jj >= kTileQ;
                     const int hv = jj - (bottom ? kTileQ : 0);
                     f = make_fetch<ST>(bottom ? y0 + TY : y0 - 1, x0 + hv * kVEC, nx, ny, pitch, px,
-                                       py, (bottom ? TY + 1 : 0) * kRW + (hv + 1) * kVEC);
+                                       py, (bottom ? TY + 1 : 0) * kRW + (hv + 1) * kVEC, FAST);
                 }
                 hfetch[j] = make_int4(f.mode, f.goff, f.soff, f.xs);
             }
@@ -739,30 +765,36 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
         const bool computes = !halo_warp && y < ny && xs < nx;
         const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
         const Fetch fo = halo_warp ? Fetch{0, 0, 0, 0}
-                                   : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB);
+                                   : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB, FAST);
         __syncthreads();   // halo descriptors written
 
         // ---- the march: plane nld (ring slot sld) is fetched P planes ahead
         int nld = z0 - 1, sld = 0;
-        int zld = pz ? wrapi(nld, nz) : nld;
-        const ST* gld = gin + (long long)zld * plane;
+        int zld = pz ? wrapi(nld, nz) : nld;      // plane index the copy reads
         auto issue = [&]() {
-            if (nld <= z1 && (pz || (nld >= 0 && nld < nz))) {
+            // zero-flux z: off the grid nothing is read (general path) or
+            // the face plane is copied (fast path)
+            const bool in_z = pz || (nld >= 0 && nld < nz);
+            if (nld <= z1 && (in_z || FAST)) {
+                const int zs = in_z ? zld : (nld < 0 ? 0 : nz - 1);
+                const ST* gld = gin + (long long)zs * plane;
                 unsigned char* buf = ring + sld * SLOTB;
                 if (halo_warp) {
                     const int hl = tid - ncomp;
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const int4 h = hfetch[hl + 32 * k];
-                        fetch_all<ST, S>(Fetch{h.x, h.y, h.z, h.w}, buf, PEB, gld, fstride, nx, wrap);
+                        fetch_all<ST, S>(Fetch{h.x, h.y, h.z, h.w}, buf, PEB, gld, fstride, nx,
+                                         elems, px);
                     }
                 } else {
-                    fetch_all<ST, S>(fo, buf, PEB, gld, fstride, nx, wrap);
+                    fetch_all<ST, S>(fo, buf, PEB, gld, fstride, nx, elems, px);
                 }
             }
             ++nld;
             sld = (sld == RING - 1) ? 0 : sld + 1;
-            if (pz && ++zld == nz) { zld = 0; gld = gin; } else { gld += plane; }
+            if (!pz) zld = nld;
+            else if (++zld == nz) zld = 0;
             cp_async_commit();
         };
 #pragma unroll 1
@@ -778,7 +810,46 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
             issue();
             cp_async_wait<P - 2>();
             __syncthreads();
-            if (!halo_warp) {
+            if (FAST && !halo_warp) {
+                // every neighbour at a fixed offset; ghosts were copied in
+                const int sm = sc == 0 ? RING - 1 : sc - 1;
+                const int sp = sc == RING - 1 ? 0 : sc + 1;
+                const unsigned char* Pc = ring + sc * SLOTB + own_b;
+                const unsigned char* Pm = ring + sm * SLOTB + own_b;
+                const unsigned char* Pp = ring + sp * SLOTB + own_b;
+                float cen[S][kVEC], inc[S][kVEC];
+#pragma unroll
+                for (int s = 0; s < S; ++s) lds_vec<ST>(Pc + s * PEB, cen[s]);
+#pragma unroll
+                for (int e = 0; e < kVEC; ++e) {
+                    float cv[S], iv[S];
+#pragma unroll
+                    for (int s = 0; s < S; ++s) cv[s] = cen[s][e];
+                    M::react(sd, cv, iv);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
+                }
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const unsigned char* Ps = Pc + s * PEB;
+                    float ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], o[kVEC];
+                    lds_vec<ST>(Pm + s * PEB, zm);
+                    lds_vec<ST>(Pp + s * PEB, zp);
+                    lds_vec<ST>(Ps - RWB, ym);
+                    lds_vec<ST>(Ps + RWB, yp);
+                    const float left = lds_one<ST>(Ps - EB);
+                    const float right = lds_one<ST>(Ps + kVEC * EB);
+                    const float k = sd.kx[s];
+#pragma unroll
+                    for (int e = 0; e < kVEC; ++e) {
+                        const float xm = e ? cen[s][e - 1] : left;
+                        const float xp = (e < kVEC - 1) ? cen[s][e + 1] : right;
+                        o[e] = euler_cell_iso(cen[s][e], xm, xp, ym[e], yp[e], zm[e], zp[e], k,
+                                              inc[s][e]);
+                    }
+                    if (computes) Store<ST>::store(gst + s * fstride, o);
+                }
+            } else if (!halo_warp) {
                 const int sm = (!pz && q == 0) ? sc : (sc == 0 ? RING - 1 : sc - 1);
                 const int sp = (!pz && q == nz - 1) ? sc : (sc == RING - 1 ? 0 : sc + 1);
                 const unsigned char* Pc = ring + sc * SLOTB;
@@ -836,12 +907,22 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
     void (*k)(const LaunchArgs);
     if constexpr (lean) {
         // register budget of the one-step kernel: 128 (regcap 0) or 64 (regcap 1)
-        k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2> : rd_step1_kernel<M, ST, ONE, 1>;
+        if constexpr (M::FASTOK) {
+            if (a.fast)
+                k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, true>
+                             : rd_step1_kernel<M, ST, ONE, 1, true>;
+            else
+                k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, false>
+                             : rd_step1_kernel<M, ST, ONE, 1, false>;
+        } else {
+            k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, false>
+                         : rd_step1_kernel<M, ST, ONE, 1, false>;
+        }
     } else {
         k = rd_step_kernel<M, ST, T, ONE>;
     }
-    static size_t configured[2] = {0, 0};
-    size_t& conf = configured[lean && a.regcap ? 1 : 0];
+    static size_t configured[4] = {0, 0, 0, 0};
+    size_t& conf = configured[(lean && a.regcap ? 1 : 0) + (lean && a.fast && M::FASTOK ? 2 : 0)];
     if (smem > conf) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
