@@ -378,62 +378,113 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
+def _timed_steps(torch, sim, steps, reps=2):
+    """Device time (CUDA events on the context's stream) of ``steps`` steps,
+    best of ``reps``; the state keeps evolving, which does not change the
+    work."""
+    stream = torch.cuda.Stream()
+    sim.set_stream(stream)
+    sim.step(min(steps, 50))
+    sim.sync()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return best
+
+
+def _entry(cells, steps, seconds, bytes_per_cell_step, tuning=None, **kw):
+    peak, _ = measured_peak()
+    glups = cells * steps / seconds / 1e9
+    d = {"glups": glups, "cells": cells, "steps": steps,
+         "bytes_per_cell_step": bytes_per_cell_step,
+         "roofline_frac": glups * bytes_per_cell_step / peak}
+    if tuning is not None:
+        d["tuning"] = tuning
+    d.update(kw)
+    return d
+
+
 def run_extras(args, Sim, Batch, torch):
-    """BF16-storage variant, and the batched front workload vs the plain
-    one-launch-per-instance stepper."""
+    """The other workloads: GLUPS and fraction of the measured HBM peak
+    (algorithmic bytes 2 x species x bytes per value per cell-step)."""
     out = {}
-    # BF16 storage, same job
+    # Brusselator 256^3 with BF16 storage (8 B per cell-step)
     cfg = W.cfg_brusselator_256()
-    cells = W.cell_count(cfg)
-    f = W.initial_fields(cfg)
     with Sim(cfg, storage="bf16") as sim:
-        sim.set_fields(f)
+        sim.set_fields(W.initial_fields(cfg))
         tun = sim.autotune()
-        sim.step(200)
-        sim.sync()
-        t0 = time.perf_counter()
-        sim.step(cfg["steps"])
-        sim.sync()
-        ms = (time.perf_counter() - t0) * 1e3
-        out["bf16_storage"] = {"glups": cells * cfg["steps"] / (ms * 1e-3) / 1e9,
-                               "tuning": tun}
-    # batched front instances vs plain per-instance stepping
+        t = _timed_steps(torch, sim, 2000)
+        out["brusselator_256_bf16"] = _entry(W.cell_count(cfg), 2000, t, 8, tun)
+    # inert diffusion 64^3, 100 steps (L2-resident: launch-bound, not HBM)
+    cfg = W.cfg_diffusion_64()
+    with Sim(cfg) as sim:
+        sim.set_fields(W.initial_fields(cfg))
+        tun = sim.autotune()
+        t = _timed_steps(torch, sim, cfg["steps"], reps=5)
+        out["diffusion_64"] = _entry(W.cell_count(cfg), cfg["steps"], t, 8, tun,
+                                     note="1 MiB per level: L2-resident, launch-bound")
+    # the same kinetics at 512^3 (1 GiB per level) for the HBM roofline
+    cfg = W.diffusion_blob(512, steps=400, dt=0.1)
+    with Sim(cfg) as sim:
+        sim.set_fields(W.initial_fields_torch(cfg, "cuda"))
+        tun = sim.autotune()
+        t = _timed_steps(torch, sim, 400)
+        out["diffusion_512"] = _entry(W.cell_count(cfg), 400, t, 8, tun)
+    # air 512 x 512 x 64, 3 species (24 B per cell-step)
+    cfg = W.cfg_air_512()
+    with Sim(cfg) as sim:
+        sim.set_fields(W.initial_fields_torch(cfg, "cuda"))
+        tun = sim.autotune()
+        t = _timed_steps(torch, sim, 1000)
+        out["air_512x512x64"] = _entry(W.cell_count(cfg), 1000, t, 24, tun)
+    # 32 uneven front instances (3 species, 24 B per cell-step), full 2000
+    # steps: one batched launch sequence vs the plain stepper
     cfgs = W.cfg_ch_front_batch(steps=args.batch_steps)
     cells_b = sum(W.cell_count(c) for c in cfgs)
     sims = [Sim(c) for c in cfgs]
-    for c, s in zip(cfgs, sims):
-        s.set_fields(W.initial_fields(c))
-    b = Batch("ch_front")
-    b.set_tuning(tsteps=1, tile_q=16, tile_y=8, zchunk=32, graph=1)
-    for s in sims:
-        b.add(s)
+    for c, sm in zip(cfgs, sims):
+        sm.set_fields(W.initial_fields_torch(c, "cuda"))
+    stream = torch.cuda.Stream()
+    b = Batch("ch_front", stream=stream)
+    btun = dict(tsteps=1, tile_q=16, tile_y=8, zchunk=32, graph=1)
+    b.set_tuning(**btun)
+    for sm in sims:
+        b.add(sm)
     b.step(20)
     b.sync()
-    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     b.step(args.batch_steps)
-    b.sync()
-    bt = time.perf_counter() - t0
-    for s in sims:
-        b.remove(s)
+    e1.record(stream)
+    e1.synchronize()
+    bt = e0.elapsed_time(e1) * 1e-3
+    for sm in sims:
+        b.remove(sm)
     b.close()
     # plain stepper: the fused kernel at T=1, one launch per instance and
     # step, no graph, instances serialised in arrival order on one stream
     common = torch.cuda.Stream()
-    for s in sims:
-        s.set_tuning(tsteps=1, graph=0)
-        s.set_stream(common)
+    for sm in sims:
+        sm.set_tuning(tsteps=1, graph=0)
+        sm.set_stream(common)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s in sims:
-        s.step(args.batch_steps)
-    common.synchronize()
-    pt = time.perf_counter() - t0
-    for s in sims:
-        s.close()
+    e0.record(common)
+    for sm in sims:
+        sm.step(args.batch_steps)
+    e1.record(common)
+    e1.synchronize()
+    pt = e0.elapsed_time(e1) * 1e-3
+    for sm in sims:
+        sm.close()
     out["ch_front_batch_32"] = {
-        "instances": len(cfgs), "cells": cells_b, "steps": args.batch_steps,
-        "batched_glups": cells_b * args.batch_steps / bt / 1e9,
-        "plain_glups": cells_b * args.batch_steps / pt / 1e9,
+        "instances": len(cfgs),
+        "batched": _entry(cells_b, args.batch_steps, bt, 24, btun),
+        "plain": _entry(cells_b, args.batch_steps, pt, 24, dict(tsteps=1, graph=0)),
         "speedup": pt / bt}
     return out
 
@@ -504,7 +555,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
-    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--job-steps", type=int, default=0,
                     help="time steps per job (default: the workload's 10 000)")
     ap.add_argument("--tuning", default="",

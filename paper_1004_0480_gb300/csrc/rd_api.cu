@@ -82,6 +82,7 @@ size_t smem_of(int model, int storage, int T, int ty) {
 // vector; the multi-level kernel (tile vectors + 2 halo) x (rows + 2 L)
 int threads_of(int model, int T, int ty) {
     if (T == 1 && model != RD_MODEL_CH_FRONT) return kTileQ * ty + 32;
+    if (T == 1) return (kTileQ + 2) * (ty + 2);   // one-step Cahn-Hilliard kernel
     const int L = (model == RD_MODEL_CH_FRONT ? 2 : 1) * T;
     return (kTileQ + 2) * (ty + 2 * L);
 }
@@ -111,9 +112,9 @@ int occupancy(int model, int storage, int T, size_t smem, int threads, int regca
     LaunchArgs dummy{};
     dummy.use_one = 1;
     dummy.regcap = regcap;
-    dummy.ty = (T == 1 && model != RD_MODEL_CH_FRONT)
-                   ? (threads - 32) / kTileQ
-                   : threads / (kTileQ + 2) - 2 * (model == RD_MODEL_CH_FRONT ? 2 : 1) * T;
+    dummy.ty = (T == 1 && model != RD_MODEL_CH_FRONT) ? (threads - 32) / kTileQ
+               : (T == 1) ? threads / (kTileQ + 2) - 2
+                          : threads / (kTileQ + 2) - 2 * (model == RD_MODEL_CH_FRONT ? 2 : 1) * T;
     if (launch_model(model, storage, T, dummy, 0, smem, nullptr, &occ) != cudaSuccess) occ = 0;
     cudaGetLastError();
     cache[key] = occ;
@@ -409,8 +410,8 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
 
 long long items_of(const InstDesc& d) { return (long long)d.ntx * d.nty * d.nzc; }
 
-// No held layers, point source or wind, and every species isotropic: the
-// one-step kernel may then use its fast variant.
+// No held layer, point source or wind, and every species isotropic: the
+// one-step kernel's branch-free update applies.
 bool plain_problem(const rd_config& g) {
     if (g.wind_kind != RD_WIND_NONE || g.src_species >= 0) return false;
     for (int s = 0; s < g.nspecies; ++s) {
@@ -465,7 +466,7 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     a.use_one = 1;
     a.one = c->desc;
     a.regcap = c->tun.regcap;
-    a.fast = plain_problem(c->cfg);
+    a.plain = plain_problem(c->cfg);
     a.ty = c->tun.tile_y;
     const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty);
     const int occ = std::max(1, occupancy(c->cfg.model, c->cfg.storage, T, sm, threads_of(c->cfg.model, T, a.ty), a.regcap));
@@ -1023,8 +1024,8 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
     a.parity = parity;
     a.nitems = nitems;
     a.regcap = t.regcap;
-    a.fast = 1;
-    for (rd_ctx* m : b->members) a.fast = a.fast && plain_problem(m->cfg);
+    a.plain = 1;
+    for (rd_ctx* m : b->members) a.plain = a.plain && plain_problem(m->cfg);
     a.ty = t.tile_y;
     const size_t sm = smem_of(b->model, b->storage, T, a.ty);
     const int occ = std::max(1, occupancy(b->model, b->storage, T, sm, threads_of(b->model, T, a.ty), a.regcap));

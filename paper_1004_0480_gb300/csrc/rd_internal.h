@@ -44,8 +44,8 @@ struct LaunchArgs {
     int ty;                    // tile height in rows (width is kTileQ vectors)
     int use_one;               // 1: a single instance, described by ``one``
     int regcap;                // one-step kernel: 1 = at most 64 registers
-    int fast;                  // one-step kernel: every instance is plain (no
-                               // held layers, source or wind; isotropic D)
+    int plain;                 // every instance has no held layer, source or
+                               // wind, and isotropic diffusivities
     InstDesc one;              // the instance of a single-instance launch
 };
 

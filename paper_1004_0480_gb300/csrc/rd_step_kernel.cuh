@@ -70,6 +70,12 @@ template <> struct Store<float> {
                      "r"(pred)
                      : "memory");
     }
+    // one element (4 bytes), asynchronously
+    static constexpr bool kAsyncElem = true;
+    __device__ __forceinline__ static void cp_async_elem(float* smem, const float* g) {
+        const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g) : "memory");
+    }
 };
 
 template <> struct Store<__nv_bfloat16> {
@@ -95,6 +101,12 @@ template <> struct Store<__nv_bfloat16> {
     __device__ __forceinline__ static void cp_async(__nv_bfloat16* smem, const __nv_bfloat16* g) {
         const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
+    }
+    // 2-byte elements have no asynchronous copy: element copies are plain
+    static constexpr bool kAsyncElem = false;
+    __device__ __forceinline__ static void cp_async_elem(__nv_bfloat16* smem,
+                                                         const __nv_bfloat16* g) {
+        *smem = *g;
     }
     __device__ __forceinline__ static void cp_async_if(__nv_bfloat16* smem,
                                                        const __nv_bfloat16* g, int pred) {
@@ -123,7 +135,6 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 struct MDiffusion {
     static constexpr int S = 1;
     static constexpr bool CH = false;
-    static constexpr bool FASTOK = true;    // fast one-step variant built
     __device__ __forceinline__ static void react(const InstDesc&, const float*, float* inc) {
         inc[0] = 0.0f;
     }
@@ -134,7 +145,6 @@ struct MDiffusion {
 struct MBrusselator {
     static constexpr int S = 2;
     static constexpr bool CH = false;
-    static constexpr bool FASTOK = true;
     __device__ __forceinline__ static void react(const InstDesc& d, const float* c, float* inc) {
         const float u = c[0], v = c[1];
         const float uuv = __fmul_rn(__fmul_rn(u, u), v);
@@ -150,7 +160,6 @@ struct MBrusselator {
 struct MAir {
     static constexpr int S = 3;
     static constexpr bool CH = false;
-    static constexpr bool FASTOK = false;   // always has wind and a source
     __device__ __forceinline__ static void react(const InstDesc& d, const float* c, float* inc) {
         const float ph = __fmul_rn(d.p[0], c[1]);
         const float ti = __fmul_rn(__fmul_rn(d.p[1], c[0]), c[2]);
@@ -166,7 +175,6 @@ struct MAir {
 struct MChFront {
     static constexpr int S = 3;
     static constexpr bool CH = true;
-    static constexpr bool FASTOK = false;
     __device__ __forceinline__ static void react(const InstDesc& d, const float* c, float* inc) {
         const float q = __fmul_rn(__fmul_rn(d.p[0], c[0]), c[1]);
         inc[0] = -q;
@@ -674,12 +682,15 @@ __device__ __forceinline__ float lds_one(const unsigned char* p) {
     return Store<ST>::get(reinterpret_cast<const ST*>(p));
 }
 
-// FAST: no held layers, point source or wind, every species isotropic.
-// Then zero-flux ghosts are loaded as copies of the face cells (rows,
-// vectors and planes at distance one), every neighbour sits at a fixed
-// offset from the thread's own vector, and the update is the isotropic one;
-// the arithmetic per cell is the same as on the general path.
-template <class M, class ST, bool ONE, int MINB, bool FAST>
+// Zero-flux ghost cells are copied in as face values at distance one (rows,
+// vectors and planes), as the paper sets its boundary layer before each
+// step; every neighbour then sits at a fixed offset from the thread's own
+// vector.  An upwind inflow face sees a zero gradient, and a held layer's
+// ghost only feeds the held cell's own update, which is replaced by its bc
+// value, so this is exact for every one-step problem.
+// PLAIN: no held layer, point source or wind, and every species isotropic;
+// the update then needs no per-plane or per-species branches.
+template <class M, class ST, bool ONE, int MINB, bool PLAIN>
 __global__ void __launch_bounds__(kMaxThreads, MINB)
 rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
     using LY = Layout1<M, ST>;
@@ -713,9 +724,8 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
 
         const int nx = sd.nx, ny = sd.ny, nz = sd.nz, pitch = sd.pitch;
         const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;
-        // element-wise copies happen for periodic x with nx % 4 != 0, and on
-        // the fast path at zero-flux x faces
-        const bool elems = sd.wrap_elems || (FAST && !sd.per_x);
+        // element-wise copies: periodic x with nx % 4 != 0, and zero-flux x faces
+        const bool elems = sd.wrap_elems || !sd.per_x;
         const long long local = item - sd.item_begin;
         const int txi = (int)(local % sd.ntx);
         const int tyi = (int)((local / sd.ntx) % sd.nty);
@@ -743,13 +753,13 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                     const bool right = j & 1;
                     const int xh = right ? x0 + kTileQ * kVEC : x0 - kVEC;
                     f = make_fetch<ST>(y0 + hr, xh, nx, ny, pitch, px, py,
-                                       (hr + 1) * kRW + (right ? kNQ - 1 : 0) * kVEC, FAST);
+                                       (hr + 1) * kRW + (right ? kNQ - 1 : 0) * kVEC, true);
                 } else if (j < 2 * TY + 2 * kTileQ) {
                     const int jj = j - 2 * TY;
                     const bool bottom = jj >= kTileQ;
                     const int hv = jj - (bottom ? kTileQ : 0);
                     f = make_fetch<ST>(bottom ? y0 + TY : y0 - 1, x0 + hv * kVEC, nx, ny, pitch, px,
-                                       py, (bottom ? TY + 1 : 0) * kRW + (hv + 1) * kVEC, FAST);
+                                       py, (bottom ? TY + 1 : 0) * kRW + (hv + 1) * kVEC, true);
                 }
                 hfetch[j] = make_int4(f.mode, f.goff, f.soff, f.xs);
             }
@@ -757,25 +767,19 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
         // ---- compute threads: own vector and its neighbours
         const int y = y0 + r;
         const int xs = x0 + v * kVEC;
-        const int offm_b = (!py && y == 0) ? own_b : own_b - RWB;
-        const int offp_b = (!py && y == ny - 1) ? own_b : own_b + RWB;
-        const int offl_b = (!px && xs == 0) ? own_b : own_b - EB;
-        const int offr_b = own_b + kVEC * EB;
-        const int xhi = (!px && xs <= nx - 1 && nx - 1 < xs + kVEC) ? nx - 1 - xs : -1;
         const bool computes = !halo_warp && y < ny && xs < nx;
         const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
         const Fetch fo = halo_warp ? Fetch{0, 0, 0, 0}
-                                   : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB, FAST);
+                                   : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB, true);
         __syncthreads();   // halo descriptors written
 
         // ---- the march: plane nld (ring slot sld) is fetched P planes ahead
         int nld = z0 - 1, sld = 0;
         int zld = pz ? wrapi(nld, nz) : nld;      // plane index the copy reads
         auto issue = [&]() {
-            // zero-flux z: off the grid nothing is read (general path) or
-            // the face plane is copied (fast path)
+            // zero-flux z: the face plane is copied in as the ghost plane
             const bool in_z = pz || (nld >= 0 && nld < nz);
-            if (nld <= z1 && (in_z || FAST)) {
+            if (nld <= z1) {
                 const int zs = in_z ? zld : (nld < 0 ? 0 : nz - 1);
                 const ST* gld = gin + (long long)zs * plane;
                 unsigned char* buf = ring + sld * SLOTB;
@@ -810,7 +814,7 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
             issue();
             cp_async_wait<P - 2>();
             __syncthreads();
-            if (FAST && !halo_warp) {
+            if (!halo_warp) {
                 // every neighbour at a fixed offset; ghosts were copied in
                 const int sm = sc == 0 ? RING - 1 : sc - 1;
                 const int sp = sc == RING - 1 ? 0 : sc + 1;
@@ -829,64 +833,34 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
 #pragma unroll
                     for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
                 }
-#pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    const unsigned char* Ps = Pc + s * PEB;
-                    float ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], o[kVEC];
-                    lds_vec<ST>(Pm + s * PEB, zm);
-                    lds_vec<ST>(Pp + s * PEB, zp);
-                    lds_vec<ST>(Ps - RWB, ym);
-                    lds_vec<ST>(Ps + RWB, yp);
-                    const float left = lds_one<ST>(Ps - EB);
-                    const float right = lds_one<ST>(Ps + kVEC * EB);
-                    const float k = sd.kx[s];
-#pragma unroll
-                    for (int e = 0; e < kVEC; ++e) {
-                        const float xm = e ? cen[s][e - 1] : left;
-                        const float xp = (e < kVEC - 1) ? cen[s][e + 1] : right;
-                        o[e] = euler_cell_iso(cen[s][e], xm, xp, ym[e], yp[e], zm[e], zp[e], k,
-                                              inc[s][e]);
-                    }
-                    if (computes) Store<ST>::store(gst + s * fstride, o);
-                }
-            } else if (!halo_warp) {
-                const int sm = (!pz && q == 0) ? sc : (sc == 0 ? RING - 1 : sc - 1);
-                const int sp = (!pz && q == nz - 1) ? sc : (sc == RING - 1 ? 0 : sc + 1);
-                const unsigned char* Pc = ring + sc * SLOTB;
-                const unsigned char* Pm = ring + sm * SLOTB;
-                const unsigned char* Pp = ring + sp * SLOTB;
-                float cen[S][kVEC], inc[S][kVEC];
-#pragma unroll
-                for (int s = 0; s < S; ++s) lds_vec<ST>(Pc + s * PEB + own_b, cen[s]);
-#pragma unroll
-                for (int e = 0; e < kVEC; ++e) {
-                    float cv[S], iv[S];
-#pragma unroll
-                    for (int s = 0; s < S; ++s) cv[s] = cen[s][e];
-                    M::react(sd, cv, iv);
-#pragma unroll
-                    for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
-                }
                 const float cx = courant ? courant[zq] : 0.0f;
                 const bool src_here = src_col && zq == sd.src_z;
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     const unsigned char* Ps = Pc + s * PEB;
                     float xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], o[kVEC];
-                    lds_vec<ST>(Pm + s * PEB + own_b, zm);
-                    lds_vec<ST>(Pp + s * PEB + own_b, zp);
-                    lds_vec<ST>(Ps + offm_b, ym);
-                    lds_vec<ST>(Ps + offp_b, yp);
-                    const float left = lds_one<ST>(Ps + offl_b);
-                    const float right = lds_one<ST>(Ps + offr_b);
+                    lds_vec<ST>(Pm + s * PEB, zm);
+                    lds_vec<ST>(Pp + s * PEB, zp);
+                    lds_vec<ST>(Ps - RWB, ym);
+                    lds_vec<ST>(Ps + RWB, yp);
+                    const float left = lds_one<ST>(Ps - EB);
+                    const float right = lds_one<ST>(Ps + kVEC * EB);
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e) {
                         xm[e] = e ? cen[s][e - 1] : left;
                         xp[e] = (e < kVEC - 1) ? cen[s][e + 1] : right;
-                        xp[e] = (e == xhi) ? cen[s][e] : xp[e];   // zero-flux +x face
                     }
-                    species_update(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s], cx, src_here, px,
-                                   xs, y, q, o);
+                    if constexpr (PLAIN) {
+                        // the same arithmetic species_update takes for this case
+                        const float k = sd.kx[s];
+#pragma unroll
+                        for (int e = 0; e < kVEC; ++e)
+                            o[e] = euler_cell_iso(cen[s][e], xm[e], xp[e], ym[e], yp[e], zm[e],
+                                                  zp[e], k, inc[s][e]);
+                    } else {
+                        species_update(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s], cx, src_here,
+                                       px, xs, y, q, o);
+                    }
                     if (computes) Store<ST>::store(gst + s * fstride, o);
                 }
             }
@@ -900,36 +874,304 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
     }
 }
 
+// -------------------------------------------- one-step Cahn-Hilliard kernel
+// The T = 1 path of the front model (a + b -> c, Cahn-Hilliard c).  Ghost
+// cells are copied in by mirror extension to distance two (index -1-i holds
+// cell i at a zero-flux face), so mu computed at a ghost cell equals mu at
+// the face cell -- the paper's "Laplacian, boundary rule, Laplacian" -- and
+// every neighbour sits at a fixed offset.  One thread per 4-cell vector of
+// the tile widened by one vector in x and one row in y: each computes mu
+// there for plane p+1 and, inside the tile, the new state of plane p.  The
+// z and own-vector inputs of the state update (own mu of planes p-1..p+1,
+// own a, b, c) were written by the thread itself; x/y neighbours come from
+// plane p, complete since the last barrier: one barrier per plane.  State
+// planes arrive in an 8-slot ring, 4 in flight; mu planes in a 4-slot ring.
+// Slot reuse: step p refills the slot of state plane p-2, whose neighbour
+// reads (mu of p-2 at step p-3, update of p-2 at step p-2) ended a barrier
+// earlier and whose last read (own vector, update of p-1) precedes the
+// refill in the owner's program order -- every vector is copied by the
+// thread that owns it; the two outer rows are only read as neighbours.  The
+// mu slot written at step p held mu of p-3, last read at step p-2.
+template <class ST> struct LayoutCH {
+    static constexpr int S = 3;
+    static constexpr int RING = 8;
+    static constexpr int P = 6;
+    static constexpr int MURING = 4;
+    __host__ __device__ static int rows(int ty) { return ty + 4; }
+    __host__ __device__ static int plane_elems(int ty) { return rows(ty) * kRW + 2 * kVEC; }
+    __host__ __device__ static size_t state_bytes(int ty) {
+        return (size_t)RING * S * plane_elems(ty) * sizeof(ST);
+    }
+    __host__ __device__ static size_t total(int ty) {
+        return state_bytes(ty) + (size_t)MURING * plane_elems(ty) * sizeof(float);
+    }
+    __host__ __device__ static int threads(int ty) { return kNQ * (ty + 2); }
+};
+
+// Mirror extension: -1-i for i < 0, 2n-1-i for i >= n; clamped so that
+// positions outside the grid by more than n (never stored) stay in bounds.
+__device__ __forceinline__ int mirror_index(int i, int n) {
+    const int m = i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i);
+    return min(max(m, 0), n - 1);
+}
+
+// Fetch with mirror-extended (zero-flux) or wrapped (periodic) coordinates.
+// Vectors past row ny + 1 or column nx + 1 feed no stored cell: not copied.
+template <class ST>
+__device__ __forceinline__ Fetch make_fetch_mirror(int yrow, int xs, int nx, int ny, int pitch,
+                                                   bool px, bool py, int soff_elems) {
+    Fetch f{0, 0, soff_elems * (int)sizeof(ST), xs};
+    if (yrow > ny + 1 || xs > nx + 1) return f;
+    const int yw = py ? wrapi(yrow, ny) : mirror_index(yrow, ny);
+    const int row = yw * pitch;
+    if (xs >= 0 && xs + kVEC <= nx) {
+        f.mode = 1;
+        f.goff = row + xs;
+    } else if (px) {
+        const int xw = wrapi(xs, nx);
+        if (xw % kVEC == 0 && xw + kVEC <= nx) { f.mode = 1; f.goff = row + xw; }
+        else { f.mode = 2; f.goff = row; }
+    } else {
+        f.mode = 2;
+        f.goff = row;
+    }
+    return f;
+}
+
+template <class ST, int S>
+__device__ __forceinline__ void fetch_all_mirror(const Fetch& f, unsigned char* plane_buf,
+                                                 int pe_bytes, const ST* gplane, long long fstride,
+                                                 int nx, bool px) {
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+        Store<ST>::cp_async_if(reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff),
+                               gplane + s * fstride + f.goff, f.mode == 1);
+    if (f.mode == 2) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            ST* d = reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff);
+#pragma unroll
+            for (int e = 0; e < kVEC; ++e) {
+                const int x = f.xs + e;
+                Store<ST>::cp_async_elem(
+                    d + e, gplane + s * fstride + f.goff + (px ? wrapi(x, nx) : mirror_index(x, nx)));
+            }
+        }
+    }
+}
+
+template <class ST, bool ONE>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
+    using LY = LayoutCH<ST>;
+    constexpr int S = 3;
+    constexpr int P = LY::P;
+    constexpr int RING = LY::RING;
+    constexpr int MURING = LY::MURING;
+    constexpr int EB = (int)sizeof(ST);
+    constexpr int RWB = kRW * EB;
+    constexpr int RWF = kRW * (int)sizeof(float);
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ InstDesc sdm;
+    __shared__ int s_inst;
+
+    const int tid = threadIdx.x;
+    const int TY = a.ty;
+    const int PE = LY::plane_elems(TY);
+    const int PEB = PE * EB;
+    const int SLOTB = S * PEB;
+    unsigned char* const ring = smem + kVEC * EB;
+    float* const muring = reinterpret_cast<float*>(smem + LY::state_bytes(TY)) + kVEC;
+    // thread (r, v): state/mu position row R = r + 1 (rows -1..TY of the
+    // tile), vector v (vectors -1..16)
+    const int r = tid / kNQ;
+    const int v = tid - r * kNQ;
+    const int own = (r + 1) * kRW + v * kVEC;       // element offset in a plane
+    const int own_b = own * EB;
+    const bool inner = r >= 1 && r <= TY && v >= 1 && v <= kTileQ;
+
+    int cur_inst = -1;
+    if (tid == 0) s_inst = 0;
+    for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+        if constexpr (!ONE) load_desc(a, item, sdm, s_inst, cur_inst);
+        const InstDesc& sd = desc_of<ONE>(a, sdm);
+
+        const int nx = sd.nx, ny = sd.ny, nz = sd.nz, pitch = sd.pitch;
+        const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;
+        const long long local = item - sd.item_begin;
+        const int txi = (int)(local % sd.ntx);
+        const int tyi = (int)((local / sd.ntx) % sd.nty);
+        const int zc = (int)(local / ((long long)sd.ntx * sd.nty));
+        const int x0 = txi * kTileQ * kVEC, y0 = tyi * TY;
+        const int z0 = zc * sd.zchunk;
+        const int z1 = min(z0 + sd.zchunk, nz);
+        const int lin = sd.par ^ a.parity;
+        const ST* const gin = reinterpret_cast<const ST*>(sd.base[lin][0]);
+        ST* const gout = reinterpret_cast<ST*>(sd.base[lin ^ 1][0]);
+        const long long fstride = reinterpret_cast<const ST*>(sd.base[lin][1]) - gin;
+        const long long plane = sd.plane;
+
+        const int y = y0 - 1 + r;                     // global row of the position
+        const int xs = x0 - kVEC + v * kVEC;          // global x of its first element
+        const bool stores = inner && y < ny && xs < nx;
+        // own state vector, and (first 2 x 18 threads) the outer halo rows
+        const Fetch fo = make_fetch_mirror<ST>(y, xs, nx, ny, pitch, px, py, own);
+        Fetch fx{0, 0, 0, 0};
+        if (tid < 2 * kNQ) {
+            const bool bottom = tid >= kNQ;
+            const int vv = tid - (bottom ? kNQ : 0);
+            fx = make_fetch_mirror<ST>(bottom ? y0 + TY + 1 : y0 - 2, x0 - kVEC + vv * kVEC, nx, ny,
+                                       pitch, px, py, (bottom ? TY + 3 : 0) * kRW + vv * kVEC);
+        }
+
+        // planes z0-2 .. z1+1 are copied, plane index nld into slot nld & 7
+        int nld = z0 - 2;
+        auto issue = [&]() {
+            if (nld <= z1 + 1) {
+                const int zs = pz ? wrapi(nld, nz) : mirror_index(nld, nz);
+                const ST* g = gin + (long long)zs * plane;
+                unsigned char* buf = ring + (nld & (RING - 1)) * SLOTB;
+                fetch_all_mirror<ST, S>(fo, buf, PEB, g, fstride, nx, px);
+                if (tid < 2 * kNQ) fetch_all_mirror<ST, S>(fx, buf, PEB, g, fstride, nx, px);
+            }
+            ++nld;
+            cp_async_commit();
+        };
+#pragma unroll 1
+        for (int j = 0; j < P; ++j) issue();
+
+        const float* courant = sd.courant;
+        const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
+        ST* gst = gout + (long long)z0 * plane + (long long)y * pitch + xs;
+#pragma unroll 1
+        for (int p = z0 - 2; p < z1; ++p) {
+            // planes through p + 2 must have landed: of the P + (p - z0 + 3)
+            // groups issued so far, all but the newest P - 2
+            issue();
+            cp_async_wait<P - 2>();
+            __syncthreads();
+            // ---- mu of plane p + 1 at every position of the widened tile
+            if (p + 1 >= z0 - 1 && r < TY + 2) {
+                const int q = p + 1;
+                const unsigned char* Cc = ring + (q & (RING - 1)) * SLOTB + 2 * PEB + own_b;
+                const unsigned char* Cm = ring + ((q - 1) & (RING - 1)) * SLOTB + 2 * PEB + own_b;
+                const unsigned char* Cp = ring + ((q + 1) & (RING - 1)) * SLOTB + 2 * PEB + own_b;
+                float c[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], mo[kVEC];
+                lds_vec<ST>(Cc, c);
+                lds_vec<ST>(Cm, zm);
+                lds_vec<ST>(Cp, zp);
+                lds_vec<ST>(Cc - RWB, ym);
+                lds_vec<ST>(Cc + RWB, yp);
+                const float left = lds_one<ST>(Cc - EB);
+                const float right = lds_one<ST>(Cc + kVEC * EB);
+#pragma unroll
+                for (int e = 0; e < kVEC; ++e) {
+                    const float xm = e ? c[e - 1] : left;
+                    const float xp = (e < kVEC - 1) ? c[e + 1] : right;
+                    mo[e] = MChFront::mu(sd, c[e], xm, xp, ym[e], yp[e], zm[e], zp[e]);
+                }
+                Store<float>::store(muring + (q & (MURING - 1)) * PE + own, mo);
+            }
+            // ---- new state of plane p inside the tile
+            if (p >= z0 && inner) {
+                const unsigned char* Sc = ring + (p & (RING - 1)) * SLOTB + own_b;
+                const unsigned char* Sm = ring + ((p - 1) & (RING - 1)) * SLOTB + own_b;
+                const unsigned char* Sp = ring + ((p + 1) & (RING - 1)) * SLOTB + own_b;
+                float cen[S][kVEC], inc[S][kVEC];
+#pragma unroll
+                for (int s = 0; s < S; ++s) lds_vec<ST>(Sc + s * PEB, cen[s]);
+#pragma unroll
+                for (int e = 0; e < kVEC; ++e) {
+                    float cv[S], iv[S];
+#pragma unroll
+                    for (int s = 0; s < S; ++s) cv[s] = cen[s][e];
+                    MChFront::react(sd, cv, iv);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
+                }
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const unsigned char* Ps = Sc + s * PEB;
+                    float xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], o[kVEC];
+                    lds_vec<ST>(Sm + s * PEB, zm);
+                    lds_vec<ST>(Sp + s * PEB, zp);
+                    lds_vec<ST>(Ps - RWB, ym);
+                    lds_vec<ST>(Ps + RWB, yp);
+                    const float left = lds_one<ST>(Ps - EB);
+                    const float right = lds_one<ST>(Ps + kVEC * EB);
+#pragma unroll
+                    for (int e = 0; e < kVEC; ++e) {
+                        xm[e] = e ? cen[s][e - 1] : left;
+                        xp[e] = (e < kVEC - 1) ? cen[s][e + 1] : right;
+                    }
+                    species_update(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s],
+                                   courant ? courant[p] : 0.0f, src_col && p == sd.src_z, px, xs,
+                                   y, p, o);
+                    if (stores) Store<ST>::store(gst + s * fstride, o);
+                }
+                {
+                    // c += dt M / h^2 * (7-point Laplacian of mu)
+                    const float* Mc = muring + (p & (MURING - 1)) * PE + own;
+                    const float* Mm = muring + ((p - 1) & (MURING - 1)) * PE + own;
+                    const float* Mp = muring + ((p + 1) & (MURING - 1)) * PE + own;
+                    float m0[kVEC], mym[kVEC], myp[kVEC], mzm[kVEC], mzp[kVEC], o[kVEC];
+                    Store<float>::load(Mc, m0);
+                    Store<float>::load(Mm, mzm);
+                    Store<float>::load(Mp, mzp);
+                    Store<float>::load(Mc - kRW, mym);
+                    Store<float>::load(Mc + kRW, myp);
+                    const float mleft = Mc[-1];
+                    const float mright = Mc[kVEC];
+#pragma unroll
+                    for (int e = 0; e < kVEC; ++e) {
+                        const float mxm = e ? m0[e - 1] : mleft;
+                        const float mxp = (e < kVEC - 1) ? m0[e + 1] : mright;
+                        const float s6 = __fadd_rn(__fadd_rn(__fadd_rn(mxm, mxp), __fadd_rn(mym[e], myp[e])),
+                                                   __fadd_rn(mzm[e], mzp[e]));
+                        const float lap = __fmaf_rn(-6.0f, m0[e], s6);
+                        o[e] = __fadd_rn(cen[2][e], __fmaf_rn(sd.p[1], lap, inc[2][e]));
+                    }
+                    held_layers(sd, 2, xs, y, p, o);
+                    if (stores) Store<ST>::store(gst + 2 * fstride, o);
+                }
+            }
+            if (p >= z0) gst += plane;
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+}
+
 // Launch helper used by the per-model translation units.
 template <class M, class ST, int T, bool ONE>
 cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t st, int* occ) {
     constexpr bool lean = (T == 1 && !M::CH);
+    constexpr bool lean_ch = (T == 1 && M::CH);
     void (*k)(const LaunchArgs);
-    if constexpr (lean) {
+    if constexpr (lean_ch) {
+        k = rd_stepch_kernel<ST, ONE>;
+    } else if constexpr (lean) {
         // register budget of the one-step kernel: 128 (regcap 0) or 64 (regcap 1)
-        if constexpr (M::FASTOK) {
-            if (a.fast)
-                k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, true>
-                             : rd_step1_kernel<M, ST, ONE, 1, true>;
-            else
-                k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, false>
-                             : rd_step1_kernel<M, ST, ONE, 1, false>;
-        } else {
+        if (a.plain)
+            k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, true> : rd_step1_kernel<M, ST, ONE, 1, true>;
+        else
             k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, false>
                          : rd_step1_kernel<M, ST, ONE, 1, false>;
-        }
     } else {
         k = rd_step_kernel<M, ST, T, ONE>;
     }
     static size_t configured[4] = {0, 0, 0, 0};
-    size_t& conf = configured[(lean && a.regcap ? 1 : 0) + (lean && a.fast && M::FASTOK ? 2 : 0)];
+    size_t& conf = configured[(lean && a.regcap ? 1 : 0) + (lean && a.plain ? 2 : 0)];
     if (smem > conf) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         conf = smem;
     }
-    const int threads = lean ? Layout1<M, ST>::threads(a.ty) : Layout<M, ST, T>::threads(a.ty);
+    const int threads = lean      ? Layout1<M, ST>::threads(a.ty)
+                        : lean_ch ? LayoutCH<ST>::threads(a.ty)
+                                  : Layout<M, ST, T>::threads(a.ty);
     if (threads > kMaxThreads) return cudaErrorInvalidConfiguration;
     if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, threads, smem);
     k<<<grid, threads, smem, st>>>(a);
@@ -971,13 +1213,13 @@ template <class M>
 size_t smem_for(int storage, int tsteps, int ty) {
     if (storage == RD_STORE_F32) {
         switch (tsteps) {
-        case 1: return M::CH ? Layout<M, float, 1>::total(ty) : Layout1<M, float>::total(ty);
+        case 1: return M::CH ? LayoutCH<float>::total(ty) : Layout1<M, float>::total(ty);
         case 2: return Layout<M, float, 2>::total(ty);
         case 3: return Layout<M, float, 3>::total(ty);
         }
     } else {
         switch (tsteps) {
-        case 1: return M::CH ? Layout<M, __nv_bfloat16, 1>::total(ty)
+        case 1: return M::CH ? LayoutCH<__nv_bfloat16>::total(ty)
                              : Layout1<M, __nv_bfloat16>::total(ty);
         case 2: return Layout<M, __nv_bfloat16, 2>::total(ty);
         case 3: return Layout<M, __nv_bfloat16, 3>::total(ty);
