@@ -451,7 +451,7 @@ def run_extras(args, Sim, Batch, torch):
         sm.set_fields(W.initial_fields_torch(c, "cuda"))
     stream = torch.cuda.Stream()
     b = Batch("ch_front", stream=stream)
-    btun = dict(tsteps=1, tile_q=16, tile_y=8, zchunk=32, graph=1)
+    btun = dict(tsteps=1, tile_q=16, tile_y=12, zchunk=32, graph=1)
     b.set_tuning(**btun)
     for sm in sims:
         b.add(sm)

@@ -345,7 +345,8 @@ rd_tuning default_tuning(const rd_config& g) {
     rd_tuning t{};
     t.tsteps = 1;
     t.tile_q = kTileQ;
-    t.tile_y = 16;
+    // the front model's one-step tile of 12 rows fits two CTAs per SM
+    t.tile_y = g.model == RD_MODEL_CH_FRONT ? 12 : 16;
     t.graph = 1;
     const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_y);
     const int occ = occupancy(g.model, g.storage, t.tsteps, sm, threads_of(g.model, t.tsteps, t.tile_y));
@@ -823,7 +824,7 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
     const rd_tuning saved = c->tun;
     std::vector<rd_tuning> cands;
     for (int T = 1; T <= max_tsteps(g.model); ++T)
-        for (int ty : {4, 8, 12, 16, 20, 24, 32}) {
+        for (int ty : {4, 8, 10, 12, 14, 16, 20, 24, 32}) {
           for (int rc = 0; rc <= ((T == 1 && g.model != RD_MODEL_CH_FRONT) ? 1 : 0); ++rc) {
             rd_tuning t{};
             t.tsteps = T; t.tile_q = kTileQ; t.tile_y = ty; t.graph = 1; t.zchunk = 1;

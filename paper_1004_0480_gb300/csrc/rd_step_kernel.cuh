@@ -345,16 +345,33 @@ __device__ __forceinline__ void held_layers(const InstDesc& sd, int s, int xs, i
     }
 }
 
+// Faces of the grid that a thread's 4 cells (x = xs..xs+3, row y, plane
+// q) lie on, as bits in the order of held_mask: -x, +x, -y, +y, -z, +z.
+__device__ __forceinline__ unsigned xy_faces(int xs, int y, int nx, int ny) {
+    return (xs <= 0 && xs + kVEC > 0 ? 1u : 0u) | (xs <= nx - 1 && xs + kVEC > nx - 1 ? 2u : 0u) |
+           (y == 0 ? 4u : 0u) | (y == ny - 1 ? 8u : 0u);
+}
+__device__ __forceinline__ unsigned z_faces(int q, int nz) {
+    return (q == 0 ? 16u : 0u) | (q == nz - 1 ? 32u : 0u);
+}
+
+// held_layers for a thread whose face bits are known: the same result, the
+// per-cell tests run only where a held face is touched
+__device__ __forceinline__ void held_layers_at(const InstDesc& sd, int s, unsigned faces, int xs,
+                                               int y, int q, float (&o)[kVEC]) {
+    if (sd.held_mask[s] & faces) held_layers(sd, s, xs, y, q, o);
+}
+
 // New value of one species on the thread's 4 cells (eq. (5)): reaction
 // increment ``inc`` (dt R), point source, upwind advection, Fickian
-// transport, then held layers.  Shared by every kernel so that all launch
-// shapes give identical bits.
-__device__ __forceinline__ void species_update(const InstDesc& sd, int s, const float (&c)[kVEC],
-                                               const float (&xm)[kVEC], const float (&xp)[kVEC],
-                                               const float (&ym)[kVEC], const float (&yp)[kVEC],
-                                               const float (&zm)[kVEC], const float (&zp)[kVEC],
-                                               const float (&inc)[kVEC], float cx, bool src_here,
-                                               bool px, int xs, int y, int q, float (&o)[kVEC]) {
+// transport; held layers are applied by the caller.  Shared by every
+// kernel so that all launch shapes give identical bits.
+__device__ __forceinline__ void species_core(const InstDesc& sd, int s, const float (&c)[kVEC],
+                                             const float (&xm)[kVEC], const float (&xp)[kVEC],
+                                             const float (&ym)[kVEC], const float (&yp)[kVEC],
+                                             const float (&zm)[kVEC], const float (&zp)[kVEC],
+                                             const float (&inc)[kVEC], float cx, bool src_here,
+                                             bool px, int xs, float (&o)[kVEC]) {
     const float kx = sd.kx[s], ky = sd.ky[s], kz = sd.kz[s];
     const bool src_s = src_here && s == sd.src_s;
     if (cx == 0.0f && !src_s) {
@@ -379,6 +396,16 @@ __device__ __forceinline__ void species_update(const InstDesc& sd, int s, const 
                        : euler_cell(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, ky, kz, in);
         }
     }
+}
+
+// species_core followed by the held layers
+__device__ __forceinline__ void species_update(const InstDesc& sd, int s, const float (&c)[kVEC],
+                                               const float (&xm)[kVEC], const float (&xp)[kVEC],
+                                               const float (&ym)[kVEC], const float (&yp)[kVEC],
+                                               const float (&zm)[kVEC], const float (&zp)[kVEC],
+                                               const float (&inc)[kVEC], float cx, bool src_here,
+                                               bool px, int xs, int y, int q, float (&o)[kVEC]) {
+    species_core(sd, s, c, xm, xp, ym, yp, zm, zp, inc, cx, src_here, px, xs, o);
     held_layers(sd, s, xs, y, q, o);
 }
 
@@ -769,6 +796,7 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
         const int xs = x0 + v * kVEC;
         const bool computes = !halo_warp && y < ny && xs < nx;
         const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
+        const unsigned xyf = xy_faces(xs, y, nx, ny);
         const Fetch fo = halo_warp ? Fetch{0, 0, 0, 0}
                                    : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB, true);
         __syncthreads();   // halo descriptors written
@@ -835,6 +863,7 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                 }
                 const float cx = courant ? courant[zq] : 0.0f;
                 const bool src_here = src_col && zq == sd.src_z;
+                const unsigned faces = xyf | z_faces(q, nz);
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     const unsigned char* Ps = Pc + s * PEB;
@@ -858,8 +887,9 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                             o[e] = euler_cell_iso(cen[s][e], xm[e], xp[e], ym[e], yp[e], zm[e],
                                                   zp[e], k, inc[s][e]);
                     } else {
-                        species_update(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s], cx, src_here,
-                                       px, xs, y, q, o);
+                        species_core(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s], cx, src_here,
+                                     px, xs, o);
+                        held_layers_at(sd, s, faces, xs, y, q, o);
                     }
                     if (computes) Store<ST>::store(gst + s * fstride, o);
                 }
@@ -880,23 +910,24 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
 // cell i at a zero-flux face), so mu computed at a ghost cell equals mu at
 // the face cell -- the paper's "Laplacian, boundary rule, Laplacian" -- and
 // every neighbour sits at a fixed offset.  One thread per 4-cell vector of
-// the tile widened by one vector in x and one row in y: each computes mu
-// there for plane p+1 and, inside the tile, the new state of plane p.  The
-// z and own-vector inputs of the state update (own mu of planes p-1..p+1,
-// own a, b, c) were written by the thread itself; x/y neighbours come from
-// plane p, complete since the last barrier: one barrier per plane.  State
-// planes arrive in an 8-slot ring, 4 in flight; mu planes in a 4-slot ring.
-// Slot reuse: step p refills the slot of state plane p-2, whose neighbour
-// reads (mu of p-2 at step p-3, update of p-2 at step p-2) ended a barrier
-// earlier and whose last read (own vector, update of p-1) precedes the
-// refill in the owner's program order -- every vector is copied by the
-// thread that owns it; the two outer rows are only read as neighbours.  The
-// mu slot written at step p held mu of p-3, last read at step p-2.
+// the tile widened by one vector in x and one row in y: at step p each
+// computes mu of plane p+1 at its position and the new state of plane p.
+// A thread keeps its own mu of planes p-1..p+1 in registers; neighbours'
+// mu of plane p come from a 2-slot shared ring (written at step p-1).
+// State planes arrive in a 6-slot ring, P = 4 copy groups ahead: at step p
+// planes p-1..p+2 are read and p+3, p+4 are in flight.  Slot reuse: step p
+// refills the slot of plane p-2, whose neighbour reads (mu of p-2 at step
+// p-3, update of p-2 at step p-2) ended a barrier earlier and whose last
+// read (own vector, update of p-1) precedes the refill in the owner's
+// program order -- every vector is copied by the thread that owns it; the
+// two outer rows are only read as neighbours.  The mu slot written at step
+// p held mu of p-1, whose last reads were at step p-1.  One barrier per
+// plane.
 template <class ST> struct LayoutCH {
     static constexpr int S = 3;
-    static constexpr int RING = 8;
-    static constexpr int P = 6;
-    static constexpr int MURING = 4;
+    static constexpr int RING = 6;
+    static constexpr int P = 4;
+    static constexpr int MURING = 2;
     __host__ __device__ static int rows(int ty) { return ty + 4; }
     __host__ __device__ static int plane_elems(int ty) { return rows(ty) * kRW + 2 * kVEC; }
     __host__ __device__ static size_t state_bytes(int ty) {
@@ -967,10 +998,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
     constexpr int S = 3;
     constexpr int P = LY::P;
     constexpr int RING = LY::RING;
-    constexpr int MURING = LY::MURING;
     constexpr int EB = (int)sizeof(ST);
     constexpr int RWB = kRW * EB;
-    constexpr int RWF = kRW * (int)sizeof(float);
 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ InstDesc sdm;
@@ -983,8 +1012,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
     const int SLOTB = S * PEB;
     unsigned char* const ring = smem + kVEC * EB;
     float* const muring = reinterpret_cast<float*>(smem + LY::state_bytes(TY)) + kVEC;
-    // thread (r, v): state/mu position row R = r + 1 (rows -1..TY of the
-    // tile), vector v (vectors -1..16)
+    // thread (r, v): position row r - 1 of the tile (rows -1..TY), vector
+    // v - 1 (vectors -1..16)
     const int r = tid / kNQ;
     const int v = tid - r * kNQ;
     const int own = (r + 1) * kRW + v * kVEC;       // element offset in a plane
@@ -1015,6 +1044,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
         const int y = y0 - 1 + r;                     // global row of the position
         const int xs = x0 - kVEC + v * kVEC;          // global x of its first element
         const bool stores = inner && y < ny && xs < nx;
+        const unsigned xyf = xy_faces(xs, y, nx, ny);
+        const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
         // own state vector, and (first 2 x 18 threads) the outer halo rows
         const Fetch fo = make_fetch_mirror<ST>(y, xs, nx, ny, pitch, px, py, own);
         Fetch fx{0, 0, 0, 0};
@@ -1025,25 +1056,27 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                                        pitch, px, py, (bottom ? TY + 3 : 0) * kRW + vv * kVEC);
         }
 
-        // planes z0-2 .. z1+1 are copied, plane index nld into slot nld & 7
-        int nld = z0 - 2;
+        // planes z0-2 .. z1+1 are copied; plane nld goes to slot sld
+        int nld = z0 - 2, sld = 0;
         auto issue = [&]() {
             if (nld <= z1 + 1) {
                 const int zs = pz ? wrapi(nld, nz) : mirror_index(nld, nz);
                 const ST* g = gin + (long long)zs * plane;
-                unsigned char* buf = ring + (nld & (RING - 1)) * SLOTB;
+                unsigned char* buf = ring + sld * SLOTB;
                 fetch_all_mirror<ST, S>(fo, buf, PEB, g, fstride, nx, px);
                 if (tid < 2 * kNQ) fetch_all_mirror<ST, S>(fx, buf, PEB, g, fstride, nx, px);
             }
             ++nld;
+            sld = (sld == RING - 1) ? 0 : sld + 1;
             cp_async_commit();
         };
 #pragma unroll 1
         for (int j = 0; j < P; ++j) issue();
 
         const float* courant = sd.courant;
-        const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
         ST* gst = gout + (long long)z0 * plane + (long long)y * pitch + xs;
+        float mu_m[kVEC] = {}, mu_0[kVEC] = {};       // own mu of planes p-1, p
+        int sc = 0;                                   // ring slot of plane p
 #pragma unroll 1
         for (int p = z0 - 2; p < z1; ++p) {
             // planes through p + 2 must have landed: of the P + (p - z0 + 3)
@@ -1051,16 +1084,16 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
             issue();
             cp_async_wait<P - 2>();
             __syncthreads();
-            // ---- mu of plane p + 1 at every position of the widened tile
-            if (p + 1 >= z0 - 1 && r < TY + 2) {
-                const int q = p + 1;
-                const unsigned char* Cc = ring + (q & (RING - 1)) * SLOTB + 2 * PEB + own_b;
-                const unsigned char* Cm = ring + ((q - 1) & (RING - 1)) * SLOTB + 2 * PEB + own_b;
-                const unsigned char* Cp = ring + ((q + 1) & (RING - 1)) * SLOTB + 2 * PEB + own_b;
-                float c[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], mo[kVEC];
+            const int sm = sc == 0 ? RING - 1 : sc - 1;
+            const int s1 = sc == RING - 1 ? 0 : sc + 1;
+            const int s2 = s1 == RING - 1 ? 0 : s1 + 1;
+            float mu_p[kVEC];                         // own mu of plane p + 1
+            {
+                const unsigned char* Cc = ring + s1 * SLOTB + 2 * PEB + own_b;
+                float c[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC];
                 lds_vec<ST>(Cc, c);
-                lds_vec<ST>(Cm, zm);
-                lds_vec<ST>(Cp, zp);
+                lds_vec<ST>(ring + sc * SLOTB + 2 * PEB + own_b, zm);
+                lds_vec<ST>(ring + s2 * SLOTB + 2 * PEB + own_b, zp);
                 lds_vec<ST>(Cc - RWB, ym);
                 lds_vec<ST>(Cc + RWB, yp);
                 const float left = lds_one<ST>(Cc - EB);
@@ -1069,15 +1102,16 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                 for (int e = 0; e < kVEC; ++e) {
                     const float xm = e ? c[e - 1] : left;
                     const float xp = (e < kVEC - 1) ? c[e + 1] : right;
-                    mo[e] = MChFront::mu(sd, c[e], xm, xp, ym[e], yp[e], zm[e], zp[e]);
+                    mu_p[e] = MChFront::mu(sd, c[e], xm, xp, ym[e], yp[e], zm[e], zp[e]);
                 }
-                Store<float>::store(muring + (q & (MURING - 1)) * PE + own, mo);
+                Store<float>::store(muring + ((p + 1) & 1) * PE + own, mu_p);
             }
-            // ---- new state of plane p inside the tile
-            if (p >= z0 && inner) {
-                const unsigned char* Sc = ring + (p & (RING - 1)) * SLOTB + own_b;
-                const unsigned char* Sm = ring + ((p - 1) & (RING - 1)) * SLOTB + own_b;
-                const unsigned char* Sp = ring + ((p + 1) & (RING - 1)) * SLOTB + own_b;
+            if (p >= z0) {
+                // ---- new state of plane p (every position; stored inside the tile)
+                const unsigned char* Sc = ring + sc * SLOTB + own_b;
+                const unsigned char* Sm = ring + sm * SLOTB + own_b;
+                const unsigned char* Sp = ring + s1 * SLOTB + own_b;
+                const unsigned faces = xyf | z_faces(p, nz);
                 float cen[S][kVEC], inc[S][kVEC];
 #pragma unroll
                 for (int s = 0; s < S; ++s) lds_vec<ST>(Sc + s * PEB, cen[s]);
@@ -1090,6 +1124,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
 #pragma unroll
                     for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
                 }
+                const float cx = courant ? courant[p] : 0.0f;
+                const bool src_here = src_col && p == sd.src_z;
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const unsigned char* Ps = Sc + s * PEB;
@@ -1105,38 +1141,39 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                         xm[e] = e ? cen[s][e - 1] : left;
                         xp[e] = (e < kVEC - 1) ? cen[s][e + 1] : right;
                     }
-                    species_update(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s],
-                                   courant ? courant[p] : 0.0f, src_col && p == sd.src_z, px, xs,
-                                   y, p, o);
+                    species_core(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s], cx, src_here, px,
+                                 xs, o);
+                    held_layers_at(sd, s, faces, xs, y, p, o);
                     if (stores) Store<ST>::store(gst + s * fstride, o);
                 }
                 {
                     // c += dt M / h^2 * (7-point Laplacian of mu)
-                    const float* Mc = muring + (p & (MURING - 1)) * PE + own;
-                    const float* Mm = muring + ((p - 1) & (MURING - 1)) * PE + own;
-                    const float* Mp = muring + ((p + 1) & (MURING - 1)) * PE + own;
-                    float m0[kVEC], mym[kVEC], myp[kVEC], mzm[kVEC], mzp[kVEC], o[kVEC];
-                    Store<float>::load(Mc, m0);
-                    Store<float>::load(Mm, mzm);
-                    Store<float>::load(Mp, mzp);
+                    const float* Mc = muring + (p & 1) * PE + own;
+                    float mym[kVEC], myp[kVEC], o[kVEC];
                     Store<float>::load(Mc - kRW, mym);
                     Store<float>::load(Mc + kRW, myp);
                     const float mleft = Mc[-1];
                     const float mright = Mc[kVEC];
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e) {
-                        const float mxm = e ? m0[e - 1] : mleft;
-                        const float mxp = (e < kVEC - 1) ? m0[e + 1] : mright;
+                        const float mxm = e ? mu_0[e - 1] : mleft;
+                        const float mxp = (e < kVEC - 1) ? mu_0[e + 1] : mright;
                         const float s6 = __fadd_rn(__fadd_rn(__fadd_rn(mxm, mxp), __fadd_rn(mym[e], myp[e])),
-                                                   __fadd_rn(mzm[e], mzp[e]));
-                        const float lap = __fmaf_rn(-6.0f, m0[e], s6);
+                                                   __fadd_rn(mu_m[e], mu_p[e]));
+                        const float lap = __fmaf_rn(-6.0f, mu_0[e], s6);
                         o[e] = __fadd_rn(cen[2][e], __fmaf_rn(sd.p[1], lap, inc[2][e]));
                     }
-                    held_layers(sd, 2, xs, y, p, o);
+                    held_layers_at(sd, 2, faces, xs, y, p, o);
                     if (stores) Store<ST>::store(gst + 2 * fstride, o);
                 }
+                gst += plane;
             }
-            if (p >= z0) gst += plane;
+#pragma unroll
+            for (int e = 0; e < kVEC; ++e) {
+                mu_m[e] = mu_0[e];
+                mu_0[e] = mu_p[e];
+            }
+            sc = s1;
         }
         cp_async_wait<0>();
         __syncthreads();
