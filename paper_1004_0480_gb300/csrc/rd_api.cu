@@ -833,8 +833,15 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
             const size_t sm = smem_of(g.model, g.storage, T, ty);
             const int occ = occupancy(g.model, g.storage, T, sm, threads_of(g.model, T, ty), rc);
             if (occ < 1) continue;
-            for (int waves : {1, 2, 4, 8}) {
-                t.zchunk = auto_zchunk(g, t, occ, waves);
+            // z-chunks for 1, 2, 4, 8 waves of CTAs; for one step per launch
+            // also every split of z into 1..16 chunks, since how evenly the
+            // items fill the CTA slots decides as much as the tile does
+            std::vector<int> zcs;
+            for (int waves : {1, 2, 4, 8}) zcs.push_back(auto_zchunk(g, t, occ, waves));
+            if (T == 1)
+                for (int k = 1; k <= 16; ++k) zcs.push_back((g.nz + k - 1) / k);
+            for (int zc : zcs) {
+                t.zchunk = zc;
                 bool dup = false;
                 for (auto& o : cands)
                     dup |= (o.tsteps == t.tsteps && o.tile_y == t.tile_y && o.zchunk == t.zchunk &&

@@ -801,16 +801,17 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                                    : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB, true);
         __syncthreads();   // halo descriptors written
 
-        // ---- the march: plane nld (ring slot sld) is fetched P planes ahead
-        int nld = z0 - 1, sld = 0;
+        // ---- the march: plane nld is fetched P planes ahead into slot sl;
+        // plane z0 - 1 goes to slot 0, plane q to slot (q - z0 + 1) mod RING
+        int nld = z0 - 1;
         int zld = pz ? wrapi(nld, nz) : nld;      // plane index the copy reads
-        auto issue = [&]() {
+        auto issue = [&](int sl) {
             // zero-flux z: the face plane is copied in as the ghost plane
             const bool in_z = pz || (nld >= 0 && nld < nz);
             if (nld <= z1) {
                 const int zs = in_z ? zld : (nld < 0 ? 0 : nz - 1);
                 const ST* gld = gin + (long long)zs * plane;
-                unsigned char* buf = ring + sld * SLOTB;
+                unsigned char* buf = ring + sl * SLOTB;
                 if (halo_warp) {
                     const int hl = tid - ncomp;
 #pragma unroll
@@ -824,34 +825,43 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                 }
             }
             ++nld;
-            sld = (sld == RING - 1) ? 0 : sld + 1;
             if (!pz) zld = nld;
             else if (++zld == nz) zld = 0;
             cp_async_commit();
         };
 #pragma unroll 1
-        for (int j = 0; j < P; ++j) issue();
+        for (int j = 0; j < P; ++j) issue(j);
         int zq = pz ? wrapi(z0, nz) : z0;       // wrapped index of plane q
-        int sc = 1;                             // ring slot of plane q (z0 - 1 is slot 0)
         ST* gst = gout + (long long)z0 * plane + (long long)y * pitch + xs;
         const float* courant = sd.courant;
+        int sc = 1;                               // ring slot of plane q
+        // own vectors of planes q-1 and q, carried down the march
+        float own_m[S][kVEC], own_0[S][kVEC];
 #pragma unroll 1
         for (int q = z0; q < z1; ++q) {
+            const int sm = sc == 0 ? RING - 1 : sc - 1;
+            const int sp = sc == RING - 1 ? 0 : sc + 1;
             // planes up to q + 1 must have landed: of the P + (q - z0 + 1)
             // groups issued so far, all but the newest P - 2
-            issue();
+            issue(sc >= RING - P + 1 ? sc + P - 1 - RING : sc + P - 1);
             cp_async_wait<P - 2>();
             __syncthreads();
             if (!halo_warp) {
                 // every neighbour at a fixed offset; ghosts were copied in
-                const int sm = sc == 0 ? RING - 1 : sc - 1;
-                const int sp = sc == RING - 1 ? 0 : sc + 1;
                 const unsigned char* Pc = ring + sc * SLOTB + own_b;
-                const unsigned char* Pm = ring + sm * SLOTB + own_b;
                 const unsigned char* Pp = ring + sp * SLOTB + own_b;
-                float cen[S][kVEC], inc[S][kVEC];
+                if (q == z0) {
+                    const unsigned char* Pm = ring + sm * SLOTB + own_b;
 #pragma unroll
-                for (int s = 0; s < S; ++s) lds_vec<ST>(Pc + s * PEB, cen[s]);
+                    for (int s = 0; s < S; ++s) {
+                        lds_vec<ST>(Pm + s * PEB, own_m[s]);
+                        lds_vec<ST>(Pc + s * PEB, own_0[s]);
+                    }
+                }
+                float own_p[S][kVEC], inc[S][kVEC];
+#pragma unroll
+                for (int s = 0; s < S; ++s) lds_vec<ST>(Pp + s * PEB, own_p[s]);
+                auto& cen = own_0;
 #pragma unroll
                 for (int e = 0; e < kVEC; ++e) {
                     float cv[S], iv[S];
@@ -867,9 +877,9 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     const unsigned char* Ps = Pc + s * PEB;
-                    float xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], o[kVEC];
-                    lds_vec<ST>(Pm + s * PEB, zm);
-                    lds_vec<ST>(Pp + s * PEB, zp);
+                    float xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], o[kVEC];
+                    const float (&zm)[kVEC] = own_m[s];
+                    const float (&zp)[kVEC] = own_p[s];
                     lds_vec<ST>(Ps - RWB, ym);
                     lds_vec<ST>(Ps + RWB, yp);
                     const float left = lds_one<ST>(Ps - EB);
@@ -893,9 +903,16 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                     }
                     if (computes) Store<ST>::store(gst + s * fstride, o);
                 }
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+#pragma unroll
+                    for (int e = 0; e < kVEC; ++e) {
+                        own_m[s][e] = own_0[s][e];
+                        own_0[s][e] = own_p[s][e];
+                    }
             }
             gst += plane;
-            sc = (sc == RING - 1) ? 0 : sc + 1;
+            sc = sc == RING - 1 ? 0 : sc + 1;
             if (!pz) zq = q + 1;
             else if (++zq == nz) zq = 0;
         }
@@ -903,7 +920,6 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
         __syncthreads();
     }
 }
-
 // -------------------------------------------- one-step Cahn-Hilliard kernel
 // The T = 1 path of the front model (a + b -> c, Cahn-Hilliard c).  Ghost
 // cells are copied in by mirror extension to distance two (index -1-i holds
@@ -1198,6 +1214,7 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
     } else {
         k = rd_step_kernel<M, ST, T, ONE>;
     }
+    // dynamic shared memory granted so far, per kernel variant
     static size_t configured[4] = {0, 0, 0, 0};
     size_t& conf = configured[(lean && a.regcap ? 1 : 0) + (lean && a.plain ? 2 : 0)];
     if (smem > conf) {

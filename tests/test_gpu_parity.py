@@ -80,6 +80,11 @@ TILINGS = [
     dict(tsteps=3, tile_q=16, tile_y=3, zchunk=4, graph=1),
     dict(tsteps=2, tile_q=16, tile_y=8, zchunk=19, graph=1),
     dict(tsteps=1, tile_q=16, tile_y=16, zchunk=8, graph=1),
+    # 64-register one-step kernel, tile heights with compile-time variants;
+    # z-chunks of 7 and 6 planes end inside and at the end of the unrolled
+    # 6-plane groups
+    dict(tsteps=1, tile_q=16, tile_y=8, zchunk=7, graph=1, regcap=1),
+    dict(tsteps=1, tile_q=16, tile_y=16, zchunk=6, graph=0, regcap=1),
 ]
 
 
