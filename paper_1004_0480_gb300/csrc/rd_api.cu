@@ -245,6 +245,8 @@ rd_status validate(const rd_config* c) {
     }
     if (c->wind_kind < RD_WIND_NONE || c->wind_kind > RD_WIND_CONST)
         return fail(nullptr, RD_EINVAL, "unknown wind kind");
+    if (c->wind_kind != RD_WIND_NONE && !std::isfinite(c->wind_u0))
+        return fail(nullptr, RD_EINVAL, "wind speed must be finite");
     if (c->src_species >= 0) {
         if (c->src_species >= c->nspecies || c->src_x < 0 || c->src_x >= c->nx || c->src_y < 0 ||
             c->src_y >= c->ny || c->src_z < 0 || c->src_z >= c->nz)

@@ -217,12 +217,6 @@ __device__ __forceinline__ float euler_cell_iso(float c, float xm, float xp, flo
     return __fadd_rn(c, __fmaf_rn(k, lap, inc));
 }
 
-// First-order upwind advection increment for Courant number cx = u dt / h.
-__device__ __forceinline__ float upwind(float inc, float cx, float c, float xm, float xp) {
-    return cx >= 0.0f ? __fmaf_rn(-cx, __fsub_rn(c, xm), inc)
-                      : __fmaf_rn(-cx, __fsub_rn(xp, c), inc);
-}
-
 // ------------------------------------------------------- shared-memory map
 // Every level keeps its planes in shared memory; slots are the low bits of
 // the plane index.  Level 0 is a ring of 8 planes per species, P of them in
@@ -374,27 +368,32 @@ __device__ __forceinline__ void species_core(const InstDesc& sd, int s, const fl
                                              bool px, int xs, float (&o)[kVEC]) {
     const float kx = sd.kx[s], ky = sd.ky[s], kz = sd.kz[s];
     const bool src_s = src_here && s == sd.src_s;
-    if (cx == 0.0f && !src_s) {
-        if (kx == ky && kx == kz) {
+    const bool iso = kx == ky && kx == kz;
+    // every test below is uniform over the 4 cells: taken once, not per cell
+    float in[kVEC];
 #pragma unroll
-            for (int e = 0; e < kVEC; ++e)
-                o[e] = euler_cell_iso(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, inc[e]);
-        } else {
+    for (int e = 0; e < kVEC; ++e) in[e] = inc[e];
+    if (src_s) {
 #pragma unroll
-            for (int e = 0; e < kVEC; ++e)
-                o[e] = euler_cell(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, ky, kz, inc[e]);
-        }
+        for (int e = 0; e < kVEC; ++e)
+            if ((px ? wrapi(xs + e, sd.nx) : xs + e) == sd.src_x) in[e] = __fadd_rn(in[e], sd.src_amt);
+    }
+    // first-order upwind advection, Courant number cx = u dt / h
+    if (cx > 0.0f) {
+#pragma unroll
+        for (int e = 0; e < kVEC; ++e) in[e] = __fmaf_rn(-cx, __fsub_rn(c[e], xm[e]), in[e]);
+    } else if (cx < 0.0f) {
+#pragma unroll
+        for (int e = 0; e < kVEC; ++e) in[e] = __fmaf_rn(-cx, __fsub_rn(xp[e], c[e]), in[e]);
+    }
+    if (iso) {
+#pragma unroll
+        for (int e = 0; e < kVEC; ++e)
+            o[e] = euler_cell_iso(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, in[e]);
     } else {
 #pragma unroll
-        for (int e = 0; e < kVEC; ++e) {
-            float in = inc[e];
-            if (src_s && (px ? wrapi(xs + e, sd.nx) : xs + e) == sd.src_x)
-                in = __fadd_rn(in, sd.src_amt);
-            if (cx != 0.0f) in = upwind(in, cx, c[e], xm[e], xp[e]);
-            o[e] = (kx == ky && kx == kz)
-                       ? euler_cell_iso(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, in)
-                       : euler_cell(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, ky, kz, in);
-        }
+        for (int e = 0; e < kVEC; ++e)
+            o[e] = euler_cell(c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e], kx, ky, kz, in[e]);
     }
 }
 
