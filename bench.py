@@ -513,14 +513,14 @@ def run_serving(args):
     rate = args.serve_load * cap / mean_work
     reqs = SV.with_rate(reqs, rate, seed=4)
     server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
-                       quantum=args.serve_quantum)
+                       quantum=args.serve_quantum, run_cells=args.serve_run_cells)
     res_b, st_b = server.run(reqs)
     server.engine.shutdown()
     res_p, st_p = SV.serve_plain(SV.CudaEngine(), reqs)
     # capacity: the first requests of the stream all arriving at once
     sat = [SV.Request(r.id, 0.0, r.cfg) for r in reqs[: args.serve_sat_requests]]
     server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
-                       quantum=args.serve_quantum)
+                       quantum=args.serve_quantum, run_cells=args.serve_run_cells)
     _, sat_b = server.run(sat)
     server.engine.shutdown()
     _, sat_p = SV.serve_plain(SV.CudaEngine(), sat)
@@ -528,12 +528,14 @@ def run_serving(args):
     def pack(st):
         return {"p50_s": st.p50, "p99_s": st.p99, "mean_s": st.mean, "glups": st.glups,
                 "makespan_s": st.makespan, "max_active": st.max_active,
+                "max_running": st.max_running,
                 "max_device_bytes": st.max_bytes, "gpu_launches": st.launches}
     line = {
         "metric": "serving latency p50/p99 (s) and aggregate GLUPS", "unit": "s",
         "requests": len(reqs), "arrival_rate_per_s": rate, "offered_load": args.serve_load,
         "plain_capacity_glups": cap / 1e9, "budget_gb": args.serve_budget_gb,
-        "quantum_steps": args.serve_quantum, "data": "synthetic",
+        "quantum_steps": args.serve_quantum, "run_cells": args.serve_run_cells,
+        "data": "synthetic",
         "config": {"workload": "serving: Poisson arrivals, diffusion/brusselator/ch_front "
                                "kinetics, edges {32..384}^3, 100..5000 steps", "seed": 4},
         "continuous_batching": pack(st_b), "plain": pack(st_p),
@@ -569,6 +571,8 @@ def main():
                     help="offered load as a fraction of the plain stepper's capacity")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-quantum", type=int, default=250)
+    ap.add_argument("--serve-run-cells", type=float, default=48e6,
+                    help="cells the running requests hold together (inf: all admitted run)")
     ap.add_argument("--serve-sat-requests", type=int, default=100,
                     help="requests of the saturated (all arrive at once) capacity run")
     args = ap.parse_args()

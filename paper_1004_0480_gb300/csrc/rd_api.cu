@@ -15,9 +15,10 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <utility>
+#include <vector>
 #include <string>
 #include <thread>
-#include <vector>
 
 #include "rd.h"
 #include "rd_internal.h"
@@ -343,16 +344,44 @@ rd_status check_tuning(const rd_config& g, const rd_tuning& t) {
     return RD_OK;
 }
 
+// z-chunk for problems of (x-y tile columns, nz) sharing ``slots`` resident
+// CTAs: the fewest waves of work items times the planes an item marches
+// (its chunk plus about three planes of pipeline start), ties to the
+// longer chunk.  A wave that is barely filled costs as much as a full one.
+int wave_zchunk(const std::vector<std::pair<long long, int>>& cols_nz, long long slots) {
+    int maxnz = 1;
+    for (auto& p : cols_nz) maxnz = std::max(maxnz, p.second);
+    int best = maxnz;
+    double best_cost = -1.0;
+    for (int zc : {8, 12, 16, 20, 24, 32, 40, 48, 64, 86, 96, 128, 192, 256, 384, 512}) {
+        const int z = std::min(zc, maxnz);
+        long long items = 0;
+        for (auto& p : cols_nz) items += p.first * tiles(p.second, std::min(z, p.second));
+        const long long waves = (items + slots - 1) / std::max<long long>(slots, 1);
+        const double cost = (double)waves * (z + 3);
+        if (best_cost < 0 || cost < best_cost || (cost == best_cost && z > best)) {
+            best_cost = cost;
+            best = z;
+        }
+        if (z == maxnz) break;
+    }
+    return best;
+}
+
+// Default tile height of the one-step kernels: 14 rows (12 for the front
+// model, whose kernel keeps more planes) fit two CTAs per SM.
+int default_tile_y(int model) { return model == RD_MODEL_CH_FRONT ? 12 : 14; }
+
 rd_tuning default_tuning(const rd_config& g) {
     rd_tuning t{};
     t.tsteps = 1;
     t.tile_q = kTileQ;
-    // the front model's one-step tile of 12 rows fits two CTAs per SM
-    t.tile_y = g.model == RD_MODEL_CH_FRONT ? 12 : 16;
+    t.tile_y = default_tile_y(g.model);
     t.graph = 1;
     const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_y);
     const int occ = occupancy(g.model, g.storage, t.tsteps, sm, threads_of(g.model, t.tsteps, t.tile_y));
-    t.zchunk = auto_zchunk(g, t, occ, 1);
+    const long long cols = (long long)tiles(g.nx, t.tile_q * vec_of(g.storage)) * tiles(g.ny, t.tile_y);
+    t.zchunk = wave_zchunk({{cols, g.nz}}, (long long)std::max(occ, 1) * num_sms());
     return t;
 }
 
@@ -974,14 +1003,24 @@ rd_status rd_batch_set_tuning(rd_batch* b, const rd_tuning* t) {
 
 namespace {
 
+// The batch's tuning: the one set by rd_batch_set_tuning, else one step per
+// launch at the default tile height with a z-chunk that fills the CTA slots
+// over all current members.
 rd_tuning batch_tuning(rd_batch* b) {
     if (b->tun_set) return b->tun;
     rd_tuning t{};
     t.tsteps = 1;
     t.tile_q = kTileQ;
-    t.tile_y = 8;
+    t.tile_y = default_tile_y(b->model);
     t.graph = 1;
-    t.zchunk = 32;
+    const size_t sm = smem_of(b->model, b->storage, 1, t.tile_y);
+    const int occ = occupancy(b->model, b->storage, 1, sm, threads_of(b->model, 1, t.tile_y));
+    std::vector<std::pair<long long, int>> cols_nz;
+    for (rd_ctx* c : b->members)
+        cols_nz.push_back({(long long)tiles(c->cfg.nx, t.tile_q * vec_of(b->storage)) *
+                               tiles(c->cfg.ny, t.tile_y),
+                           c->cfg.nz});
+    t.zchunk = cols_nz.empty() ? 32 : wave_zchunk(cols_nz, (long long)std::max(occ, 1) * num_sms());
     return t;
 }
 
@@ -1051,6 +1090,18 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
 rd_status rd_batch_step(rd_batch* b, int64_t nsteps) {
     if (!b || nsteps < 0) return RD_EINVAL;
     if (b->members.empty() || nsteps == 0) return RD_OK;
+    if (b->members.size() == 1) {
+        // a batch of one steps its member as a single context does (its own
+        // tuning, descriptor in the kernel parameters), on the batch's stream
+        rd_ctx* c = b->members[0];
+        cudaStream_t own = c->stream;
+        const int64_t before = c->launches;
+        c->stream = b->stream;
+        rd_status st = step_ctx(c, nsteps);
+        c->stream = own;
+        b->launches += c->launches - before;
+        return st;
+    }
     const rd_tuning t = batch_tuning(b);
     rd_status st = check_tuning(b->members[0]->cfg, t);
     if (st != RD_OK) return st;

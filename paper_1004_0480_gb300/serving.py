@@ -2,12 +2,20 @@
 
 Requests (a problem, an arrival time, a step count) arrive over time.  The
 server admits them in arrival order as soon as their device memory fits a
-budget, keeps their state resident, and advances all admitted requests of
-one kinetics family together with one batched launch sequence per tick
+budget and keeps their state resident.  The oldest admitted requests, up to
+``run_cells`` cells in all (at least one request), are running: those of one
+kinetics family advance together with one batched launch sequence per tick
 (``rd_batch_step``), each family on its own stream so the families' kernels
 overlap on the device.  A request is retired the moment its step count is
-reached; its memory is freed and the next arrivals can be admitted.  Reports
-per-request latency (finish - arrival), p50/p99 and aggregate GLUPS.
+reached; its memory is freed, the next admitted requests start running and
+the next arrivals can be admitted.  Reports per-request latency (finish -
+arrival), p50/p99 and aggregate GLUPS.
+
+The running set is a first-come-first-served prefix sized to fill the GPU:
+small requests share it (batching is what gets them past the launch-bound
+regime of one small grid), while a request that fills the GPU by itself
+runs nearly alone instead of being slowed by everything admitted after it,
+as it would be if every admitted request advanced at once.
 
 ``serve_plain`` is the baseline: one request at a time in arrival order,
 each stepped alone by the plain stepper (the fused kernel at one step per
@@ -74,6 +82,7 @@ class Stats:
     max_bytes: int
     max_active: int
     launches: int = 0
+    max_running: int = 0
     extra: dict = field(default_factory=dict)
 
 
@@ -88,14 +97,15 @@ def percentile(xs, q):
     return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
 
 
-def summarize(results, makespan, max_bytes, max_active, launches=0):
+def summarize(results, makespan, max_bytes, max_active, launches=0, max_running=0):
     lat = [r.latency for r in results]
     work = sum(r.cells * r.steps for r in results)
     return Stats(n=len(results), makespan=makespan,
                  glups=work / makespan / 1e9 if makespan > 0 else float("nan"),
                  p50=percentile(lat, 50), p99=percentile(lat, 99),
                  mean=float(np.mean(lat)) if lat else float("nan"),
-                 max_bytes=max_bytes, max_active=max_active, launches=launches)
+                 max_bytes=max_bytes, max_active=max_active, launches=launches,
+                 max_running=max_running)
 
 
 # --------------------------------------------------------------- engines
@@ -114,6 +124,7 @@ class CudaEngine:
         self.batch_tuning = batch_tuning or {}
         self.batches = {}
         self.streams = {}
+        self.running = set()
 
     def bytes_for(self, req):
         st, sc = self._query(req.cfg, self.storage)
@@ -129,18 +140,21 @@ class CudaEngine:
         return sim
 
     def open(self, req):
-        sim = self._new_sim(req)
-        fam = req.family
-        if fam not in self.batches:
+        """Admit: allocate the request's state and set its initial fields."""
+        return self._new_sim(req)
+
+    def start(self, family, handle):
+        """The request joins its family's batch and advances from now on."""
+        if family not in self.batches:
             s = self._torch.cuda.Stream()
-            b = self._Batch(fam, self.storage, stream=s)
-            tun = self.batch_tuning.get(fam)
+            b = self._Batch(family, self.storage, stream=s)
+            tun = self.batch_tuning.get(family)
             if tun:
                 b.set_tuning(**tun)
-            self.batches[fam] = b
-            self.streams[fam] = s
-        self.batches[fam].add(sim)
-        return sim
+            self.batches[family] = b
+            self.streams[family] = s
+        self.batches[family].add(handle)
+        self.running.add(id(handle))
 
     def step(self, family, n):
         self.batches[family].step(n)
@@ -154,7 +168,9 @@ class CudaEngine:
         return handle.get_fields()
 
     def close(self, family, handle):
-        self.batches[family].remove(handle)
+        if id(handle) in self.running:
+            self.batches[family].remove(handle)
+            self.running.discard(id(handle))
         handle.close()
 
     def launches(self):
@@ -181,18 +197,23 @@ class CudaEngine:
 class Server:
     """Continuous batching under a device-memory budget.
 
-    ``quantum``  steps per tick for a family batch (a tick never steps a
-                 request past its count: the batch advances by the smallest
-                 remaining count if that is smaller)
-    ``budget``   bytes of device memory the admitted requests may hold
-    ``clock``    seconds (monotonic); ``sleep`` waits for the next arrival
+    ``quantum``    steps per tick for a family batch (a tick never steps a
+                   request past its count: the batch advances by the smallest
+                   remaining count if that is smaller)
+    ``budget``     bytes of device memory the admitted requests may hold
+    ``run_cells``  cells the running requests may hold together: requests
+                   start in admission order while the running ones hold
+                   fewer (so the oldest always runs); ``inf`` runs every
+                   admitted request at once
+    ``clock``      seconds (monotonic); ``sleep`` waits for the next arrival
     """
 
-    def __init__(self, engine, budget_bytes=120e9, quantum=200, clock=time.perf_counter,
-                 sleep=time.sleep):
+    def __init__(self, engine, budget_bytes=120e9, quantum=200, run_cells=48e6,
+                 clock=time.perf_counter, sleep=time.sleep):
         self.engine = engine
         self.budget = float(budget_bytes)
         self.quantum = int(quantum)
+        self.run_cells = float(run_cells)
         self.clock = clock
         self.sleep = sleep
 
@@ -201,13 +222,14 @@ class Server:
         for r in pending:
             if self.engine.bytes_for(r) > self.budget:
                 raise ValueError(f"request {r.id} alone exceeds the memory budget")
-        active = collections.OrderedDict()       # family -> list of slots
+        admitted = []            # slots in admission order
         results = []
         used = 0
         max_used = 0
         max_active = 0
+        max_running = 0
         t0 = self.clock()
-        while pending or any(active.values()):
+        while pending or admitted:
             now = self.clock() - t0
             # ---- admit arrivals, first come first served, while memory allows
             while pending and pending[0].arrival <= now:
@@ -219,48 +241,51 @@ class Server:
                 handle = self.engine.open(req)
                 used += need
                 max_used = max(max_used, used)
-                active.setdefault(req.family, []).append(
-                    dict(req=req, handle=handle, left=req.steps, bytes=need,
-                         admitted=self.clock() - t0))
-            n_active = sum(len(v) for v in active.values())
-            max_active = max(max_active, n_active)
-            if n_active == 0:
+                admitted.append(dict(req=req, handle=handle, left=req.steps, bytes=need,
+                                     admitted=self.clock() - t0, running=False))
+            max_active = max(max_active, len(admitted))
+            if not admitted:
                 if pending:
                     wait = pending[0].arrival - (self.clock() - t0)
                     if wait > 0:
                         self.sleep(wait)
                 continue
-            # ---- one tick: every family batch advances (asynchronously)
-            stepped = []
-            for fam, slots in active.items():
-                if not slots:
-                    continue
+            # ---- the running set: the oldest admitted requests up to run_cells
+            cells = 0
+            for s in admitted:
+                if cells >= self.run_cells:
+                    break
+                if not s["running"]:
+                    self.engine.start(s["req"].family, s["handle"])
+                    s["running"] = True
+                cells += s["req"].cells
+            running = [s for s in admitted if s["running"]]
+            max_running = max(max_running, len(running))
+            # ---- one tick: every family's running batch advances (asynchronously)
+            by_family = collections.OrderedDict()
+            for s in running:
+                by_family.setdefault(s["req"].family, []).append(s)
+            for fam, slots in by_family.items():
                 n = min(self.quantum, min(s["left"] for s in slots))
                 self.engine.step(fam, n)
                 for s in slots:
                     s["left"] -= n
-                stepped.append(fam)
             # ---- end of tick: wait for the device (the host admits the next
             # arrivals between ticks), then retire what is done
             self.engine.sync()
             finished = self.clock() - t0
-            for fam in stepped:
-                slots = active[fam]
-                done = [s for s in slots if s["left"] == 0]
-                if not done:
-                    continue
-                for s in done:
-                    req = s["req"]
-                    fields = self.engine.result(s["handle"]) if collect_fields else None
-                    results.append(Result(req.id, req.arrival, s["admitted"], finished, req.steps,
-                                          req.cells, fields))
-                    self.engine.close(fam, s["handle"])
-                    used -= s["bytes"]
-                    slots.remove(s)
+            for s in [s for s in running if s["left"] == 0]:
+                req = s["req"]
+                fields = self.engine.result(s["handle"]) if collect_fields else None
+                results.append(Result(req.id, req.arrival, s["admitted"], finished, req.steps,
+                                      req.cells, fields))
+                self.engine.close(req.family, s["handle"])
+                used -= s["bytes"]
+                admitted.remove(s)
         self.engine.sync()
         makespan = self.clock() - t0
         launches = self.engine.launches()
-        return results, summarize(results, makespan, max_used, max_active, launches)
+        return results, summarize(results, makespan, max_used, max_active, launches, max_running)
 
 
 def serve_plain(engine, requests, collect_fields=False, clock=time.perf_counter,

@@ -214,6 +214,34 @@ def test_batch_members_join_at_different_times(rd):
     Bs.close()
 
 
+def test_batch_of_one_with_odd_step_counts(rd):
+    # a batch of one steps its member as a single context (graph replays
+    # start from level 0); members then join and leave between odd counts
+    a_cfg = W.air((40, 18, 22), src=(3, 4, 5), seed=7)
+    b_cfg = W.air((70, 10, 13), src=(1, 2, 3), seed=8)
+    fa, fb = W.initial_fields(a_cfg), W.initial_fields(b_cfg)
+    ra = run_gpu(rd, a_cfg, 57, fields=fa)
+    rb = run_gpu(rd, b_cfg, 38, fields=fb)
+    A, Bs = rd.Sim(a_cfg), rd.Sim(b_cfg)
+    A.set_fields(fa)
+    Bs.set_fields(fb)
+    bt = rd.Batch("air")
+    bt.add(A)
+    bt.step(7)
+    bt.step(20)
+    bt.step(9)
+    bt.add(Bs)
+    bt.step(21)
+    bt.remove(A)
+    bt.step(17)
+    bt.sync()
+    assert np.array_equal(A.get_fields(), ra)
+    assert np.array_equal(Bs.get_fields(), rb)
+    bt.close()
+    A.close()
+    Bs.close()
+
+
 # ------------------------------------------------------------ reductions
 def test_mass_reduction_fp64(rd):
     cfg = W.diffusion_blob(shape=(37, 29, 23))

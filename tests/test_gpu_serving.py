@@ -20,12 +20,15 @@ def serving():
     return serving
 
 
-def test_mix_equals_alone(serving):
+@pytest.mark.parametrize("run_cells", [float("inf"), 60_000])
+def test_mix_equals_alone(serving, run_cells):
+    # run_cells 60 000: requests join running batches one after another
     specs = W.serving_requests(count=10, rate_per_s=400.0, seed=11, edges=(24, 33, 48, 64),
                                steps_lo=10, steps_hi=90)
     reqs = serving.requests_from_workload(specs)
     eng = serving.CudaEngine()
-    res, st = serving.Server(eng, budget_bytes=2e9, quantum=13).run(reqs, collect_fields=True)
+    res, st = serving.Server(eng, budget_bytes=2e9, quantum=13,
+                             run_cells=run_cells).run(reqs, collect_fields=True)
     eng.shutdown()
     alone, _ = serving.serve_plain(serving.CudaEngine(), reqs, collect_fields=True)
     by_id = {r.id: r for r in alone}

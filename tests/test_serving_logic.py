@@ -24,7 +24,8 @@ class FakeEngine:
 
     def __init__(self, clock, rate=1e6):
         self.clock, self.rate = clock, rate
-        self.members = {}
+        self.members = {}        # family -> running requests
+        self.step_log = []       # (family, n, ids of the running requests)
         self.pending = {}
         self.used = 0
         self.peak = 0
@@ -37,14 +38,17 @@ class FakeEngine:
         return req.cells * req.cfg["nspecies"] * 8
 
     def open(self, req):
-        self.members.setdefault(req.family, []).append(req)
         self.used += self.bytes_for(req)
         self.peak = max(self.peak, self.used)
         self.admit_order.append(req.id)
         self.steps_done[req.id] = 0
         return req
 
+    def start(self, fam, handle):
+        self.members.setdefault(fam, []).append(handle)
+
     def step(self, fam, n):
+        self.step_log.append((fam, n, sorted(r.id for r in self.members[fam])))
         work = sum(r.cells for r in self.members[fam]) * n
         self.pending[fam] = self.pending.get(fam, 0.0) + work / self.rate
         for r in self.members[fam]:
@@ -60,7 +64,8 @@ class FakeEngine:
         return None
 
     def close(self, fam, handle):
-        self.members[fam].remove(handle)
+        if handle in self.members.get(fam, []):
+            self.members[fam].remove(handle)
         self.used -= self.bytes_for(handle)
 
     def launches(self):
@@ -124,6 +129,42 @@ def test_batching_beats_serial_plain_on_the_fake_engine():
     _, plain = serve_plain(FakeEngine(c2), reqs, clock=c2, sleep=c2.sleep)
     assert batched.makespan < plain.makespan
     assert batched.p99 <= plain.p99
+
+
+def test_running_set_is_the_oldest_requests_up_to_run_cells():
+    clk = FakeClock()
+    eng = FakeEngine(clk)
+    # 10^3 cells each; request 0 needs 10 steps, the others 30
+    reqs = [mk(i, 0.0, 10, 10 if i == 0 else 30) for i in range(4)]
+    res, st = Server(eng, budget_bytes=1e12, quantum=10, run_cells=2500, clock=clk,
+                     sleep=clk.sleep).run(reqs)
+    # first tick: 0, 1, 2 (2000 cells < 2500 before 2 joins, 3000 after)
+    assert eng.step_log[0] == ("brusselator", 10, [0, 1, 2])
+    # request 0 retired after that tick; 3 joins the running set
+    assert eng.step_log[1] == ("brusselator", 10, [1, 2, 3])
+    assert st.max_active == 4 and st.max_running == 3
+    assert all(eng.steps_done[r.id] == r.steps for r in reqs)
+
+
+def test_a_request_that_fills_the_gpu_runs_alone_in_arrival_order():
+    clk = FakeClock()
+    eng = FakeEngine(clk)
+    reqs = [mk(i, 0.001 * i, 10, 20 + i, ["brusselator", "ch_front"][i % 2]) for i in range(5)]
+    res, st = Server(eng, budget_bytes=1e12, quantum=8, run_cells=1000, clock=clk,
+                     sleep=clk.sleep).run(reqs)
+    assert st.max_running == 1
+    assert [r.id for r in sorted(res, key=lambda r: r.finished)] == list(range(5))
+    assert all(len(ids) == 1 for _, _, ids in eng.step_log)
+
+
+def test_unbounded_running_set_advances_every_admitted_request():
+    clk = FakeClock()
+    eng = FakeEngine(clk)
+    reqs = [mk(i, 0.0, 10, 50) for i in range(6)]
+    _, st = Server(eng, budget_bytes=1e12, quantum=25, run_cells=float("inf"), clock=clk,
+                   sleep=clk.sleep).run(reqs)
+    assert st.max_running == 6
+    assert eng.step_log[0] == ("brusselator", 25, list(range(6)))
 
 
 def test_percentiles():
