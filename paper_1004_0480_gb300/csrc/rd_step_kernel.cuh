@@ -675,8 +675,9 @@ __device__ __forceinline__ Fetch make_fetch(int yrow, int xs, int nx, int ny, in
     return f;
 }
 
-// one fetch of every species of a plane; ``wrap`` is true only for periodic
-// x with nx not a multiple of 4, the one case where mode 2 occurs
+// one fetch of every species of a plane; ``elems`` is true where mode 2 can
+// occur (zero-flux x faces, periodic x with nx not a multiple of 4); its
+// element copies are 4-byte async copies for FP32, plain loads for BF16
 template <class ST, int S>
 __device__ __forceinline__ void fetch_all(const Fetch& f, unsigned char* plane_buf, int pe_bytes,
                                           const ST* gplane, long long fstride, int nx,
@@ -693,7 +694,7 @@ __device__ __forceinline__ void fetch_all(const Fetch& f, unsigned char* plane_b
             for (int e = 0; e < kVEC; ++e) {
                 const int x = f.xs + e;
                 const int xi = px ? wrapi(x, nx) : (x < 0 ? 0 : (x >= nx ? nx - 1 : x));
-                d[e] = gplane[s * fstride + f.goff + xi];
+                Store<ST>::cp_async_elem(d + e, gplane + s * fstride + f.goff + xi);
             }
         }
     }
