@@ -243,6 +243,12 @@ rd_status validate(const rd_config* c) {
                 return fail(nullptr, RD_EUNSUPPORTED, "no held layer on the Cahn-Hilliard species");
         if (c->D[2][0] != 0 || c->D[2][1] != 0 || c->D[2][2] != 0)
             return fail(nullptr, RD_EUNSUPPORTED, "the Cahn-Hilliard species has no Fickian term");
+        // the front problem (Section 4.1, Table 1) has no wind, and the
+        // Cahn-Hilliard species moves only by its chemical potential
+        if (c->wind_kind != RD_WIND_NONE)
+            return fail(nullptr, RD_EUNSUPPORTED, "the front model has no advection");
+        if (c->src_species == 2)
+            return fail(nullptr, RD_EUNSUPPORTED, "no point source on the Cahn-Hilliard species");
     }
     if (c->wind_kind < RD_WIND_NONE || c->wind_kind > RD_WIND_CONST)
         return fail(nullptr, RD_EINVAL, "unknown wind kind");
@@ -442,13 +448,16 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
 
 long long items_of(const InstDesc& d) { return (long long)d.ntx * d.nty * d.nzc; }
 
-// No held layer, point source or wind, and every species isotropic: the
-// one-step kernel's branch-free update applies.
+// No point source or wind, every species isotropic and, except for the front
+// model (whose one-step kernel applies held layers on this path too), no
+// held layer: the one-step kernels' branch-free update applies.
 bool plain_problem(const rd_config& g) {
     if (g.wind_kind != RD_WIND_NONE || g.src_species >= 0) return false;
+    // the front kernel's plain path still applies held layers
+    const bool held_ok = g.model == RD_MODEL_CH_FRONT;
     for (int s = 0; s < g.nspecies; ++s) {
         for (int f = 0; f < 6; ++f)
-            if (g.bc[s][f] == RD_BC_DIRICHLET) return false;
+            if (g.bc[s][f] == RD_BC_DIRICHLET && !held_ok) return false;
         if (g.D[s][0] != g.D[s][1] || g.D[s][0] != g.D[s][2]) return false;
     }
     return true;

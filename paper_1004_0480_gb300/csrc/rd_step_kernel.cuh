@@ -962,33 +962,48 @@ __device__ __forceinline__ int mirror_index(int i, int n) {
     return min(max(m, 0), n - 1);
 }
 
+// How one vector of the front kernel is fetched: 1 = one async copy, 2 =
+// element by element from the precomputed in-row offsets e[] (a vector
+// crossing a face: mirror-extended or wrapped elements), 0 = nothing.
+struct FetchM {
+    int mode;
+    int goff;    // element offset of the row (+ x for mode 1) within a plane
+    int soff;    // byte offset of the position within a plane buffer
+    int e[kVEC]; // mode 2: element offsets within the row
+};
+
 // Fetch with mirror-extended (zero-flux) or wrapped (periodic) coordinates.
 // Vectors past row ny + 1 or column nx + 1 feed no stored cell: not copied.
 template <class ST>
-__device__ __forceinline__ Fetch make_fetch_mirror(int yrow, int xs, int nx, int ny, int pitch,
-                                                   bool px, bool py, int soff_elems) {
-    Fetch f{0, 0, soff_elems * (int)sizeof(ST), xs};
+__device__ __forceinline__ FetchM make_fetch_mirror(int yrow, int xs, int nx, int ny, int pitch,
+                                                    bool px, bool py, int soff_elems) {
+    FetchM f{0, 0, soff_elems * (int)sizeof(ST), {0, 0, 0, 0}};
     if (yrow > ny + 1 || xs > nx + 1) return f;
     const int yw = py ? wrapi(yrow, ny) : mirror_index(yrow, ny);
     const int row = yw * pitch;
+    f.goff = row;
     if (xs >= 0 && xs + kVEC <= nx) {
         f.mode = 1;
         f.goff = row + xs;
-    } else if (px) {
-        const int xw = wrapi(xs, nx);
-        if (xw % kVEC == 0 && xw + kVEC <= nx) { f.mode = 1; f.goff = row + xw; }
-        else { f.mode = 2; f.goff = row; }
-    } else {
-        f.mode = 2;
-        f.goff = row;
+        return f;
     }
+    if (px) {
+        const int xw = wrapi(xs, nx);
+        if (xw % kVEC == 0 && xw + kVEC <= nx) {
+            f.mode = 1;
+            f.goff = row + xw;
+            return f;
+        }
+    }
+    f.mode = 2;
+#pragma unroll
+    for (int e = 0; e < kVEC; ++e) f.e[e] = px ? wrapi(xs + e, nx) : mirror_index(xs + e, nx);
     return f;
 }
 
 template <class ST, int S>
-__device__ __forceinline__ void fetch_all_mirror(const Fetch& f, unsigned char* plane_buf,
-                                                 int pe_bytes, const ST* gplane, long long fstride,
-                                                 int nx, bool px) {
+__device__ __forceinline__ void fetch_all_mirror(const FetchM& f, unsigned char* plane_buf,
+                                                 int pe_bytes, const ST* gplane, long long fstride) {
 #pragma unroll
     for (int s = 0; s < S; ++s)
         Store<ST>::cp_async_if(reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff),
@@ -997,17 +1012,16 @@ __device__ __forceinline__ void fetch_all_mirror(const Fetch& f, unsigned char* 
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             ST* d = reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff);
+            const ST* g = gplane + s * fstride + f.goff;
 #pragma unroll
-            for (int e = 0; e < kVEC; ++e) {
-                const int x = f.xs + e;
-                Store<ST>::cp_async_elem(
-                    d + e, gplane + s * fstride + f.goff + (px ? wrapi(x, nx) : mirror_index(x, nx)));
-            }
+            for (int e = 0; e < kVEC; ++e) Store<ST>::cp_async_elem(d + e, g + f.e[e]);
         }
     }
 }
 
-template <class ST, bool ONE>
+// PLAIN: no point source or wind and isotropic D for a and b (held layers
+// are still applied); the update of a and b then needs no per-plane tests.
+template <class ST, bool ONE, bool PLAIN>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
     using LY = LayoutCH<ST>;
@@ -1063,8 +1077,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
         const unsigned xyf = xy_faces(xs, y, nx, ny);
         const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
         // own state vector, and (first 2 x 18 threads) the outer halo rows
-        const Fetch fo = make_fetch_mirror<ST>(y, xs, nx, ny, pitch, px, py, own);
-        Fetch fx{0, 0, 0, 0};
+        const FetchM fo = make_fetch_mirror<ST>(y, xs, nx, ny, pitch, px, py, own);
+        FetchM fx{0, 0, 0, {0, 0, 0, 0}};
         if (tid < 2 * kNQ) {
             const bool bottom = tid >= kNQ;
             const int vv = tid - (bottom ? kNQ : 0);
@@ -1079,8 +1093,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                 const int zs = pz ? wrapi(nld, nz) : mirror_index(nld, nz);
                 const ST* g = gin + (long long)zs * plane;
                 unsigned char* buf = ring + sld * SLOTB;
-                fetch_all_mirror<ST, S>(fo, buf, PEB, g, fstride, nx, px);
-                if (tid < 2 * kNQ) fetch_all_mirror<ST, S>(fx, buf, PEB, g, fstride, nx, px);
+                fetch_all_mirror<ST, S>(fo, buf, PEB, g, fstride);
+                if (tid < 2 * kNQ) fetch_all_mirror<ST, S>(fx, buf, PEB, g, fstride);
             }
             ++nld;
             sld = (sld == RING - 1) ? 0 : sld + 1;
@@ -1157,8 +1171,17 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                         xm[e] = e ? cen[s][e - 1] : left;
                         xp[e] = (e < kVEC - 1) ? cen[s][e + 1] : right;
                     }
-                    species_core(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s], cx, src_here, px,
-                                 xs, o);
+                    if constexpr (PLAIN) {
+                        // the same arithmetic species_core takes for this case
+                        const float k = sd.kx[s];
+#pragma unroll
+                        for (int e = 0; e < kVEC; ++e)
+                            o[e] = euler_cell_iso(cen[s][e], xm[e], xp[e], ym[e], yp[e], zm[e],
+                                                  zp[e], k, inc[s][e]);
+                    } else {
+                        species_core(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s], cx, src_here,
+                                     px, xs, o);
+                    }
                     held_layers_at(sd, s, faces, xs, y, p, o);
                     if (stores) Store<ST>::store(gst + s * fstride, o);
                 }
@@ -1203,7 +1226,7 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
     constexpr bool lean_ch = (T == 1 && M::CH);
     void (*k)(const LaunchArgs);
     if constexpr (lean_ch) {
-        k = rd_stepch_kernel<ST, ONE>;
+        k = a.plain ? rd_stepch_kernel<ST, ONE, true> : rd_stepch_kernel<ST, ONE, false>;
     } else if constexpr (lean) {
         // register budget of the one-step kernel: 128 (regcap 0) or 64 (regcap 1)
         if (a.plain)
@@ -1216,7 +1239,7 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
     }
     // dynamic shared memory granted so far, per kernel variant
     static size_t configured[4] = {0, 0, 0, 0};
-    size_t& conf = configured[(lean && a.regcap ? 1 : 0) + (lean && a.plain ? 2 : 0)];
+    size_t& conf = configured[(lean && a.regcap ? 1 : 0) + ((lean || lean_ch) && a.plain ? 2 : 0)];
     if (smem > conf) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

@@ -101,6 +101,17 @@ def test_validation_host_only(lib):
     c = _cfg(W.ch_front(8))
     c.bc[2][4] = L.BC["dirichlet"]        # no held layer on the CH species
     assert q(c) == L.RD_EUNSUPPORTED
+    c = _cfg(W.ch_front(8))
+    c.wind_kind, c.wind_u0 = 1, 0.5       # the front model has no wind
+    assert q(c) == L.RD_EUNSUPPORTED
+    c = _cfg(W.ch_front(8))
+    c.src_species, c.src_x, c.src_y, c.src_z = 2, 1, 1, 1   # nor a source on c
+    assert q(c) == L.RD_EUNSUPPORTED
+    c.src_species = 0                     # a source on a is fine
+    assert q(c) == L.RD_OK
+    c = _cfg(W.air((8, 8, 8), src=(1, 1, 1)))
+    c.wind_u0 = float("nan")              # wind speed must be finite
+    assert q(c) == L.RD_EINVAL
     c = _cfg(W.air((8, 8, 8), src=(1, 1, 1)))
     c.src_x = 8                           # source outside the grid
     assert q(c) == L.RD_EINVAL

@@ -57,6 +57,9 @@ def family_cases():
     per_ch["init"] = "uniform_noise"
     per_air = W.air(SHAPE, src=(40, 0, 17))
     per_air["bc"] = [["periodic"] * 6 for _ in range(3)]
+    ch_src = W.ch_front(shape=SHAPE)
+    ch_src["D"][0] = [1.0, 0.5, 0.25]
+    ch_src["source"] = {"x": 70, "y": 11, "z": 9, "species": 0, "rate": 2.0}
     aniso = W.diffusion_blob(shape=SHAPE)
     aniso["D"] = [[0.9, 0.3, 0.05]]
     aniso["dt"] = 0.4
@@ -68,6 +71,7 @@ def family_cases():
         "brusselator_neumann": (neu_b, TOL_NONLIN),
         "ch_front_dirichlet": (W.ch_front(shape=SHAPE), TOL_NONLIN),
         "ch_periodic": (per_ch, TOL_NONLIN),
+        "ch_front_aniso_source": (ch_src, TOL_NONLIN),
         "air_neumann": (W.air(SHAPE, src=(5, 17, 2)), TOL_NONLIN),
         "air_periodic": (per_air, TOL_NONLIN),
     }
