@@ -101,13 +101,17 @@ def kernel_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(tsteps, tile_q, tile_y, regcap=0):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source and the same tuning; else None."""
+def profiled_traffic(tsteps, tile_q, tile_y):
+    """(DRAM bytes per launch, tuning they were taken at) from the committed
+    ncu summary, if it was taken on the current kernel source at the same
+    steps per launch and tile; else (None, None).  The register cap does not
+    change what the kernel reads and writes; the z-chunk changes only how
+    many halo planes are re-read (mostly from L2), so the tuning is reported
+    beside the number instead of being required to match."""
     try:
         text = open(PROFILE_FILE).read()
     except OSError:
-        return None
+        return None, None
     fields = {}
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):
@@ -115,13 +119,14 @@ def profiled_traffic(tsteps, tile_q, tile_y, regcap=0):
             fields[k.strip()] = v.strip().strip("`")
     try:
         if fields.get("kernel_sha") != kernel_sha():
-            return None
-        if (int(fields["tsteps"]), int(fields["tile_q"]), int(fields["tile_y"]),
-                int(fields.get("regcap", 0))) != (tsteps, tile_q, tile_y, regcap):
-            return None
-        return float(fields["dram_bytes_per_launch"])
+            return None, None
+        if (int(fields["tsteps"]), int(fields["tile_q"]), int(fields["tile_y"])) != \
+                (tsteps, tile_q, tile_y):
+            return None, None
+        tun = {k: int(fields[k]) for k in ("tsteps", "tile_q", "tile_y", "zchunk", "regcap")}
+        return float(fields["dram_bytes_per_launch"]), tun
     except (KeyError, ValueError):
-        return None
+        return None, None
 
 
 class ClockSampler:
@@ -241,6 +246,8 @@ def run_ours(args, ws, rank, local):
     from paper_1004_0480_gb300.sim import Batch, Sim
 
     torch.cuda.set_device(local)
+    if args.profile and args.profile_workload != "brusselator_256":
+        return profile_other(args, Sim, torch)
     cfg = W.cfg_brusselator_256()
     steps_per_job = args.job_steps or cfg["steps"]
     cells = W.cell_count(cfg)
@@ -314,9 +321,10 @@ def run_ours(args, ws, rank, local):
     bytes_per_launch = 16.0 * cells * T
     achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
     peak, peak_src = measured_peak()
+    traffic, traffic_tun = profiled_traffic(T, tun["tile_q"], tun["tile_y"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": profiled_traffic(T, tun["tile_q"], tun["tile_y"], tun.get("regcap", 0)),
+                "traffic": traffic, "traffic_tuning": traffic_tun,
                 "peak_source": peak_src,
                 "kernel": ("rd_step1_kernel<MBrusselator,float>" if T == 1
                            else f"rd_step_kernel<MBrusselator,float,{T}>"),
@@ -375,6 +383,29 @@ def run_ours(args, ws, rank, local):
     if extras:
         line["extras"] = extras
     print(json.dumps(line), flush=True)
+    return 0
+
+
+PROFILE_WORKLOADS = {
+    "air_512x512x64": lambda: W.cfg_air_512(),
+    "ch_front_256": lambda: W.ch_front(256),
+}
+
+
+def profile_other(args, Sim, torch):
+    """A few single launches of another workload's step kernel (for ncu):
+    the problem with the given tuning, two warm-up steps, then ``--profile``
+    single-step calls, no graph."""
+    cfg = PROFILE_WORKLOADS[args.profile_workload]()
+    vals = [int(x) for x in args.tuning.split(",")]
+    with Sim(cfg) as sim:
+        sim.set_fields(W.initial_fields_torch(cfg, "cuda"))
+        sim.set_tuning(tsteps=vals[0], tile_y=vals[1], zchunk=vals[2],
+                       regcap=vals[3] if len(vals) > 3 else 0, graph=0)
+        sim.step(2)
+        for _ in range(args.profile):
+            sim.step(vals[0])
+        sim.sync()
     return 0
 
 
@@ -564,6 +595,9 @@ def main():
                     help="fixed tuning 'tsteps,tile_y,zchunk[,regcap]' instead of the autotuner")
     ap.add_argument("--profile", type=int, default=0,
                     help="only run this many single step-kernel launches (for ncu)")
+    ap.add_argument("--profile-workload", default="brusselator_256",
+                    choices=["brusselator_256", *PROFILE_WORKLOADS],
+                    help="workload of --profile (the others need --tuning)")
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload instead of the step benchmark")
     ap.add_argument("--serve-requests", type=int, default=500)
