@@ -533,9 +533,20 @@ def run_serving(args):
     specs = W.serving_requests(count=args.serve_requests, rate_per_s=1.0, seed=4)
     reqs = SV.requests_from_workload(specs)
     mean_work = float(np.mean([r.cells * r.steps for r in reqs]))
+    # warm up every family once (first use of each kernel and of the device
+    # field generator costs seconds of one-time loading per process), then
     # calibrate the plain stepper's capacity on a few requests of the mix
-    probe = reqs[: max(3, min(8, len(reqs)))]
+    warm = [SV.Request(-1 - i, 0.0, mk(16, steps=4))
+            for i, mk in enumerate((W.diffusion_blob, W.brusselator, W.ch_front))]
     eng = SV.CudaEngine()
+    for r in warm:
+        eng.run_alone(r, False)
+    server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
+                       quantum=args.serve_quantum, run_cells=args.serve_run_cells)
+    server.run(warm)
+    server.engine.shutdown()
+    torch.cuda.synchronize()
+    probe = reqs[: max(3, min(8, len(reqs)))]
     t0 = time.perf_counter()
     for r in probe:
         eng.run_alone(r, False)
@@ -543,18 +554,31 @@ def run_serving(args):
     cap = sum(r.cells * r.steps for r in probe) / (time.perf_counter() - t0)
     rate = args.serve_load * cap / mean_work
     reqs = SV.with_rate(reqs, rate, seed=4)
+    if args.serve_progress:
+        print(f"serve plain capacity {cap / 1e9:.1f} GLUPS, arrival rate {rate:.3f}/s",
+              file=sys.stderr, flush=True)
+    last = [0.0]
+
+    def progress(t, n_adm, n_run, n_done):
+        # one line every 10 s on stderr, with --serve-progress
+        if args.serve_progress and (t < last[0] or t - last[0] >= 10.0):
+            last[0] = t
+            print(f"serve t={t:.1f}s admitted={n_adm} running={n_run} done={n_done}",
+                  file=sys.stderr, flush=True)
     server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
-                       quantum=args.serve_quantum, run_cells=args.serve_run_cells)
+                       quantum=args.serve_quantum, run_cells=args.serve_run_cells,
+                       progress=progress)
     res_b, st_b = server.run(reqs)
     server.engine.shutdown()
-    res_p, st_p = SV.serve_plain(SV.CudaEngine(), reqs)
+    res_p, st_p = SV.serve_plain(SV.CudaEngine(), reqs, progress=progress)
     # capacity: the first requests of the stream all arriving at once
     sat = [SV.Request(r.id, 0.0, r.cfg) for r in reqs[: args.serve_sat_requests]]
     server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
-                       quantum=args.serve_quantum, run_cells=args.serve_run_cells)
+                       quantum=args.serve_quantum, run_cells=args.serve_run_cells,
+                       progress=progress)
     _, sat_b = server.run(sat)
     server.engine.shutdown()
-    _, sat_p = SV.serve_plain(SV.CudaEngine(), sat)
+    _, sat_p = SV.serve_plain(SV.CudaEngine(), sat, progress=progress)
 
     def pack(st):
         return {"p50_s": st.p50, "p99_s": st.p99, "mean_s": st.mean, "glups": st.glups,
@@ -605,6 +629,8 @@ def main():
                     help="offered load as a fraction of the plain stepper's capacity")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-quantum", type=int, default=250)
+    ap.add_argument("--serve-progress", action="store_true",
+                    help="report the serving loop's progress on stderr every 10 s")
     ap.add_argument("--serve-run-cells", type=float, default=48e6,
                     help="cells the running requests hold together (inf: all admitted run)")
     ap.add_argument("--serve-sat-requests", type=int, default=100,

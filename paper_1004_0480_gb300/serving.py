@@ -209,7 +209,8 @@ class Server:
     """
 
     def __init__(self, engine, budget_bytes=120e9, quantum=200, run_cells=48e6,
-                 clock=time.perf_counter, sleep=time.sleep):
+                 clock=time.perf_counter, sleep=time.sleep, progress=None):
+        self.progress = progress     # called as progress(t, admitted, running, done)
         self.engine = engine
         self.budget = float(budget_bytes)
         self.quantum = int(quantum)
@@ -274,6 +275,8 @@ class Server:
             # arrivals between ticks), then retire what is done
             self.engine.sync()
             finished = self.clock() - t0
+            if self.progress:
+                self.progress(finished, len(admitted), len(running), len(results))
             for s in [s for s in running if s["left"] == 0]:
                 req = s["req"]
                 fields = self.engine.result(s["handle"]) if collect_fields else None
@@ -289,7 +292,7 @@ class Server:
 
 
 def serve_plain(engine, requests, collect_fields=False, clock=time.perf_counter,
-                sleep=time.sleep):
+                sleep=time.sleep, progress=None):
     """Baseline: requests one at a time in arrival order, each alone."""
     order = sorted(requests, key=lambda r: (r.arrival, r.id))
     results = []
@@ -304,6 +307,8 @@ def serve_plain(engine, requests, collect_fields=False, clock=time.perf_counter,
         launches += nl
         results.append(Result(req.id, req.arrival, admitted, clock() - t0, req.steps, req.cells,
                                fields))
+        if progress:
+            progress(clock() - t0, 1, 1, len(results))
     makespan = clock() - t0
     return results, summarize(results, makespan, 0, 1, launches)
 
