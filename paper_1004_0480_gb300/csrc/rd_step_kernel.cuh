@@ -927,7 +927,8 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
 // the face cell -- the paper's "Laplacian, boundary rule, Laplacian" -- and
 // every neighbour sits at a fixed offset.  One thread per 4-cell vector of
 // the tile widened by one vector in x and one row in y: at step p each
-// computes mu of plane p+1 at its position and the new state of plane p.
+// computes mu of plane p+1 at its position, and the threads of the tile
+// proper (the first warps) the new state of plane p.
 // A thread keeps its own mu of planes p-1..p+1 in registers; neighbours'
 // mu of plane p come from a 2-slot shared ring (written at step p-1).
 // State planes arrive in a 6-slot ring, P = 4 copy groups ahead: at step p
@@ -1042,13 +1043,32 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
     const int SLOTB = S * PEB;
     unsigned char* const ring = smem + kVEC * EB;
     float* const muring = reinterpret_cast<float*>(smem + LY::state_bytes(TY)) + kVEC;
-    // thread (r, v): position row r - 1 of the tile (rows -1..TY), vector
-    // v - 1 (vectors -1..16)
-    const int r = tid / kNQ;
-    const int v = tid - r * kNQ;
+    // thread -> position (r, v): row r - 1 of the tile (rows -1..TY), vector
+    // v - 1 (vectors -1..16).  The 16 x TY inner positions come first, then
+    // the halo ring (the row above, the row below, then left/right of each
+    // row), so the halo threads fill the last warps and skip the update as
+    // whole warps.
+    const int ninner = kTileQ * TY;
+    const bool inner = tid < ninner;
+    int r, v;
+    if (inner) {
+        r = tid / kTileQ + 1;
+        v = tid - (r - 1) * kTileQ + 1;
+    } else {
+        const int j = tid - ninner;
+        if (j < kNQ) {
+            r = 0;
+            v = j;
+        } else if (j < 2 * kNQ) {
+            r = TY + 1;
+            v = j - kNQ;
+        } else {
+            r = (j - 2 * kNQ) / 2 + 1;
+            v = ((j - 2 * kNQ) & 1) ? kNQ - 1 : 0;
+        }
+    }
     const int own = (r + 1) * kRW + v * kVEC;       // element offset in a plane
     const int own_b = own * EB;
-    const bool inner = r >= 1 && r <= TY && v >= 1 && v <= kTileQ;
 
     int cur_inst = -1;
     if (tid == 0) s_inst = 0;
@@ -1136,8 +1156,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                 }
                 Store<float>::store(muring + ((p + 1) & 1) * PE + own, mu_p);
             }
-            if (p >= z0) {
-                // ---- new state of plane p (every position; stored inside the tile)
+            if (p >= z0 && inner) {
+                // ---- new state of plane p at the inner positions
                 const unsigned char* Sc = ring + sc * SLOTB + own_b;
                 const unsigned char* Sm = ring + sm * SLOTB + own_b;
                 const unsigned char* Sp = ring + s1 * SLOTB + own_b;
@@ -1205,8 +1225,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                     held_layers_at(sd, 2, faces, xs, y, p, o);
                     if (stores) Store<ST>::store(gst + 2 * fstride, o);
                 }
-                gst += plane;
             }
+            if (p >= z0) gst += plane;
 #pragma unroll
             for (int e = 0; e < kVEC; ++e) {
                 mu_m[e] = mu_0[e];
