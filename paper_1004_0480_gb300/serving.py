@@ -11,6 +11,10 @@ reached; its memory is freed, the next admitted requests start running and
 the next arrivals can be admitted.  Reports per-request latency (finish -
 arrival), p50/p99 and aggregate GLUPS.
 
+Each tick the family of the oldest running request gets a high-priority
+stream, so that request's kernels are scheduled first where families
+compete for SMs.
+
 The running set is a first-come-first-served prefix sized to fill the GPU:
 small requests share it (batching is what gets them past the launch-bound
 regime of one small grid), while a request that fills the GPU by itself
@@ -124,6 +128,7 @@ class CudaEngine:
         self.batch_tuning = batch_tuning or {}
         self.batches = {}
         self.streams = {}
+        self.on_high = {}
         self.running = set()
 
     def bytes_for(self, req):
@@ -146,15 +151,29 @@ class CudaEngine:
     def start(self, family, handle):
         """The request joins its family's batch and advances from now on."""
         if family not in self.batches:
-            s = self._torch.cuda.Stream()
-            b = self._Batch(family, self.storage, stream=s)
+            # a normal and a high-priority stream per family (see prioritize)
+            lo, hi = self._torch.cuda.Stream.priority_range()
+            pair = (self._torch.cuda.Stream(priority=lo), self._torch.cuda.Stream(priority=hi))
+            b = self._Batch(family, self.storage, stream=pair[0])
             tun = self.batch_tuning.get(family)
             if tun:
                 b.set_tuning(**tun)
             self.batches[family] = b
-            self.streams[family] = s
+            self.streams[family] = pair
+            self.on_high[family] = False
         self.batches[family].add(handle)
         self.running.add(id(handle))
+
+    def prioritize(self, family):
+        """The next tick of ``family`` runs on its high-priority stream and
+        every other family's on its normal one: where kernels of several
+        families compete for SMs, the one holding the oldest running request
+        is scheduled first.  Called between ticks (streams are idle)."""
+        for fam, b in self.batches.items():
+            want = fam == family
+            if self.on_high[fam] != want:
+                b.set_stream(self.streams[fam][1 if want else 0])
+                self.on_high[fam] = want
 
     def step(self, family, n):
         self.batches[family].step(n)
@@ -262,6 +281,9 @@ class Server:
                 cells += s["req"].cells
             running = [s for s in admitted if s["running"]]
             max_running = max(max_running, len(running))
+            # the oldest running request's family is scheduled first
+            if hasattr(self.engine, "prioritize"):
+                self.engine.prioritize(running[0]["req"].family)
             # ---- one tick: every family's running batch advances (asynchronously)
             by_family = collections.OrderedDict()
             for s in running:

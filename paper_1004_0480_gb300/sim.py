@@ -228,9 +228,13 @@ class Batch:
         self.b = b
         self.members = []
         if stream is not None:
-            handle = getattr(stream, "cuda_stream", stream)
-            L.check(self.lib.rd_batch_set_stream(self.b, ctypes.c_void_p(handle)), None,
-                    "rd_batch_set_stream")
+            self.set_stream(stream)
+
+    def set_stream(self, stream):
+        """Later steps run on ``stream`` (waits for the current one first)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        L.check(self.lib.rd_batch_set_stream(self.b, ctypes.c_void_p(handle)), None,
+                "rd_batch_set_stream")
 
     def add(self, sim: Sim):
         L.check(self.lib.rd_batch_add(self.b, sim.ctx), sim.ctx, "rd_batch_add")
