@@ -37,6 +37,7 @@ from paper_1004_0480_gb300 import workloads as W  # noqa: E402
 METRIC = "GLUPS (cell updates per second / 1e9), brusselator 256^3 FP32"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE_FILE = os.path.join(ROOT, "profiles", "rd_step_brusselator_256.md")
+WORKLOAD = "brusselator_256^3_periodic_10000_steps"
 KERNEL_SOURCES = ["paper_1004_0480_gb300/csrc/rd_step_kernel.cuh",
                   "paper_1004_0480_gb300/csrc/rd_k_brusselator.cu",
                   "paper_1004_0480_gb300/csrc/rd_internal.h"]
@@ -226,8 +227,8 @@ def reference_arm(args, ws, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "brusselator_256^3_periodic", "cells": W.cell_count(cfg),
-                   "species": 2, "sample": sample},
+        "config": {"workload": WORKLOAD, "cells": W.cell_count(cfg), "species": 2,
+                   "steps_per_job": cfg["steps"], "sample": sample},
         "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0,
