@@ -212,7 +212,9 @@ rd_status rd_set_step_count(rd_ctx* ctx, int64_t n);
  *   zchunk  z planes per work item, >= 1
  *   graph   1: replay rd_step launches from a captured CUDA graph
  * rd_set_tuning validates; RD_EINVAL if the CTA or its shared memory does
- * not fit one SM. */
+ * not fit one SM.  A new context starts with tsteps 1, tile_y 14 (12 for
+ * the Cahn-Hilliard model), graph 1, regcap 0 and the z-chunk whose work
+ * items fill the resident CTA slots in the fewest waves. */
 typedef struct rd_tuning {
     int32_t tsteps, tile_q, tile_y, zchunk, graph;
     int32_t regcap;   /* 1: cap the one-step kernel at 64 registers per thread
@@ -278,9 +280,14 @@ rd_status rd_batch_remove(rd_batch* b, rd_ctx* ctx);
 int32_t rd_batch_size(const rd_batch* b);
 /* Enqueue on ``stream`` (NULL = legacy default stream). */
 rd_status rd_batch_set_stream(rd_batch* b, void* stream);
-/* Tuning shared by all members (tile_q, tile_y, zchunk, tsteps, graph). */
+/* Tuning shared by all members (tile_q, tile_y, zchunk, tsteps, graph,
+ * regcap).  Without it a batch uses one step per launch, the default tile
+ * height and the z-chunk that fills the CTA slots in the fewest waves over
+ * its current members. */
 rd_status rd_batch_set_tuning(rd_batch* b, const rd_tuning* t);
-/* Advance every member by nsteps (asynchronous). */
+/* Advance every member by nsteps (asynchronous).  A batch with a single
+ * member steps it exactly as rd_step would (the member's own tuning), on
+ * the batch's stream. */
 rd_status rd_batch_step(rd_batch* b, int64_t nsteps);
 /* Wait for the batch's stream. */
 rd_status rd_batch_sync(rd_batch* b);

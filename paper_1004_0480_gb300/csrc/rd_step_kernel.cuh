@@ -1,7 +1,13 @@
-// rd_step_kernel.cuh -- the fused forward-Euler step kernel (sm_103a).
+// rd_step_kernel.cuh -- the fused forward-Euler step kernels (sm_103a).
 //
-// One launch advances T steps of eq. (5) for every species of every work
-// item.  A work item is an x-y tile of 64 x TY cells and a chunk of z planes
+// Three kernels share the per-cell update functions below, so every launch
+// shape gives the same bits: rd_step_kernel (T steps per launch, described
+// here), rd_step1_kernel (one step per launch, models without
+// Cahn-Hilliard) and rd_stepch_kernel (one step per launch, the front
+// model); the last two are described where they are defined.
+//
+// rd_step_kernel: one launch advances T steps of eq. (5) for every species
+// of every work item.  A work item is an x-y tile of 64 x TY cells and a chunk of z planes
 // of one instance.  The CTA marches up the chunk, as the paper's Shared
 // method does (Section 4.1, Table 4), restated for this hardware:
 //
@@ -35,7 +41,6 @@
 
 #include <cuda_bf16.h>
 #include <stdint.h>
-
 
 #include "rd_internal.h"
 
@@ -71,7 +76,6 @@ template <> struct Store<float> {
                      : "memory");
     }
     // one element (4 bytes), asynchronously
-    static constexpr bool kAsyncElem = true;
     __device__ __forceinline__ static void cp_async_elem(float* smem, const float* g) {
         const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g) : "memory");
@@ -103,7 +107,6 @@ template <> struct Store<__nv_bfloat16> {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
     }
     // 2-byte elements have no asynchronous copy: element copies are plain
-    static constexpr bool kAsyncElem = false;
     __device__ __forceinline__ static void cp_async_elem(__nv_bfloat16* smem,
                                                          const __nv_bfloat16* g) {
         *smem = *g;
