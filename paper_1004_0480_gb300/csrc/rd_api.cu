@@ -893,28 +893,55 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
     cudaEvent_t e0, e1;
     RD_CUDA(c, cudaEventCreate(&e0));
     RD_CUDA(c, cudaEventCreate(&e1));
-    double best = -1.0;
-    rd_tuning bt = saved;
     const double cells = (double)g.nx * g.ny * g.nz;
-    for (const rd_tuning& t : cands) {
+    // GLUPS of tuning t: the median of ``samples`` timings of ``reps``
+    // launches after one warm-up launch, all reading the current level
+    // (negative if the tuning cannot run)
+    auto time_tuning = [&](const rd_tuning& t, int reps, int samples) -> double {
         c->tun = t;
         c->desc_dirty = true;
-        rd_status st = upload_desc(c);
-        if (st != RD_OK) break;
-        // warm-up, then time launches that all read the current level
-        st = launch_ctx(c, t.tsteps, c->cur, c->stream);
-        if (st != RD_OK) { cudaGetLastError(); continue; }
-        const int reps = 4;
-        cudaEventRecord(e0, c->stream);
-        for (int i = 0; i < reps && st == RD_OK; ++i) st = launch_ctx(c, t.tsteps, c->cur, c->stream);
-        cudaEventRecord(e1, c->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess || st != RD_OK) { cudaGetLastError(); continue; }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double rate = cells * t.tsteps * reps / (ms * 1e-3) / 1e9;
+        if (upload_desc(c) != RD_OK) return -1.0;
+        rd_status st = launch_ctx(c, t.tsteps, c->cur, c->stream);
+        if (st != RD_OK) { cudaGetLastError(); return -1.0; }
+        std::vector<double> rates;
+        for (int k = 0; k < samples; ++k) {
+            cudaEventRecord(e0, c->stream);
+            for (int i = 0; i < reps && st == RD_OK; ++i)
+                st = launch_ctx(c, t.tsteps, c->cur, c->stream);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess || st != RD_OK) {
+                cudaGetLastError();
+                return -1.0;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            rates.push_back(cells * t.tsteps * reps / (ms * 1e-3) / 1e9);
+        }
+        std::sort(rates.begin(), rates.end());
+        return rates[rates.size() / 2];
+    };
+    // pass 1: every candidate, briefly; pass 2: the best few, median of
+    // several longer timings (one short timing is too noisy to rank tilings
+    // a few percent apart)
+    std::vector<std::pair<double, rd_tuning>> ranked;
+    for (const rd_tuning& t : cands) {
+        const double rate = time_tuning(t, 4, 1);
         if (std::getenv("RD_AUTOTUNE_VERBOSE"))
-            std::fprintf(stderr, "rd_autotune %s T=%d tile_y=%d zchunk=%d regcap=%d: %.2f GLUPS (%.4f ms/launch)\n",
-                         key.c_str(), t.tsteps, t.tile_y, t.zchunk, t.regcap, rate, ms / reps);
+            std::fprintf(stderr, "rd_autotune %s T=%d tile_y=%d zchunk=%d regcap=%d: %.2f GLUPS\n",
+                         key.c_str(), t.tsteps, t.tile_y, t.zchunk, t.regcap, rate);
+        if (rate > 0) ranked.push_back({rate, t});
+    }
+    std::stable_sort(ranked.begin(), ranked.end(),
+                     [](const auto& x, const auto& y) { return x.first > y.first; });
+    double best = -1.0;
+    rd_tuning bt = saved;
+    const size_t finalists = std::min<size_t>(ranked.size(), 8);
+    for (size_t i = 0; i < finalists; ++i) {
+        const rd_tuning& t = ranked[i].second;
+        const double rate = time_tuning(t, 8, 5);
+        if (std::getenv("RD_AUTOTUNE_VERBOSE"))
+            std::fprintf(stderr, "rd_autotune %s final T=%d tile_y=%d zchunk=%d regcap=%d: %.2f GLUPS\n",
+                         key.c_str(), t.tsteps, t.tile_y, t.zchunk, t.regcap, rate);
         if (rate > best) { best = rate; bt = t; }
     }
     cudaEventDestroy(e0);
