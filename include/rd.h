@@ -188,7 +188,8 @@ rd_status rd_get_field(rd_ctx* ctx, int s, float* dst, size_t count);
  * stream; returns RD_ENONFINITE (with out filled) if out[2] > 0. */
 rd_status rd_mass(rd_ctx* ctx, int s, double out[3]);
 
-/* Wait for all work enqueued on the context's stream. */
+/* Wait for all work enqueued on the context's stream (and, for a batch
+ * member, on the batch's stream). */
 rd_status rd_sync(rd_ctx* ctx);
 
 /* Like rd_sync, but give up after timeout_ms milliseconds of polling and

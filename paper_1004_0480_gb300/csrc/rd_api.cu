@@ -82,7 +82,11 @@ size_t smem_of(int model, int storage, int T, int ty) {
 // CTA size of a step kernel: the one-step kernel has a thread per tile
 // vector; the multi-level kernel (tile vectors + 2 halo) x (rows + 2 L)
 int threads_of(int model, int T, int ty) {
-    if (T == 1 && model != RD_MODEL_CH_FRONT) return kTileQ * ty + 32;
+    // the one-step kernel needs an even tile height (16 ty compute threads,
+    // then a whole halo warp); an odd height at one step per launch (the
+    // last launch of a call whose tuning steps 2 or 3 per launch) runs the
+    // multi-level kernel at T = 1
+    if (T == 1 && model != RD_MODEL_CH_FRONT && !(ty & 1)) return kTileQ * ty + 32;
     if (T == 1) return (kTileQ + 2) * (ty + 2);   // one-step Cahn-Hilliard kernel
     const int L = (model == RD_MODEL_CH_FRONT ? 2 : 1) * T;
     return (kTileQ + 2) * (ty + 2 * L);
@@ -102,20 +106,22 @@ cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int
 int max_tsteps(int model) { return model == RD_MODEL_CH_FRONT ? 2 : 3; }
 
 // CTAs per SM for a variant (cached).
-int occupancy(int model, int storage, int T, size_t smem, int threads, int regcap = 0) {
+bool plain_problem(const rd_config& g);
+
+int occupancy(int model, int storage, int T, int ty, int regcap = 0, int plain = 0) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, size_t, int, int>, int> cache;
+    static std::map<std::tuple<int, int, int, int, int, int>, int> cache;
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_tuple(model, storage, T, smem, threads, regcap);
+    auto key = std::make_tuple(model, storage, T, ty, regcap, plain);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int occ = 0;
     LaunchArgs dummy{};
     dummy.use_one = 1;
     dummy.regcap = regcap;
-    dummy.ty = (T == 1 && model != RD_MODEL_CH_FRONT) ? (threads - 32) / kTileQ
-               : (T == 1) ? threads / (kTileQ + 2) - 2
-                          : threads / (kTileQ + 2) - 2 * (model == RD_MODEL_CH_FRONT ? 2 : 1) * T;
+    dummy.plain = plain;
+    dummy.ty = ty;
+    const size_t smem = smem_of(model, storage, T, ty);
     if (launch_model(model, storage, T, dummy, 0, smem, nullptr, &occ) != cudaSuccess) occ = 0;
     cudaGetLastError();
     cache[key] = occ;
@@ -384,8 +390,7 @@ rd_tuning default_tuning(const rd_config& g) {
     t.tile_q = kTileQ;
     t.tile_y = default_tile_y(g.model);
     t.graph = 1;
-    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_y);
-    const int occ = occupancy(g.model, g.storage, t.tsteps, sm, threads_of(g.model, t.tsteps, t.tile_y));
+    const int occ = occupancy(g.model, g.storage, t.tsteps, t.tile_y, 0, plain_problem(g));
     const long long cols = (long long)tiles(g.nx, t.tile_q * vec_of(g.storage)) * tiles(g.ny, t.tile_y);
     t.zchunk = wave_zchunk({{cols, g.nz}}, (long long)std::max(occ, 1) * num_sms());
     return t;
@@ -510,7 +515,7 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     a.plain = plain_problem(c->cfg);
     a.ty = c->tun.tile_y;
     const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty);
-    const int occ = std::max(1, occupancy(c->cfg.model, c->cfg.storage, T, sm, threads_of(c->cfg.model, T, a.ty), a.regcap));
+    const int occ = std::max(1, occupancy(c->cfg.model, c->cfg.storage, T, a.ty, a.regcap, a.plain));
     const long long grid = std::min<long long>(a.nitems, (long long)occ * num_sms());
     cudaError_t e = launch_model(c->cfg.model, c->cfg.storage, T, a, (int)grid, sm, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
@@ -801,6 +806,7 @@ rd_status rd_mass(rd_ctx* c, int s, double out[3]) {
 
 rd_status rd_sync(rd_ctx* c) {
     if (!c) return RD_EINVAL;
+    drain_batch(c);
     RD_CUDA(c, cudaStreamSynchronize(c->stream));
     return RD_OK;
 }
@@ -870,8 +876,7 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
             t.tsteps = T; t.tile_q = kTileQ; t.tile_y = ty; t.graph = 1; t.zchunk = 1;
             t.regcap = rc;
             if (check_tuning(g, t) != RD_OK) continue;
-            const size_t sm = smem_of(g.model, g.storage, T, ty);
-            const int occ = occupancy(g.model, g.storage, T, sm, threads_of(g.model, T, ty), rc);
+            const int occ = occupancy(g.model, g.storage, T, ty, rc, plain_problem(g));
             if (occ < 1) continue;
             // z-chunks for 1, 2, 4, 8 waves of CTAs; for one step per launch
             // also every split of z into 1..16 chunks, since how evenly the
@@ -1049,8 +1054,7 @@ rd_tuning batch_tuning(rd_batch* b) {
     t.tile_q = kTileQ;
     t.tile_y = default_tile_y(b->model);
     t.graph = 1;
-    const size_t sm = smem_of(b->model, b->storage, 1, t.tile_y);
-    const int occ = occupancy(b->model, b->storage, 1, sm, threads_of(b->model, 1, t.tile_y));
+    const int occ = occupancy(b->model, b->storage, 1, t.tile_y);
     std::vector<std::pair<long long, int>> cols_nz;
     for (rd_ctx* c : b->members)
         cols_nz.push_back({(long long)tiles(c->cfg.nx, t.tile_q * vec_of(b->storage)) *
@@ -1113,7 +1117,7 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
     for (rd_ctx* m : b->members) a.plain = a.plain && plain_problem(m->cfg);
     a.ty = t.tile_y;
     const size_t sm = smem_of(b->model, b->storage, T, a.ty);
-    const int occ = std::max(1, occupancy(b->model, b->storage, T, sm, threads_of(b->model, T, a.ty), a.regcap));
+    const int occ = std::max(1, occupancy(b->model, b->storage, T, a.ty, a.regcap, a.plain));
     const long long grid = std::min<long long>(nitems, (long long)occ * num_sms());
     cudaError_t e = launch_model(b->model, b->storage, T, a, (int)grid, sm, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch step launch");

@@ -1245,12 +1245,15 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
 // Launch helper used by the per-model translation units.
 template <class M, class ST, int T, bool ONE>
 cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t st, int* occ) {
-    constexpr bool lean = (T == 1 && !M::CH);
+    // the one-step kernel needs an even tile height (16 ty compute threads,
+    // then a whole halo warp); an odd one -- the last launch of a call whose
+    // tuning steps 2 or 3 per launch -- runs the multi-level kernel at T = 1
+    const bool lean = (T == 1 && !M::CH) && !(a.ty & 1);
     constexpr bool lean_ch = (T == 1 && M::CH);
     void (*k)(const LaunchArgs);
     if constexpr (lean_ch) {
         k = a.plain ? rd_stepch_kernel<ST, ONE, true> : rd_stepch_kernel<ST, ONE, false>;
-    } else if constexpr (lean) {
+    } else if (lean) {
         // register budget of the one-step kernel: 128 (regcap 0) or 64 (regcap 1)
         if (a.plain)
             k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, true> : rd_step1_kernel<M, ST, ONE, 1, true>;
@@ -1260,9 +1263,13 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
     } else {
         k = rd_step_kernel<M, ST, T, ONE>;
     }
-    // dynamic shared memory granted so far, per kernel variant
-    static size_t configured[4] = {0, 0, 0, 0};
-    size_t& conf = configured[(lean && a.regcap ? 1 : 0) + ((lean || lean_ch) && a.plain ? 2 : 0)];
+    // dynamic shared memory granted so far, per kernel variant (4: the
+    // multi-level kernel at T = 1)
+    static size_t configured[5] = {0, 0, 0, 0, 0};
+    const int variant = (T == 1 && !M::CH && !lean)
+                            ? 4
+                            : (lean && a.regcap ? 1 : 0) + ((lean || lean_ch) && a.plain ? 2 : 0);
+    size_t& conf = configured[variant];
     if (smem > conf) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -1313,14 +1320,16 @@ template <class M>
 size_t smem_for(int storage, int tsteps, int ty) {
     if (storage == RD_STORE_F32) {
         switch (tsteps) {
-        case 1: return M::CH ? LayoutCH<float>::total(ty) : Layout1<M, float>::total(ty);
+        case 1: return M::CH ? LayoutCH<float>::total(ty)
+                             : (ty & 1) ? Layout<M, float, 1>::total(ty) : Layout1<M, float>::total(ty);
         case 2: return Layout<M, float, 2>::total(ty);
         case 3: return Layout<M, float, 3>::total(ty);
         }
     } else {
         switch (tsteps) {
         case 1: return M::CH ? LayoutCH<__nv_bfloat16>::total(ty)
-                             : Layout1<M, __nv_bfloat16>::total(ty);
+                             : (ty & 1) ? Layout<M, __nv_bfloat16, 1>::total(ty)
+                                        : Layout1<M, __nv_bfloat16>::total(ty);
         case 2: return Layout<M, __nv_bfloat16, 2>::total(ty);
         case 3: return Layout<M, __nv_bfloat16, 3>::total(ty);
         }

@@ -130,6 +130,33 @@ def test_bf16_storage_is_close_and_depth_invariant(rd, orc, name):
     assert rel_err(outs[0], ref) < 3e-2
 
 
+def test_periodic_tiles_wrapping_and_ragged(rd, orc):
+    # periodic nx = 132: the x-tile at 0 wraps its left halo vector, the tile
+    # at 64 has both halo vectors inside the row, the tile at 128 is ragged
+    # (one vector of real cells, its right halo wraps to x = 0)
+    cfg = W.brusselator(shape=(132, 20, 17))
+    f = W.initial_fields(cfg)
+    ref = orc.run(cfg, f, 9)
+    one = run_gpu(rd, cfg, 9, tuning=dict(tsteps=1, tile_y=6, zchunk=5, graph=0), fields=f)
+    two = run_gpu(rd, cfg, 9, tuning=dict(tsteps=2, tile_y=6, zchunk=5, graph=0), fields=f)
+    assert rel_err(one, ref) <= TOL_NONLIN
+    assert np.array_equal(one.view(np.uint32), two.view(np.uint32))
+
+
+def test_odd_tile_height_leftover_step(rd, orc):
+    # 2 and 3 steps per launch with odd tile heights leave a one-step launch
+    # at the end of the call; the one-step kernel needs an even height, so
+    # that launch runs the multi-level kernel at T = 1 (same bits)
+    cfg = W.air((70, 15, 11), src=(9, 4, 3))
+    f = W.initial_fields(cfg)
+    ref = orc.run(cfg, f, 7)
+    even = run_gpu(rd, cfg, 7, tuning=dict(tsteps=1, tile_y=6, zchunk=4), fields=f)
+    assert rel_err(even, ref) <= TOL_NONLIN
+    for t in (dict(tsteps=2, tile_y=5, zchunk=4, graph=0), dict(tsteps=3, tile_y=3, zchunk=5, graph=1)):
+        got = run_gpu(rd, cfg, 7, tuning=t, fields=f)
+        assert np.array_equal(got.view(np.uint32), even.view(np.uint32)), t
+
+
 def test_graph_replay_matches_plain_launches(rd):
     cfg = W.brusselator(shape=(48, 40, 36))
     f = W.initial_fields(cfg)
