@@ -101,20 +101,24 @@ class Sim:
         ctx = ctypes.c_void_p()
         L.check(self.lib.rd_create(ctypes.byref(conf), ctypes.byref(ctx)), None, "rd_create")
         self.ctx = ctx
-        if stream is not None:
-            self.set_stream(stream)
-        if torch_memory:
-            import torch
-            sb, xb = query_sizes(cfg, storage)
-            st = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
-            sc = torch.empty(xb + 256, dtype=torch.uint8, device="cuda")
-            self._keep += [st, sc]
-            a0 = (st.data_ptr() + 255) // 256 * 256
-            a1 = (sc.data_ptr() + 255) // 256 * 256
-            self._check(self.lib.rd_attach(self.ctx, ctypes.c_void_p(a0), ctypes.c_void_p(a1)),
-                        "rd_attach")
-        if tuning is not None:
-            self.set_tuning(**tuning)
+        try:
+            if stream is not None:
+                self.set_stream(stream)
+            if torch_memory:
+                import torch
+                sb, xb = query_sizes(cfg, storage)
+                st = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
+                sc = torch.empty(xb + 256, dtype=torch.uint8, device="cuda")
+                self._keep += [st, sc]
+                a0 = (st.data_ptr() + 255) // 256 * 256
+                a1 = (sc.data_ptr() + 255) // 256 * 256
+                self._check(self.lib.rd_attach(self.ctx, ctypes.c_void_p(a0),
+                                               ctypes.c_void_p(a1)), "rd_attach")
+            if tuning is not None:
+                self.set_tuning(**tuning)
+        except BaseException:
+            self.close()     # do not leak the context when setup fails
+            raise
 
     # -- helpers
     def _check(self, st, what):
