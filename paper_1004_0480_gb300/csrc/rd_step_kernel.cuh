@@ -932,8 +932,9 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
 // the tile widened by one vector in x and one row in y: at step p each
 // computes mu of plane p+1 at its position, and the threads of the tile
 // proper (the first warps) the new state of plane p.
-// A thread keeps its own mu of planes p-1..p+1 in registers; neighbours'
-// mu of plane p come from a 2-slot shared ring (written at step p-1).
+// A thread keeps its own mu of planes p-1..p+1 and its own c of planes
+// p..p+2 in registers; neighbours' mu of plane p come from a 2-slot shared
+// ring (written at step p-1).
 // State planes arrive in a 6-slot ring, P = 4 copy groups ahead: at step p
 // planes p-1..p+2 are read and p+3, p+4 are in flight.  Slot reuse: step p
 // refills the slot of plane p-2, whose neighbour reads (mu of p-2 at step
@@ -1129,6 +1130,7 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
         const float* courant = sd.courant;
         ST* gst = gout + (long long)z0 * plane + (long long)y * pitch + xs;
         float mu_m[kVEC] = {}, mu_0[kVEC] = {};       // own mu of planes p-1, p
+        float cz_m[kVEC] = {}, cz_0[kVEC] = {};       // own c of planes p, p+1
         int sc = 0;                                   // ring slot of plane p
 #pragma unroll 1
         for (int p = z0 - 2; p < z1; ++p) {
@@ -1141,12 +1143,18 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
             const int s1 = sc == RING - 1 ? 0 : sc + 1;
             const int s2 = s1 == RING - 1 ? 0 : s1 + 1;
             float mu_p[kVEC];                         // own mu of plane p + 1
+            float cz_p[kVEC];                         // own c of plane p + 2
             {
                 const unsigned char* Cc = ring + s1 * SLOTB + 2 * PEB + own_b;
-                float c[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC];
-                lds_vec<ST>(Cc, c);
-                lds_vec<ST>(ring + sc * SLOTB + 2 * PEB + own_b, zm);
-                lds_vec<ST>(ring + s2 * SLOTB + 2 * PEB + own_b, zp);
+                if (p == z0 - 2) {
+                    lds_vec<ST>(ring + sc * SLOTB + 2 * PEB + own_b, cz_m);
+                    lds_vec<ST>(Cc, cz_0);
+                }
+                const float(&zm)[kVEC] = cz_m;
+                const float(&c)[kVEC] = cz_0;
+                float ym[kVEC], yp[kVEC];
+                const float(&zp)[kVEC] = cz_p;
+                lds_vec<ST>(ring + s2 * SLOTB + 2 * PEB + own_b, cz_p);
                 lds_vec<ST>(Cc - RWB, ym);
                 lds_vec<ST>(Cc + RWB, yp);
                 const float left = lds_one<ST>(Cc - EB);
@@ -1167,7 +1175,9 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                 const unsigned faces = xyf | z_faces(p, nz);
                 float cen[S][kVEC], inc[S][kVEC];
 #pragma unroll
-                for (int s = 0; s < S; ++s) lds_vec<ST>(Sc + s * PEB, cen[s]);
+                for (int s = 0; s < 2; ++s) lds_vec<ST>(Sc + s * PEB, cen[s]);
+#pragma unroll
+                for (int e = 0; e < kVEC; ++e) cen[2][e] = cz_m[e];   // c of plane p, carried
 #pragma unroll
                 for (int e = 0; e < kVEC; ++e) {
                     float cv[S], iv[S];
@@ -1234,6 +1244,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
             for (int e = 0; e < kVEC; ++e) {
                 mu_m[e] = mu_0[e];
                 mu_0[e] = mu_p[e];
+                cz_m[e] = cz_0[e];
+                cz_0[e] = cz_p[e];
             }
             sc = s1;
         }
