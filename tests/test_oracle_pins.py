@@ -328,6 +328,80 @@ def test_dirichlet_linear_profile_is_steady(orc):
     np.testing.assert_allclose(out, c0, rtol=0, atol=1e-6)
 
 
+@pytest.mark.parametrize("model", ["brusselator", "air", "ch_front"])
+def test_uniform_state_follows_the_scalar_ode(orc, model):
+    # with every face periodic and no wind or source, a uniform state stays
+    # uniform and each cell follows the forward-Euler map of the model's
+    # ODE, written here from the kinetics of the benchmark problems
+    if model == "brusselator":
+        cfg = W.brusselator(shape=(5, 4, 6))
+        y0 = [1.0, 2.0]
+        a, b = cfg["params"]["a"], cfg["params"]["b"]
+
+        def rate(y):
+            u, v = y
+            return [a - (b + 1.0) * u + u * u * v, b * u - u * u * v]
+    elif model == "air":
+        cfg = W.air((5, 4, 6), src=(0, 0, 0))
+        cfg["source"], cfg["wind"] = None, None
+        y0 = [0.2, 0.5, 0.8]
+        j, k = cfg["params"]["j"], cfg["params"]["k"]
+
+        def rate(y):
+            no, no2, o3 = y
+            net = j * no2 - k * no * o3          # NO2 -> NO + O3 minus NO + O3 -> NO2
+            return [net, -net, net]
+    else:
+        cfg = W.ch_front(shape=(5, 4, 6))
+        y0 = [0.9, 0.6, 0.3]
+        k = cfg["params"]["k"]
+
+        def rate(y):
+            q = k * y[0] * y[1]                  # a + b -> c; mu is uniform
+            return [-q, -q, q]
+    S = cfg["nspecies"]
+    cfg["bc"] = [["periodic"] * 6 for _ in range(S)]
+    cfg["bc_value"] = [[0.0] * 6 for _ in range(S)]
+    c0 = np.stack([np.full((6, 4, 5), v) for v in y0])
+    steps = 25
+    out = orc.run(cfg, c0, steps)
+    y = list(y0)
+    for _ in range(steps):
+        r = rate(y)
+        y = [y[s] + cfg["dt"] * r[s] for s in range(S)]
+    for s in range(S):
+        assert np.ptp(out[s]) == 0.0
+        assert out[s].flat[0] == pytest.approx(y[s], rel=1e-13, abs=1e-15)
+    assert any(abs(y[s] - y0[s]) > 1e-3 for s in range(S))   # the state moved
+
+
+def test_mirror_ghost_equivalence_for_cahn_hilliard(orc):
+    # Section 4.1 re-applies the boundary rule to mu before the second
+    # Laplacian.  At zero-flux faces that equals extending c by two mirrored
+    # cells (ghost(-1) = c(0), ghost(-2) = c(1)) and evaluating mu on the
+    # ghosts: computed here with np.pad, against one oracle step
+    shape = (7, 6, 5)
+    cfg = W.ch_front(shape=shape, k=0.0, Da=0.0, Db=0.0)
+    cfg["bc"] = [["neumann"] * 6 for _ in range(3)]
+    cfg["bc_value"] = [[0.0] * 6 for _ in range(3)]
+    rng = np.random.default_rng(7)
+    c0 = np.zeros((3, 5, 6, 7))
+    c0[2] = 0.5 + 0.3 * rng.standard_normal((5, 6, 7))
+    out = orc.run(cfg, c0, 1)
+    h2 = cfg["h"] ** 2
+    kappa, M, dt = cfg["params"]["kappa"], cfg["params"]["M"], cfg["dt"]
+    c = np.pad(c0[2], 2, mode="symmetric")            # (z, y, x), two ghost layers
+
+    def lap(f):   # 7-point Laplacian on the interior one cell in from f's edge
+        return (f[2:, 1:-1, 1:-1] + f[:-2, 1:-1, 1:-1] + f[1:-1, 2:, 1:-1] + f[1:-1, :-2, 1:-1]
+                + f[1:-1, 1:-1, 2:] + f[1:-1, 1:-1, :-2] - 6.0 * f[1:-1, 1:-1, 1:-1]) / h2
+    cm = c[1:-1, 1:-1, 1:-1]                          # the grid plus one ghost layer
+    mu = 2.0 * cm * (cm - 1.0) * (2.0 * cm - 1.0) - kappa * lap(c)
+    expect = c0[2] + dt * M * lap(mu)
+    np.testing.assert_allclose(out[2], expect, rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(out[0], c0[0])
+
+
 def test_oracles_agree_on_every_family(orc):
     cases = [W.diffusion_blob(8), W.brusselator(8), W.ch_front(8),
              W.air((8, 8, 8), src=(3, 4, 2)),
