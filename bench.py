@@ -582,8 +582,11 @@ def run_serving(args):
         eng.run_alone(r, False)
     torch.cuda.synchronize()
     cap = sum(r.cells * r.steps for r in probe) / (time.perf_counter() - t0)
+    base_reqs = reqs
     rate = args.serve_load * cap / mean_work
     reqs = SV.with_rate(reqs, rate, seed=4)
+    if args.serve_loads:
+        return serving_sweep(args, SV, base_reqs, cap, mean_work)
     if args.serve_progress:
         print(f"serve plain capacity {cap / 1e9:.1f} GLUPS, arrival rate {rate:.3f}/s",
               file=sys.stderr, flush=True)
@@ -633,6 +636,30 @@ def run_serving(args):
     return 0
 
 
+def serving_sweep(args, SV, reqs, cap, mean_work):
+    """Both servers at each offered load of --serve-loads (fraction of the
+    plain stepper's measured capacity); one JSON line."""
+    rows = []
+    for load in (float(x) for x in args.serve_loads.split(",")):
+        rate = load * cap / mean_work
+        rr = SV.with_rate(reqs, rate, seed=4)
+        server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
+                           quantum=args.serve_quantum, run_cells=args.serve_run_cells)
+        _, st_b = server.run(rr)
+        server.engine.shutdown()
+        _, st_p = SV.serve_plain(SV.CudaEngine(), rr)
+        rows.append({"offered_load": load, "arrival_rate_per_s": rate,
+                     "continuous_batching": {"p50_s": st_b.p50, "p99_s": st_b.p99,
+                                             "mean_s": st_b.mean, "glups": st_b.glups},
+                     "plain": {"p50_s": st_p.p50, "p99_s": st_p.p99, "mean_s": st_p.mean,
+                               "glups": st_p.glups}})
+    print(json.dumps({"metric": "serving latency p50/p99 (s) and aggregate GLUPS vs offered load",
+                      "unit": "s", "requests": len(reqs), "plain_capacity_glups": cap / 1e9,
+                      "run_cells": args.serve_run_cells, "quantum_steps": args.serve_quantum,
+                      "data": "synthetic", "sweep": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -659,6 +686,8 @@ def main():
                     help="offered load as a fraction of the plain stepper's capacity")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-quantum", type=int, default=250)
+    ap.add_argument("--serve-loads", default="",
+                    help="comma-separated offered loads: run both servers at each instead")
     ap.add_argument("--serve-progress", action="store_true",
                     help="report the serving loop's progress on stderr every 10 s")
     ap.add_argument("--serve-run-cells", type=float, default=48e6,
