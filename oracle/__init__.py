@@ -28,6 +28,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liborc.so")
 _SRC = os.path.join(_HERE, "rd_oracle.c")
+_HDR = os.path.join(_HERE, "rd_oracle.h")
 
 MAXS = 4
 _BC = {"neumann": 0, "periodic": 1, "dirichlet": 2}
@@ -49,6 +50,7 @@ class OrcProblem(ctypes.Structure):
         ("src_x", ctypes.c_int32), ("src_y", ctypes.c_int32),
         ("src_z", ctypes.c_int32), ("src_species", ctypes.c_int32),
         ("src_rate", ctypes.c_double),
+        ("stencil", ctypes.c_int32), ("pad0", ctypes.c_int32),
     ]
 
 
@@ -56,7 +58,8 @@ def build(force: bool = False) -> str:
     """Compile the C oracle with gcc into ``oracle/_build/liborc.so``."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                   os.path.getmtime(_HDR))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fPIC",
@@ -116,6 +119,7 @@ def make_problem(cfg) -> OrcProblem:
         p.src_rate = src["rate"]
     else:
         p.src_species = -1
+    p.stencil = cfg.get("stencil", 7)
     return p
 
 

@@ -7,7 +7,8 @@ whole-array operations on a field padded by one ghost layer per axis
 instead of per-cell boundary-aware accessors.
 
 Definitions followed: eq. (1) with a diagonal D (per species and axis),
-eq. (5) forward Euler, the 7-point Laplacian per axis, first-order upwind
+eq. (5) forward Euler, the 7-point Laplacian per axis or the 19-point
+Laplacian of eqs. (3)-(4) (``cfg["stencil"] == 19``), first-order upwind
 advection (Section 4.1), the Cahn-Hilliard biharmonic as Laplacian, boundary
 rule, Laplacian (Section 4.1), held boundary layers for Dirichlet faces
 (Section 4.1, boundary points set before each step).
@@ -48,6 +49,31 @@ def _second_diffs(f, bc_s, h):
         lo, hi = _shifted(f, arr_axis, per[a])
         out.append((lo + hi - 2.0 * f) / (h * h))
     return out
+
+
+# eq. (4): T[r + 1][q + 1][p + 1] for offsets (p, q, r) along (x, y, z)
+_T_PLUS = np.array([[0.0, 1.0, 0.0], [1.0, 2.0, 1.0], [0.0, 1.0, 0.0]])
+_T_MID = np.array([[1.0, 2.0, 1.0], [2.0, -24.0, 2.0], [1.0, 2.0, 1.0]])
+_T19 = np.stack([_T_PLUS, _T_MID, _T_PLUS])
+
+
+def _lap19(f, bc_s, h):
+    """Eq. (3): the 19-point Laplacian of f (nz, ny, nx).  The field is
+    padded along x, then y, then z, so an edge ghost takes both crossed
+    axes' rules in turn."""
+    per = _periodic_axes(bc_s)
+    g = f
+    for a, arr_axis in ((0, 2), (1, 1), (2, 0)):
+        g = _pad_axis(g, arr_axis, per[a])
+    nz, ny, nx = f.shape
+    acc = np.zeros_like(f)
+    for r in range(3):
+        for q in range(3):
+            for p in range(3):
+                w = _T19[r, q, p]
+                if w:
+                    acc += w * g[r:r + nz, q:q + ny, p:p + nx]
+    return acc / (6.0 * h * h)
 
 
 def _held_mask(shape, bc_s):
@@ -105,6 +131,11 @@ def np_step(cfg, c):
     """One step; c has shape (S, nz, ny, nx) float64; returns the new array."""
     S = cfg["nspecies"]
     h, dt = cfg["h"], cfg["dt"]
+    stencil = cfg.get("stencil", 7)
+    if stencil not in (7, 19):
+        raise ValueError(f"stencil {stencil}")
+    if stencil == 19 and any(len(set(d)) != 1 for d in cfg["D"][:S]):
+        raise ValueError("eq. (3) has one diffusivity per species")
     c = c.copy()
     held = [_held_mask(c.shape[1:], cfg["bc"][s]) for s in range(S)]
     for s in range(S):
@@ -115,9 +146,14 @@ def np_step(cfg, c):
     out = np.empty_like(c)
     for s in range(S):
         bc_s = cfg["bc"][s]
-        dxx, dyy, dzz = _second_diffs(c[s], bc_s, h)
         D = cfg["D"][s]
-        tend = rates[s] + D[0] * dxx + D[1] * dyy + D[2] * dzz
+        if stencil == 19:
+            lap_c = _lap19(c[s], bc_s, h)
+            tend = rates[s] + D[0] * lap_c
+        else:
+            dxx, dyy, dzz = _second_diffs(c[s], bc_s, h)
+            lap_c = dxx + dyy + dzz
+            tend = rates[s] + D[0] * dxx + D[1] * dyy + D[2] * dzz
         if cfg.get("wind"):
             per_x = bc_s[0] == "periodic"
             xm, xp = _shifted(c[s], 2, per_x)
@@ -127,10 +163,13 @@ def np_step(cfg, c):
         if cfg["model"] == "ch_front" and s == 2:
             P = cfg["params"]
             cc = c[2]
-            lap_c = dxx + dyy + dzz
             mu = 2.0 * cc * (cc - 1.0) * (2.0 * cc - 1.0) - P["kappa"] * lap_c
-            mx, my, mz = _second_diffs(mu, bc_s, h)
-            tend = tend + P["M"] * (mx + my + mz)
+            if stencil == 19:
+                lap_mu = _lap19(mu, bc_s, h)
+            else:
+                mx, my, mz = _second_diffs(mu, bc_s, h)
+                lap_mu = mx + my + mz
+            tend = tend + P["M"] * lap_mu
         src = cfg.get("source")
         if src and src["species"] == s:
             tend[src["z"], src["y"], src["x"]] += src["rate"]

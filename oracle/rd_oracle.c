@@ -54,9 +54,44 @@ static double second_diff(const orc_problem* p, const double* f, int s,
     return (m + q - 2.0 * c) / (p->h * p->h);
 }
 
+/* Weights T_pqr of eq. (4), indexed [r+1][q+1][p+1]: the planes r = -1 and
+ * r = +1 hold the "plus" matrix, the plane r = 0 the matrix with -24 in its
+ * centre. */
+static const double T19[3][3][3] = {
+    /* r = -1 */ {{0, 1, 0}, {1, 2, 1}, {0, 1, 0}},
+    /* r =  0 */ {{1, 2, 1}, {2, -24, 2}, {1, 2, 1}},
+    /* r = +1 */ {{0, 1, 0}, {1, 2, 1}, {0, 1, 0}},
+};
+
+/* Value at (x+dx, y+dy, z+dz), each shifted axis mapped through its own
+ * boundary rule in turn (edge ghosts are composed from the face rules). */
+static double nb3(const orc_problem* p, const double* f, int s,
+                  int x, int y, int z, int dx, int dy, int dz)
+{
+    int X = ghost_index(x + dx, p->nx, p->bc[s][0], p->bc[s][1]);
+    int Y = ghost_index(y + dy, p->ny, p->bc[s][2], p->bc[s][3]);
+    int Z = ghost_index(z + dz, p->nz, p->bc[s][4], p->bc[s][5]);
+    return f[lin(p, X, Y, Z)];
+}
+
+/* Eq. (3): the 19-point Laplacian, (1 / 6h^2) sum_pqr T_pqr c_{i+p,j+q,k+r}. */
+static double laplacian19(const orc_problem* p, const double* f, int s,
+                          int x, int y, int z)
+{
+    double acc = 0.0;
+    for (int r = -1; r <= 1; ++r)
+        for (int q = -1; q <= 1; ++q)
+            for (int pp = -1; pp <= 1; ++pp) {
+                double w = T19[r + 1][q + 1][pp + 1];
+                if (w != 0.0) acc += w * nb3(p, f, s, x, y, z, pp, q, r);
+            }
+    return acc / (6.0 * p->h * p->h);
+}
+
 static double laplacian(const orc_problem* p, const double* f, int s,
                         int x, int y, int z)
 {
+    if (p->stencil == 19) return laplacian19(p, f, s, x, y, z);
     return second_diff(p, f, s, x, y, z, 0) + second_diff(p, f, s, x, y, z, 1)
          + second_diff(p, f, s, x, y, z, 2);
 }
@@ -94,6 +129,10 @@ static int check(const orc_problem* p)
         for (int a = 0; a < 3; ++a)
             if ((p->bc[s][2 * a] == ORC_PERIODIC) != (p->bc[s][2 * a + 1] == ORC_PERIODIC))
                 return -1;
+    if (p->stencil != 0 && p->stencil != 7 && p->stencil != 19) return -1;
+    if (p->stencil == 19)   /* eq. (3) has one diffusivity per species */
+        for (int s = 0; s < p->ns; ++s)
+            if (p->D[s][1] != p->D[s][0] || p->D[s][2] != p->D[s][0]) return -1;
     switch (p->model) {
     case ORC_DIFFUSION: break;
     case ORC_BRUSSELATOR: if (p->ns != 2) return -1; break;
@@ -180,8 +219,11 @@ static void step(const orc_problem* p, double* cur, double* nxt, double* mu)
                 for (int s = 0; s < ns; ++s) {
                     const double* f = cur + s * nc;
                     double rate = r[s];
-                    for (int a = 0; a < 3; ++a)
-                        rate += p->D[s][a] * second_diff(p, f, s, x, y, z, a);
+                    if (p->stencil == 19)
+                        rate += p->D[s][0] * laplacian19(p, f, s, x, y, z);
+                    else
+                        for (int a = 0; a < 3; ++a)
+                            rate += p->D[s][a] * second_diff(p, f, s, x, y, z, a);
                     if (u != 0.0) {
                         /* first-order upwind: -u dc/dx from the upstream side */
                         if (u > 0.0)

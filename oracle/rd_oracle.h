@@ -10,6 +10,10 @@
  *            per axis), plus first-order upwind advection (Section 4.1,
  *            Table 1 row 4) and a point emission term E;
  *   7-point Laplacian per axis: (c[i-1] + c[i+1] - 2 c[i]) / h^2;
+ *   eqs. (3)-(4) the 19-point Laplacian (stencil = 19): (1 / 6h^2) times
+ *            the sum of T_pqr c[i+p, j+q, k+r] over the 3x3x3 block, with
+ *            the weights of eq. (4) (-24 centre, 2 face, 1 edge, 0
+ *            corner); one diffusivity per species (D[s][0..2] equal);
  *   eq. (5)  forward Euler: c(t+dt) = c(t) + dt * [diffusion + R + ...],
  *            every term taken from level t;
  *   Table 3  host loop: set boundary values, update all points from the
@@ -26,6 +30,9 @@
  *                 layer held at bc_value (set before each step, never
  *                 updated), as the paper stores boundary points in the
  *                 outermost grid layer (Section 4.1, boundary kernels).
+ * The 19-point stencil also reads edge neighbours (two axes shifted); their
+ * ghost index applies each crossed axis's rule in turn, as the paper's
+ * separate edge kernels fill the edges from the faces (Section 4.1).
  */
 #ifndef RD_ORACLE_H
 #define RD_ORACLE_H
@@ -58,6 +65,8 @@ typedef struct orc_problem {
     double wind_u0;                  /* scale of u_x                        */
     int32_t src_x, src_y, src_z, src_species;   /* src_species < 0: none    */
     double src_rate;
+    int32_t stencil;                 /* 7 (or 0): 7-point; 19: eqs. (3)-(4) */
+    int32_t pad0;
 } orc_problem;
 
 /* Advance ``state`` (ns x nz x ny x nx doubles, x fastest) by nsteps

@@ -42,6 +42,15 @@ MUTANTS = {
     "front_reaction_sign": ("r[2] = q;", "r[2] = -q;"),
     "euler_half_step": ("double out = v[s] + p->dt * rate;",
                         "double out = v[s] + 0.5 * p->dt * rate;"),
+    "stencil19_centre_weight": ("{{1, 2, 1}, {2, -24, 2}, {1, 2, 1}}",
+                                "{{1, 2, 1}, {2, -26, 2}, {1, 2, 1}}"),
+    "stencil19_diagonals_doubled": ("{{1, 2, 1}, {2, -24, 2}, {1, 2, 1}}",
+                                    "{{2, 2, 2}, {2, -28, 2}, {2, 2, 2}}"),
+    "stencil19_corners_for_edges": ("/* r = -1 */ {{0, 1, 0}, {1, 2, 1}, {0, 1, 0}}",
+                                    "/* r = -1 */ {{1, 0, 1}, {0, 2, 0}, {1, 0, 1}}"),
+    "stencil19_normalisation": ("acc / (6.0 * p->h * p->h)", "acc / (4.0 * p->h * p->h)"),
+    "stencil19_edge_ghost_rule": ("int Y = ghost_index(y + dy, p->ny, p->bc[s][2], p->bc[s][3]);",
+                                  "int Y = ghost_index(y + dy, p->ny, p->bc[s][0], p->bc[s][1]);"),
 }
 
 # pins that stand on their own (the NumPy cross-check is excluded)

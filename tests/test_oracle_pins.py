@@ -6,7 +6,7 @@ construction, chosen so that a plausible slip (dropped term, wrong sign,
 wrong index, transposed axis, wrong boundary rule) breaks at least one.
 
 Definitions pinned: eq. (1)/(2) diffusion with diagonal D, the 7-point
-Laplacian, eq. (5) forward Euler, first-order upwind advection and the
+Laplacian, the 19-point Laplacian of eqs. (3)-(4), eq. (5) forward Euler, first-order upwind advection and the
 Cahn-Hilliard chained Laplacian of Section 4.1, boundary layers of
 Section 4.1, and the reaction terms of the benchmark problems.
 """
@@ -402,11 +402,173 @@ def test_mirror_ghost_equivalence_for_cahn_hilliard(orc):
     np.testing.assert_array_equal(out[0], c0[0])
 
 
+# --------------------------------------------------------------------------
+# the 19-point Laplacian of eqs. (3)-(4)
+# --------------------------------------------------------------------------
+def _symbol19(theta):
+    """(6 h^2) times the eigenvalue of eq. (3) on exp(i theta . x): face
+    neighbours (weight 2) give 4 cos(theta_d), the four edge neighbours of
+    each axis pair (weight 1) give 4 cos(theta_d) cos(theta_e)."""
+    c = [math.cos(t) for t in theta]
+    return -24.0 + 4.0 * sum(c) + 4.0 * (c[0] * c[1] + c[0] * c[2] + c[1] * c[2])
+
+
+def _cfg19(shape, D=1.0, dt=0.05, bc="neumann", h=1.0):
+    cfg = _diff_cfg(shape, D=(D, D, D), dt=dt, bc=bc, h=h)
+    cfg["stencil"] = 19
+    return cfg
+
+
+@pytest.mark.parametrize("impl", ["c", "np"])
+def test_stencil19_oblique_plane_wave_periodic(orc, impl):
+    # cos(theta . x) with all three wave numbers non-zero: the edge weights
+    # enter through the products cos(theta_d) cos(theta_e)
+    nx, ny, nz = 12, 10, 8
+    m = (1, 3, 2)
+    D, h, dt = 0.8, 0.7, 0.06
+    cfg = _cfg19((nx, ny, nz), D=D, dt=dt, bc="periodic", h=h)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    theta = [2 * np.pi * m[d] / N for d, N in enumerate((nx, ny, nz))]
+    mode = np.cos(theta[0] * x + theta[1] * y + theta[2] * z)
+    g = 1.0 + D * dt / (6.0 * h * h) * _symbol19(theta)
+    n = 20
+    run = orc.run if impl == "c" else orc.np_run
+    out = run(cfg, (1.0 + mode)[None], n)[0]
+    np.testing.assert_allclose(out, 1.0 + g ** n * mode, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("impl", ["c", "np"])
+def test_stencil19_cosine_mode_neumann(orc, impl):
+    # cell-centred zero-flux modes: each axis's reflecting shift-sum has
+    # eigenvalue 2 cos(pi m / n), and the edge ghosts compose the face rules,
+    # so the product mode keeps the symbol at theta_d = pi m_d / n_d
+    nx, ny, nz = 9, 7, 8
+    m = (2, 1, 3)
+    D, dt = 0.5, 0.1
+    cfg = _cfg19((nx, ny, nz), D=D, dt=dt, bc="neumann")
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    mode = (np.cos(np.pi * m[0] * (x + 0.5) / nx) * np.cos(np.pi * m[1] * (y + 0.5) / ny)
+            * np.cos(np.pi * m[2] * (z + 0.5) / nz))
+    theta = [np.pi * m[d] / N for d, N in enumerate((nx, ny, nz))]
+    g = 1.0 + D * dt / 6.0 * _symbol19(theta)
+    n = 25
+    run = orc.run if impl == "c" else orc.np_run
+    out = run(cfg, (3.0 + mode)[None], n)[0]
+    np.testing.assert_allclose(out, 3.0 + g ** n * mode, rtol=0, atol=1e-12)
+
+
+def _shift_sum1d(n, periodic):
+    # c[i-1] + c[i+1] with the face rule of the axis
+    return _lap1d(n, periodic) + 2.0 * np.eye(n)
+
+
+@pytest.mark.parametrize("per", [(True, True, True), (False, False, False),
+                                 (True, False, False), (False, True, False)])
+def test_stencil19_dense_operator_power(orc, per):
+    # eq. (3) as a matrix: -24 I + 2 (Sx + Sy + Sz) + Sx Sy + Sx Sz + Sy Sz
+    # over 6 h^2, S_a the shift-sum of axis a; mixed boundary rules check that
+    # an edge ghost takes each crossed axis's own rule
+    nx, ny, nz = 4, 3, 5
+    D, h, dt, u = 0.3, 0.9, 0.2, 0.5
+    cfg = _cfg19((nx, ny, nz), D=D, dt=dt, h=h)
+    cfg["bc"] = [[("periodic" if per[f // 2] else "neumann") for f in range(6)]]
+    cfg["wind"] = dict(kind="const", u0=u)
+    Ix, Iy, Iz = np.eye(nx), np.eye(ny), np.eye(nz)
+    Sx = np.kron(Iz, np.kron(Iy, _shift_sum1d(nx, per[0])))
+    Sy = np.kron(Iz, np.kron(_shift_sum1d(ny, per[1]), Ix))
+    Sz = np.kron(_shift_sum1d(nz, per[2]), np.kron(Iy, Ix))
+    N = nx * ny * nz
+    L = (-24.0 * np.eye(N) + 2.0 * (Sx + Sy + Sz) + Sx @ Sy + Sx @ Sz + Sy @ Sz) / (6 * h * h)
+    A = D * L + u / h * np.kron(Iz, np.kron(Iy, _upwind1d(nx, per[0])))
+    step = np.eye(N) + dt * A
+    c0 = W.uniform01(9, 0, N)
+    n = 11
+    ref = np.linalg.matrix_power(step, n) @ c0
+    out = orc.run(cfg, c0.reshape(1, nz, ny, nx), n).ravel()
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-13)
+
+
+def test_stencil19_exact_on_cubic_polynomials(orc):
+    # both stencils are exact for polynomials of degree <= 3 (the weights of
+    # eq. (4) are even in each offset and sum p^2 T_pqr = 12 per axis); away
+    # from the faces one step adds dt D times the analytic Laplacian
+    nx, ny, nz = 9, 8, 7
+    h, D, dt = 0.5, 0.7, 0.01
+    z, y, x = np.meshgrid(np.arange(nz) * h, np.arange(ny) * h, np.arange(nx) * h,
+                          indexing="ij")
+    c = (1.0 + 0.3 * x - 0.2 * y + 0.1 * z + 0.05 * x * x + 0.02 * x * y - 0.03 * y * y
+         + 0.04 * y * z + 0.01 * z * z + 0.002 * x ** 3 - 0.001 * x * y * z + 0.003 * z ** 3)
+    lap = 0.1 - 0.06 + 0.02 + 0.012 * x + 0.018 * z
+    for stencil in (7, 19):
+        cfg = _cfg19((nx, ny, nz), D=D, dt=dt, h=h)
+        cfg["stencil"] = stencil
+        out = orc.run(cfg, c[None], 1)[0]
+        inner = (slice(1, -1),) * 3
+        np.testing.assert_allclose(out[inner], (c + dt * D * lap)[inner], rtol=0, atol=1e-14)
+
+
+def test_stencil19_isotropy_beats_seven_point(orc):
+    # the paper's reason for eq. (3): equal |k| in different directions decays
+    # at nearly equal rates.  Wave vectors (5,0,0) and (3,4,0) on a 40^2 x 4
+    # periodic grid have the same |k|; the spread of their measured decay
+    # rates must be far smaller than with the 7-point stencil
+    nx, ny, nz = 40, 40, 4
+    D, dt = 1.0, 0.05
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    rates = {}
+    for stencil in (7, 19):
+        cfg = _cfg19((nx, ny, nz), D=D, dt=dt, bc="periodic")
+        cfg["stencil"] = stencil
+        for m in ((5, 0), (3, 4)):
+            mode = np.cos(2 * np.pi * (m[0] * x + m[1] * y) / nx)
+            out = orc.run(cfg, mode[None], 1)[0]
+            g = float((out * mode).sum() / (mode * mode).sum())
+            rates[stencil, m] = (1.0 - g) / (D * dt)
+    k2 = (2 * np.pi * 5 / nx) ** 2
+    for stencil in (7, 19):
+        assert abs(rates[stencil, (5, 0)] - k2) < 0.06 * k2
+    spread7 = abs(rates[7, (5, 0)] - rates[7, (3, 4)])
+    spread19 = abs(rates[19, (5, 0)] - rates[19, (3, 4)])
+    assert spread19 < spread7 / 20.0
+
+
+@pytest.mark.parametrize("factor,grows", [(1.0 + 1e-2, True), (1.0 - 1e-2, False)])
+def test_stencil19_stability_bound(orc, factor, grows):
+    # the symbol's minimum over the cube of cosines is -32, at two cosines -1
+    # and one +1: the x-y checkerboard, constant in z, has g = 1 - (16/3) r
+    # (r = D dt / h^2) and stays bounded iff r <= 3/8; the full 3-D
+    # checkerboard has g = 1 - 4 r
+    n = 8
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    cb2 = ((-1.0) ** (x + y))[None]
+    cb3 = ((-1.0) ** (x + y + z))[None]
+    dt = factor * 3.0 / 8.0
+    cfg = _cfg19((n, n, n), dt=dt, bc="periodic")
+    out = orc.run(cfg, cb2, 150)
+    np.testing.assert_allclose(out, (1.0 - 16.0 / 3.0 * dt) ** 150 * cb2, rtol=1e-10, atol=0)
+    assert (np.abs(out).max() > 1.0) == grows
+    out3 = orc.run(cfg, cb3, 7)
+    np.testing.assert_allclose(out3, (1.0 - 4.0 * dt) ** 7 * cb3, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("bc", ["neumann", "periodic"])
+def test_stencil19_mass_conserved(orc, bc):
+    cfg = _cfg19((9, 6, 7), D=0.9, dt=0.1, bc=bc)
+    c0 = W.initial_fields(W.with_(cfg, init="uniform_noise"), seed=13).astype(np.float64)
+    out = orc.run(cfg, c0, 30)
+    assert abs(out.sum() - c0.sum()) <= 1e-12 * abs(c0.sum())
+    assert not np.allclose(out, c0)
+
+
 def test_oracles_agree_on_every_family(orc):
     cases = [W.diffusion_blob(8), W.brusselator(8), W.ch_front(8),
              W.air((8, 8, 8), src=(3, 4, 2)),
              W.brusselator(shape=(7, 9, 6), bc="neumann"),
-             W.ch_front(shape=(9, 7, 10)), W.air((11, 6, 5), src=(10, 0, 4))]
+             W.ch_front(shape=(9, 7, 10)), W.air((11, 6, 5), src=(10, 0, 4)),
+             W.with_(W.brusselator(shape=(7, 9, 6), bc="neumann"), stencil=19),
+             W.with_(W.brusselator(8), stencil=19),
+             W.with_(W.air((9, 7, 6), src=(8, 1, 3)), stencil=19, D=[[0.1] * 3] * 3),
+             W.with_(W.ch_front(shape=(8, 7, 9)), stencil=19)]
     for cfg in cases:
         f = W.initial_fields(cfg)
         a = orc.run(cfg, f, 9)
