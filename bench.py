@@ -419,6 +419,7 @@ def run_ours(args, ws, rank, local):
 PROFILE_WORKLOADS = {
     "air_512x512x64": lambda: W.cfg_air_512(),
     "ch_front_256": lambda: W.ch_front(256),
+    "brusselator_256_19pt": lambda: W.cfg_brusselator_256_19pt(),
 }
 
 
@@ -481,6 +482,14 @@ def run_extras(args, Sim, Batch, torch):
         tun = sim.autotune()
         t = _timed_steps(torch, sim, 2000)
         out["brusselator_256_bf16"] = _entry(W.cell_count(cfg), 2000, t, 8, tun)
+    # the same problem with the paper's 19-point Laplacian, eqs. (3)-(4)
+    # (FP32, the same 16 B per cell-step)
+    cfg = W.cfg_brusselator_256_19pt()
+    with Sim(cfg) as sim:
+        sim.set_fields(W.initial_fields_torch(cfg, "cuda"))
+        tun = sim.autotune()
+        t = _timed_steps(torch, sim, 2000)
+        out["brusselator_256_19pt"] = _entry(W.cell_count(cfg), 2000, t, 16, tun)
     # inert diffusion 64^3, 100 steps (L2-resident: launch-bound, not HBM)
     cfg = W.cfg_diffusion_64()
     with Sim(cfg) as sim:

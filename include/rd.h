@@ -3,7 +3,8 @@
  *
  * The library advances reaction-diffusion systems with the method of lines
  * of the paper's Section 2: a 7-point finite-difference Laplacian per
- * species and axis, the pointwise reaction term R(c) of eq. (1), optional
+ * species and axis (or the paper's isotropic 19-point Laplacian, eqs.
+ * (3)-(4)), the pointwise reaction term R(c) of eq. (1), optional
  * first-order upwind advection and a point emission term (Section 4.1 and
  * Table 1), and the forward-Euler update of eq. (5).  Every species is
  * stored as its own array, x fastest, as in the paper's kernels (Tables
@@ -107,6 +108,15 @@ enum {
  *   src_*        point emission: species src_species gains src_rate per
  *                unit time at cell (src_x, src_y, src_z); src_species < 0
  *                means none
+ *   stencil      Laplacian: 0 or 7 = the 7-point stencil, per axis;
+ *                19 = the isotropic 19-point stencil of eqs. (3)-(4),
+ *                (1/6h^2) (-24 c + 2 x 6 face + 1 x 12 edge neighbours),
+ *                edge ghosts taking both crossed faces' rules.  It needs
+ *                one diffusivity per species (D[s][0] = D[s][1] = D[s][2],
+ *                else RD_EINVAL), steps once per launch (tsteps = 1), is not
+ *                available for RD_MODEL_CH_FRONT nor in batches
+ *                (RD_EUNSUPPORTED), and its stability check uses the centre
+ *                weight 4 D / h^2 in place of 2 sum(D) / h^2.
  */
 typedef struct rd_config {
     int32_t nx, ny, nz, nspecies;
@@ -116,7 +126,7 @@ typedef struct rd_config {
     int32_t bc[RD_MAX_SPECIES][6];
     double bc_value[RD_MAX_SPECIES][6];
     double params[8];
-    int32_t wind_kind, reserved0;
+    int32_t wind_kind, stencil;
     double wind_u0;
     int32_t src_x, src_y, src_z, src_species;
     double src_rate;
@@ -202,12 +212,12 @@ rd_status rd_set_step_count(rd_ctx* ctx, int64_t n);
 
 /* Kernel tuning of a context.
  *   tsteps  steps per launch (temporal blocking depth), 1..3 (1..2 for
- *           the Cahn-Hilliard model)
+ *           the Cahn-Hilliard model, 1 for the 19-point stencil)
  *   tile_q  tile width in 4-cell vectors; this build fixes it at 16 (a tile
  *           is 64 cells wide)
  *   tile_y  tile height in rows, >= 1 (even for tsteps = 1 without
  *           Cahn-Hilliard, where the CTA is 16 tile_y compute threads plus
- *           one halo warp); otherwise the CTA has (tile_q + 2) x
+ *           one halo warp, with either stencil); otherwise the CTA has (tile_q + 2) x
  *           (tile_y + 2 L) threads (L = tsteps, 2 tsteps for Cahn-Hilliard);
  *           at most 512 threads
  *   zchunk  z planes per work item, >= 1
@@ -218,15 +228,16 @@ rd_status rd_set_step_count(rd_ctx* ctx, int64_t n);
  * items fill the resident CTA slots in the fewest waves. */
 typedef struct rd_tuning {
     int32_t tsteps, tile_q, tile_y, zchunk, graph;
-    int32_t regcap;   /* 1: cap the one-step kernel at 64 registers per thread
-                         (more resident warps), 0: let it use up to 128      */
+    int32_t regcap;   /* 1: cap the 7-point one-step kernel at 64 registers
+                         per thread (more resident warps), 0: let it use up
+                         to 128; the 19-point kernel ignores it              */
 } rd_tuning;
 rd_status rd_get_tuning(const rd_ctx* ctx, rd_tuning* out);
 rd_status rd_set_tuning(rd_ctx* ctx, const rd_tuning* t);
 
 /* Time a built-in list of tunings on this context's problem (launches read
  * the current level and write the spare level, so the state is unchanged)
- * and keep the fastest.  Results are cached per (model, storage, grid, BC)
+ * and keep the fastest.  Results are cached per (model, storage, grid, BC, stencil)
  * in-process and, if the environment variable RD_AUTOTUNE_CACHE names a
  * file, in that file (one JSON object per line).  *best may be NULL. */
 rd_status rd_autotune(rd_ctx* ctx, rd_tuning* best);

@@ -27,7 +27,7 @@ class RdConfig(ctypes.Structure):
         ("bc", (ctypes.c_int32 * 6) * MAX_S),
         ("bc_value", (ctypes.c_double * 6) * MAX_S),
         ("params", ctypes.c_double * 8),
-        ("wind_kind", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("wind_kind", ctypes.c_int32), ("stencil", ctypes.c_int32),
         ("wind_u0", ctypes.c_double),
         ("src_x", ctypes.c_int32), ("src_y", ctypes.c_int32), ("src_z", ctypes.c_int32),
         ("src_species", ctypes.c_int32), ("src_rate", ctypes.c_double),

@@ -22,6 +22,7 @@
 
 #include "rd.h"
 #include "rd_internal.h"
+#include "rd_step19.h"
 
 using namespace rdk;
 
@@ -69,7 +70,15 @@ int max_smem_optin() {
 int vec_of(int) { return 4; }
 int elem_bytes(int storage) { return storage == RD_STORE_BF16 ? 2 : 4; }
 
-size_t smem_of(int model, int storage, int T, int ty) {
+// the stencil of a configuration: 7 (7-point, the default) or 19 (eqs. (3)-(4))
+int stencil_of(const rd_config& g) { return g.stencil == 19 ? 19 : 7; }
+
+int species_of(int model) {
+    return model == RD_MODEL_DIFFUSION ? 1 : model == RD_MODEL_BRUSSELATOR ? 2 : 3;
+}
+
+size_t smem_of(int model, int storage, int T, int ty, int stencil = 7) {
+    if (stencil == 19) return smem19_bytes(species_of(model), elem_bytes(storage), ty);
     switch (model) {
     case RD_MODEL_DIFFUSION: return smem_diffusion(storage, T, ty);
     case RD_MODEL_BRUSSELATOR: return smem_brusselator(storage, T, ty);
@@ -81,7 +90,8 @@ size_t smem_of(int model, int storage, int T, int ty) {
 
 // CTA size of a step kernel: the one-step kernel has a thread per tile
 // vector; the multi-level kernel (tile vectors + 2 halo) x (rows + 2 L)
-int threads_of(int model, int T, int ty) {
+int threads_of(int model, int T, int ty, int stencil = 7) {
+    if (stencil == 19) return threads19(ty);
     // the one-step kernel needs an even tile height (16 ty compute threads,
     // then a whole halo warp); an odd height at one step per launch (the
     // last launch of a call whose tuning steps 2 or 3 per launch) runs the
@@ -93,7 +103,16 @@ int threads_of(int model, int T, int ty) {
 }
 
 cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int grid,
-                         size_t smem, cudaStream_t st, int* occ) {
+                         size_t smem, cudaStream_t st, int* occ, int stencil = 7) {
+    if (stencil == 19) {
+        if (T != 1) return cudaErrorInvalidValue;
+        switch (model) {
+        case RD_MODEL_DIFFUSION: return launch19_diffusion(storage, a, grid, smem, st, occ);
+        case RD_MODEL_BRUSSELATOR: return launch19_brusselator(storage, a, grid, smem, st, occ);
+        case RD_MODEL_AIR: return launch19_air(storage, a, grid, smem, st, occ);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (model) {
     case RD_MODEL_DIFFUSION: return launch_diffusion(storage, T, a, grid, smem, st, occ);
     case RD_MODEL_BRUSSELATOR: return launch_brusselator(storage, T, a, grid, smem, st, occ);
@@ -103,16 +122,22 @@ cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int
     return cudaErrorInvalidValue;
 }
 
-int max_tsteps(int model) { return model == RD_MODEL_CH_FRONT ? 2 : 3; }
+// temporal blocking: up to 3 steps per launch (2 with Cahn-Hilliard); the
+// 19-point kernel steps once per launch
+int max_tsteps(const rd_config& g) {
+    if (stencil_of(g) == 19) return 1;
+    return g.model == RD_MODEL_CH_FRONT ? 2 : 3;
+}
 
 // CTAs per SM for a variant (cached).
 bool plain_problem(const rd_config& g);
 
-int occupancy(int model, int storage, int T, int ty, int regcap = 0, int plain = 0) {
+int occupancy(int model, int storage, int T, int ty, int regcap = 0, int plain = 0,
+              int stencil = 7) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int, int>, int> cache;
+    static std::map<std::tuple<int, int, int, int, int, int, int>, int> cache;
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_tuple(model, storage, T, ty, regcap, plain);
+    auto key = std::make_tuple(model, storage, T, ty, regcap, plain, stencil);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int occ = 0;
@@ -121,8 +146,9 @@ int occupancy(int model, int storage, int T, int ty, int regcap = 0, int plain =
     dummy.regcap = regcap;
     dummy.plain = plain;
     dummy.ty = ty;
-    const size_t smem = smem_of(model, storage, T, ty);
-    if (launch_model(model, storage, T, dummy, 0, smem, nullptr, &occ) != cudaSuccess) occ = 0;
+    const size_t smem = smem_of(model, storage, T, ty, stencil);
+    if (launch_model(model, storage, T, dummy, 0, smem, nullptr, &occ, stencil) != cudaSuccess)
+        occ = 0;
     cudaGetLastError();
     cache[key] = occ;
     return occ;
@@ -256,6 +282,18 @@ rd_status validate(const rd_config* c) {
         if (c->src_species == 2)
             return fail(nullptr, RD_EUNSUPPORTED, "no point source on the Cahn-Hilliard species");
     }
+    if (c->stencil != 0 && c->stencil != 7 && c->stencil != 19)
+        return fail(nullptr, RD_EINVAL, "stencil must be 7 or 19");
+    if (c->stencil == 19) {
+        if (c->model == RD_MODEL_CH_FRONT)
+            return fail(nullptr, RD_EUNSUPPORTED,
+                        "the 19-point kernels of this build cover the models without "
+                        "Cahn-Hilliard");
+        for (int s = 0; s < c->nspecies; ++s)
+            if (c->D[s][1] != c->D[s][0] || c->D[s][2] != c->D[s][0])
+                return fail(nullptr, RD_EINVAL,
+                            "the 19-point Laplacian takes one diffusivity per species");
+    }
     if (c->wind_kind < RD_WIND_NONE || c->wind_kind > RD_WIND_CONST)
         return fail(nullptr, RD_EINVAL, "unknown wind kind");
     if (c->wind_kind != RD_WIND_NONE && !std::isfinite(c->wind_u0))
@@ -269,12 +307,18 @@ rd_status validate(const rd_config* c) {
         double umax = 0.0;
         if (c->wind_kind == RD_WIND_LOG) umax = std::fabs(c->wind_u0) * std::log1p((double)c->nz - 1) / std::log1p((double)c->nz);
         if (c->wind_kind == RD_WIND_CONST) umax = std::fabs(c->wind_u0);
+        // the centre coefficient of the update stays >= 0: it is
+        // 1 - dt (w D / h^2 + |u| / h), w = 2 per axis (7-point) or
+        // 24 / 6 = 4 (19-point)
+        const bool s19 = stencil_of(*c) == 19;
         for (int s = 0; s < c->nspecies; ++s) {
-            const double g = c->dt * (2.0 * (c->D[s][0] + c->D[s][1] + c->D[s][2]) / (c->h * c->h) +
-                                      umax / c->h);
+            const double wd = s19 ? 4.0 * c->D[s][0]
+                                  : 2.0 * (c->D[s][0] + c->D[s][1] + c->D[s][2]);
+            const double g = c->dt * (wd / (c->h * c->h) + umax / c->h);
             if (g > 1.0 + 1e-12)
                 return fail(nullptr, RD_EUNSTABLE,
-                            "dt too large for species %d: dt*(2*sum(D)/h^2+|u|/h) = %g > 1", s, g);
+                            "dt too large for species %d: dt*(%s/h^2+|u|/h) = %g > 1", s,
+                            s19 ? "4*D" : "2*sum(D)", g);
         }
         if (c->model == RD_MODEL_CH_FRONT) {
             const double L = 12.0 / (c->h * c->h);
@@ -339,7 +383,7 @@ int auto_zchunk(const rd_config& g, const rd_tuning& t, int occ, int waves) {
 }
 
 rd_status check_tuning(const rd_config& g, const rd_tuning& t) {
-    if (t.tsteps < 1 || t.tsteps > max_tsteps(g.model))
+    if (t.tsteps < 1 || t.tsteps > max_tsteps(g))
         return fail(nullptr, RD_EINVAL, "tsteps out of range");
     if (t.tile_q != kTileQ)
         return fail(nullptr, RD_EINVAL, "tile_q must be %d in this build", kTileQ);
@@ -347,10 +391,10 @@ rd_status check_tuning(const rd_config& g, const rd_tuning& t) {
     if (t.regcap != 0 && t.regcap != 1) return fail(nullptr, RD_EINVAL, "regcap must be 0 or 1");
     if (t.tsteps == 1 && g.model != RD_MODEL_CH_FRONT && (t.tile_y & 1))
         return fail(nullptr, RD_EINVAL, "tile_y must be even for one step per launch");
-    if (threads_of(g.model, t.tsteps, t.tile_y) > kMaxThreads)
+    if (threads_of(g.model, t.tsteps, t.tile_y, stencil_of(g)) > kMaxThreads)
         return fail(nullptr, RD_EINVAL, "tile_y %d too tall for %d steps per launch", t.tile_y,
                     t.tsteps);
-    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_y);
+    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_y, stencil_of(g));
     if (sm + sizeof(InstDesc) + 64 > (size_t)max_smem_optin())
         return fail(nullptr, RD_EINVAL, "tile needs %zu bytes of shared memory", sm);
     return RD_OK;
@@ -390,7 +434,8 @@ rd_tuning default_tuning(const rd_config& g) {
     t.tile_q = kTileQ;
     t.tile_y = default_tile_y(g.model);
     t.graph = 1;
-    const int occ = occupancy(g.model, g.storage, t.tsteps, t.tile_y, 0, plain_problem(g));
+    const int occ = occupancy(g.model, g.storage, t.tsteps, t.tile_y, 0, plain_problem(g),
+                              stencil_of(g));
     const long long cols = (long long)tiles(g.nx, t.tile_q * vec_of(g.storage)) * tiles(g.ny, t.tile_y);
     t.zchunk = wave_zchunk({{cols, g.nz}}, (long long)std::max(occ, 1) * num_sms());
     return t;
@@ -514,10 +559,13 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     a.regcap = c->tun.regcap;
     a.plain = plain_problem(c->cfg);
     a.ty = c->tun.tile_y;
-    const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty);
-    const int occ = std::max(1, occupancy(c->cfg.model, c->cfg.storage, T, a.ty, a.regcap, a.plain));
+    const int sten = stencil_of(c->cfg);
+    const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty, sten);
+    const int occ = std::max(
+        1, occupancy(c->cfg.model, c->cfg.storage, T, a.ty, a.regcap, a.plain, sten));
     const long long grid = std::min<long long>(a.nitems, (long long)occ * num_sms());
-    cudaError_t e = launch_model(c->cfg.model, c->cfg.storage, T, a, (int)grid, sm, st, nullptr);
+    cudaError_t e =
+        launch_model(c->cfg.model, c->cfg.storage, T, a, (int)grid, sm, st, nullptr, sten);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     c->launches++;
     return RD_OK;
@@ -608,9 +656,10 @@ bool g_tune_file_loaded = false;
 
 std::string tune_key(const rd_config& g) {
     char buf[256];
-    std::snprintf(buf, sizeof(buf), "m%d_s%d_%dx%dx%d_p%d%d%d_w%d_sm%d", g.model, g.storage, g.nx,
-                  g.ny, g.nz, periodic_axis(g, 0, 0), periodic_axis(g, 0, 1),
-                  periodic_axis(g, 0, 2), g.wind_kind != RD_WIND_NONE, num_sms());
+    std::snprintf(buf, sizeof(buf), "m%d_s%d_%dx%dx%d_p%d%d%d_w%d_sm%d%s", g.model, g.storage,
+                  g.nx, g.ny, g.nz, periodic_axis(g, 0, 0), periodic_axis(g, 0, 1),
+                  periodic_axis(g, 0, 2), g.wind_kind != RD_WIND_NONE, num_sms(),
+                  stencil_of(g) == 19 ? "_st19" : "");
     return buf;
 }
 
@@ -869,14 +918,17 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
     }
     const rd_tuning saved = c->tun;
     std::vector<rd_tuning> cands;
-    for (int T = 1; T <= max_tsteps(g.model); ++T)
+    const int sten = stencil_of(g);
+    for (int T = 1; T <= max_tsteps(g); ++T)
         for (int ty : {4, 8, 10, 12, 14, 16, 20, 24, 32}) {
-          for (int rc = 0; rc <= ((T == 1 && g.model != RD_MODEL_CH_FRONT) ? 1 : 0); ++rc) {
+          // the register cap is a variant of the 7-point one-step kernel
+          const bool rc_variant = T == 1 && g.model != RD_MODEL_CH_FRONT && sten == 7;
+          for (int rc = 0; rc <= (rc_variant ? 1 : 0); ++rc) {
             rd_tuning t{};
             t.tsteps = T; t.tile_q = kTileQ; t.tile_y = ty; t.graph = 1; t.zchunk = 1;
             t.regcap = rc;
             if (check_tuning(g, t) != RD_OK) continue;
-            const int occ = occupancy(g.model, g.storage, T, ty, rc, plain_problem(g));
+            const int occ = occupancy(g.model, g.storage, T, ty, rc, plain_problem(g), sten);
             if (occ < 1) continue;
             // z-chunks for 1, 2, 4, 8 waves of CTAs; for one step per launch
             // also every split of z into 1..16 chunks, since how evenly the
@@ -1005,6 +1057,8 @@ rd_status rd_batch_add(rd_batch* b, rd_ctx* c) {
     if (c->batch) return fail(c, RD_EINVAL, "context already in a batch");
     if (c->cfg.model != b->model || c->cfg.storage != b->storage)
         return fail(c, RD_EINVAL, "model/storage differ from the batch");
+    if (stencil_of(c->cfg) != 7)
+        return fail(c, RD_EUNSUPPORTED, "batches of this build step the 7-point stencil only");
     if (!c->state) return fail(c, RD_EINVAL, "no memory attached");
     cudaStreamSynchronize(c->stream);
     b->members.push_back(c);

@@ -1,0 +1,12 @@
+// rd_k19_diffusion.cu -- instantiations of the 19-point step kernel for one model
+// family (its own translation unit, so the families compile in parallel).
+#include "rd_step19_kernel.cuh"
+
+namespace rdk {
+
+cudaError_t launch19_diffusion(int storage, const LaunchArgs& a, int grid, size_t smem,
+                        cudaStream_t st, int* occ) {
+    return launch19_model<MDiffusion>(storage, a, grid, smem, st, occ);
+}
+
+}  // namespace rdk

@@ -1,0 +1,357 @@
+// rd_step19_kernel.cuh -- one forward-Euler step of eq. (5) with the
+// 19-point Laplacian of eqs. (3)-(4), for the models without Cahn-Hilliard
+// (sm_103a).
+//
+// Work items, thread layout and copies follow the one-step 7-point kernel
+// (rd_step1_kernel): one thread per 4-cell vector of a 64 x TY tile plus one
+// halo warp, planes of the current state copied into a shared-memory ring
+// by per-thread cp.async several planes ahead, one barrier per plane.  What
+// differs:
+//
+//  * Neighbourhood.  A cell reads the 3x3 block of its own plane (weights
+//    -24 centre, 2 faces, 1 diagonals) and the 5-point cross of the planes
+//    below and above (2 centre, 1 faces); corners weigh 0.  The diagonals
+//    need the tile's four corner vectors, which the halo warp also copies.
+//  * Per-plane sums carried down the march.  When plane k arrives, a
+//    thread forms at each of its 4 cells, with X = xm + xp + ym + yp,
+//        Z_k = 2 c + X                 (plane k as a z-neighbour)
+//        W_k = 2 X + the 4 diagonals   (plane k as the centre plane)
+//    so that 6 h^2 Lap c on plane q = W_q - 24 c_q + Z_{q-1} + Z_{q+1}.
+//    Z_{q-1}, Z_q, W_q and c_q stay in registers; each plane is read from
+//    shared memory once, on arrival (plane q+1 at step q).
+//  * Ring reuse.  A plane's last reads are its arrival and, with wind, the
+//    two elements beside a thread's own row at its own step, so the copy
+//    issued at step q may overwrite plane q-2, whose reads all ended before
+//    the barrier of step q-1: the 7-point kernel's ring of 6 slots with
+//    P = 5 copy groups ahead of q-1.  The first step of a work item also
+//    reads the neighbours of plane z0-1, whose slot the copy of step z0+1
+//    refills; one more barrier after those reads keeps the rule.
+//
+// Boundary rules are those of the 7-point kernels: ghost rows, vectors and
+// planes are copied in under each axis's rule (zero flux: the face value;
+// periodic: wrapped), so an edge ghost composes the rules of the two axes
+// it crosses, as the paper fills its edges after its faces (Section 4.1); a
+// held layer's cell takes its bc value.
+#pragma once
+
+#include "rd_step19.h"
+#include "rd_step_kernel.cuh"
+
+namespace rdk {
+
+template <class M, class ST> struct Layout19 {
+    static constexpr int S = M::S;
+    static constexpr int RING = kRing19;
+    static constexpr int P = 5;
+    static_assert(RING == P + 1, "the copy of step q refills the slot of plane q - 2");
+    __host__ __device__ static int plane_elems(int ty) { return plane_elems19(ty); }
+    __host__ __device__ static size_t total(int ty) {
+        return smem19_bytes(S, (int)sizeof(ST), ty);
+    }
+    __host__ __device__ static int threads(int ty) { return kTileQ * ty + 32; }
+};
+
+// Own vector c and the sums Z, W of one species plane at the thread's 4
+// cells; ``p`` points at the own vector in the ring.
+template <class ST>
+__device__ __forceinline__ void plane_sums19(const unsigned char* p, float (&c)[kVEC],
+                                             float (&zs)[kVEC], float (&ws)[kVEC]) {
+    constexpr int EB = (int)sizeof(ST);
+    constexpr int RWB = kRW * EB;
+    float ym[kVEC], yp[kVEC];
+    lds_vec<ST>(p, c);
+    lds_vec<ST>(p - RWB, ym);
+    lds_vec<ST>(p + RWB, yp);
+    const float l = lds_one<ST>(p - EB), r = lds_one<ST>(p + kVEC * EB);
+    const float ul = lds_one<ST>(p - RWB - EB), ur = lds_one<ST>(p - RWB + kVEC * EB);
+    const float dl = lds_one<ST>(p + RWB - EB), dr = lds_one<ST>(p + RWB + kVEC * EB);
+#pragma unroll
+    for (int e = 0; e < kVEC; ++e) {
+        const float xm = e ? c[e - 1] : l;
+        const float xp = e < kVEC - 1 ? c[e + 1] : r;
+        const float yml = e ? ym[e - 1] : ul;
+        const float ymr = e < kVEC - 1 ? ym[e + 1] : ur;
+        const float ypl = e ? yp[e - 1] : dl;
+        const float ypr = e < kVEC - 1 ? yp[e + 1] : dr;
+        const float cross = __fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym[e], yp[e]));
+        const float diag = __fadd_rn(__fadd_rn(yml, ymr), __fadd_rn(ypl, ypr));
+        zs[e] = __fmaf_rn(2.0f, c[e], cross);
+        ws[e] = __fmaf_rn(2.0f, cross, diag);
+    }
+}
+
+// New value of one species on the thread's 4 cells: c + inc + k6 * lap6,
+// k6 = D dt / (6 h^2), lap6 = 6 h^2 Lap c, plus the point source and
+// first-order upwind advection (Courant number cx, x neighbours from the
+// own vector and the elements ``left`` / ``right`` beside it).
+template <bool PLAIN>
+__device__ __forceinline__ void species19(const InstDesc& sd, int s, float k6,
+                                          const float (&c)[kVEC], const float (&lap6)[kVEC],
+                                          const float (&inc)[kVEC], float cx, float left,
+                                          float right, bool src_here, bool px, int xs,
+                                          float (&o)[kVEC]) {
+    float in[kVEC];
+#pragma unroll
+    for (int e = 0; e < kVEC; ++e) in[e] = inc[e];
+    if constexpr (!PLAIN) {
+        if (src_here && s == sd.src_s) {
+#pragma unroll
+            for (int e = 0; e < kVEC; ++e)
+                if ((px ? wrapi(xs + e, sd.nx) : xs + e) == sd.src_x)
+                    in[e] = __fadd_rn(in[e], sd.src_amt);
+        }
+        if (cx > 0.0f) {
+#pragma unroll
+            for (int e = 0; e < kVEC; ++e) {
+                const float xm = e ? c[e - 1] : left;
+                in[e] = __fmaf_rn(-cx, __fsub_rn(c[e], xm), in[e]);
+            }
+        } else if (cx < 0.0f) {
+#pragma unroll
+            for (int e = 0; e < kVEC; ++e) {
+                const float xp = e < kVEC - 1 ? c[e + 1] : right;
+                in[e] = __fmaf_rn(-cx, __fsub_rn(xp, c[e]), in[e]);
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < kVEC; ++e) o[e] = __fadd_rn(c[e], __fmaf_rn(k6, lap6[e], in[e]));
+}
+
+// PLAIN: no held layer, point source or wind.
+template <class M, class ST, bool ONE, bool PLAIN>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
+    using LY = Layout19<M, ST>;
+    constexpr int S = M::S;
+    constexpr int P = LY::P;
+    constexpr int RING = LY::RING;
+    constexpr int EB = (int)sizeof(ST);
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ InstDesc sdm;
+    __shared__ int s_inst;
+
+    const int tid = threadIdx.x;
+    const int TY = a.ty;
+    const int PEB = LY::plane_elems(TY) * EB;                // bytes per species plane
+    const int SLOTB = S * PEB;                               // bytes per ring slot
+    unsigned char* const ring = smem + kVEC * EB;            // slot 0, species 0
+    int4* const hfetch = reinterpret_cast<int4*>(smem + RING * SLOTB);
+    const int ncomp = kTileQ * TY;
+    const bool halo_warp = tid >= ncomp;
+    const int r = tid / kTileQ;
+    const int v = tid - r * kTileQ;
+    const int own_b = ((r + 1) * kRW + (v + 1) * kVEC) * EB;
+
+    int cur_inst = -1;
+    if (tid == 0) s_inst = 0;
+    for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+        if constexpr (!ONE) load_desc(a, item, sdm, s_inst, cur_inst);
+        const InstDesc& sd = desc_of<ONE>(a, sdm);
+
+        const int nx = sd.nx, ny = sd.ny, nz = sd.nz, pitch = sd.pitch;
+        const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;
+        const bool elems = sd.wrap_elems || !sd.per_x;
+        const long long local = item - sd.item_begin;
+        const int txi = (int)(local % sd.ntx);
+        const int tyi = (int)((local / sd.ntx) % sd.nty);
+        const int zc = (int)(local / ((long long)sd.ntx * sd.nty));
+        const int x0 = txi * kTileQ * kVEC, y0 = tyi * TY;
+        const int z0 = zc * sd.zchunk;
+        const int z1 = min(z0 + sd.zchunk, nz);
+        const int lin = sd.par ^ a.parity;
+        const ST* const gin = reinterpret_cast<const ST*>(sd.base[lin][0]);
+        ST* const gout = reinterpret_cast<ST*>(sd.base[lin ^ 1][0]);
+        const long long fstride = S > 1 ? reinterpret_cast<const ST*>(sd.base[lin][1]) - gin : 0;
+        const long long plane = sd.plane;
+
+        // ---- halo lanes: 2 TY side vectors, 2 x 16 row vectors, then the 4
+        // corner vectors (rows -1 and TY, vector columns -1 and 16)
+        if (halo_warp) {
+            const int hl = tid - ncomp;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int j = hl + 32 * k;
+                Fetch f{0, 0, 0, 0};
+                if (j < 2 * TY) {
+                    const int hr = j >> 1;
+                    const bool right = j & 1;
+                    const int xh = right ? x0 + kTileQ * kVEC : x0 - kVEC;
+                    f = make_fetch<ST>(y0 + hr, xh, nx, ny, pitch, px, py,
+                                       (hr + 1) * kRW + (right ? kNQ - 1 : 0) * kVEC, true);
+                } else if (j < 2 * TY + 2 * kTileQ) {
+                    const int jj = j - 2 * TY;
+                    const bool bottom = jj >= kTileQ;
+                    const int hv = jj - (bottom ? kTileQ : 0);
+                    f = make_fetch<ST>(bottom ? y0 + TY : y0 - 1, x0 + hv * kVEC, nx, ny, pitch, px,
+                                       py, (bottom ? TY + 1 : 0) * kRW + (hv + 1) * kVEC, true);
+                } else if (j < 2 * TY + 2 * kTileQ + 4) {
+                    const int jj = j - 2 * TY - 2 * kTileQ;
+                    const bool bottom = jj >= 2;
+                    const bool right = jj & 1;
+                    f = make_fetch<ST>(bottom ? y0 + TY : y0 - 1,
+                                       right ? x0 + kTileQ * kVEC : x0 - kVEC, nx, ny, pitch, px,
+                                       py,
+                                       (bottom ? TY + 1 : 0) * kRW + (right ? kNQ - 1 : 0) * kVEC,
+                                       true);
+                }
+                hfetch[j] = make_int4(f.mode, f.goff, f.soff, f.xs);
+            }
+        }
+        // ---- compute threads: own vector
+        const int y = y0 + r;
+        const int xs = x0 + v * kVEC;
+        const bool computes = !halo_warp && y < ny && xs < nx;
+        const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
+        const unsigned xyf = xy_faces(xs, y, nx, ny);
+        const Fetch fo = halo_warp ? Fetch{0, 0, 0, 0}
+                                   : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB, true);
+        float k6[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) k6[s] = __fdiv_rn(sd.kx[s], 6.0f);
+        __syncthreads();   // halo descriptors written
+
+        // ---- the march: plane nld is fetched P planes ahead into slot sl;
+        // plane z0 - 1 goes to slot 0, plane q to slot (q - z0 + 1) mod RING
+        int nld = z0 - 1;
+        int zld = pz ? wrapi(nld, nz) : nld;
+        auto issue = [&](int sl) {
+            const bool in_z = pz || (nld >= 0 && nld < nz);
+            if (nld <= z1) {
+                const int zs = in_z ? zld : (nld < 0 ? 0 : nz - 1);
+                const ST* gld = gin + (long long)zs * plane;
+                unsigned char* buf = ring + sl * SLOTB;
+                if (halo_warp) {
+                    const int hl = tid - ncomp;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const int4 h = hfetch[hl + 32 * k];
+                        fetch_all<ST, S>(Fetch{h.x, h.y, h.z, h.w}, buf, PEB, gld, fstride, nx,
+                                         elems, px);
+                    }
+                } else {
+                    fetch_all<ST, S>(fo, buf, PEB, gld, fstride, nx, elems, px);
+                }
+            }
+            ++nld;
+            if (!pz) zld = nld;
+            else if (++zld == nz) zld = 0;
+            cp_async_commit();
+        };
+#pragma unroll 1
+        for (int j = 0; j < P; ++j) issue(j);
+        int zq = pz ? wrapi(z0, nz) : z0;
+        ST* gst = gout + (long long)z0 * plane + (long long)y * pitch + xs;
+        const float* courant = sd.courant;
+        int sc = 1;                               // ring slot of plane q
+        // sums of planes q-1 and q, and the own vector of plane q
+        float zsum_m[S][kVEC], zsum_0[S][kVEC], wsum_0[S][kVEC], c_0[S][kVEC];
+#pragma unroll 1
+        for (int q = z0; q < z1; ++q) {
+            const int sm = sc == 0 ? RING - 1 : sc - 1;
+            const int sp = sc == RING - 1 ? 0 : sc + 1;
+            // overwrite plane q - 2; planes up to q + 1 must have landed
+            issue(sc + P - 1 >= RING ? sc + P - 1 - RING : sc + P - 1);
+            cp_async_wait<P - 2>();
+            __syncthreads();
+            const unsigned char* Pc = ring + sc * SLOTB + own_b;
+            if (q == z0) {   // block-uniform
+                if (!halo_warp) {
+                    const unsigned char* Pm = ring + sm * SLOTB + own_b;
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        float cm[kVEC], wm[kVEC];
+                        plane_sums19<ST>(Pm + s * PEB, cm, zsum_m[s], wm);
+                        plane_sums19<ST>(Pc + s * PEB, c_0[s], zsum_0[s], wsum_0[s]);
+                    }
+                }
+                __syncthreads();   // plane z0 - 1 is refilled at the next step
+            }
+            if (!halo_warp) {
+                const unsigned char* Pp = ring + sp * SLOTB + own_b;
+                float c_p[S][kVEC], zsum_p[S][kVEC], wsum_p[S][kVEC], inc[S][kVEC];
+#pragma unroll
+                for (int s = 0; s < S; ++s) plane_sums19<ST>(Pp + s * PEB, c_p[s], zsum_p[s], wsum_p[s]);
+#pragma unroll
+                for (int e = 0; e < kVEC; ++e) {
+                    float cv[S], iv[S];
+#pragma unroll
+                    for (int s = 0; s < S; ++s) cv[s] = c_0[s][e];
+                    M::react(sd, cv, iv);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
+                }
+                const float cx = (!PLAIN && courant) ? courant[zq] : 0.0f;
+                const bool src_here = src_col && zq == sd.src_z;
+                const unsigned faces = xyf | z_faces(q, nz);
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    float lap6[kVEC], o[kVEC];
+#pragma unroll
+                    for (int e = 0; e < kVEC; ++e)
+                        lap6[e] = __fmaf_rn(-24.0f, c_0[s][e],
+                                            __fadd_rn(__fadd_rn(zsum_m[s][e], zsum_p[s][e]),
+                                                      wsum_0[s][e]));
+                    float left = 0.0f, right = 0.0f;
+                    if (!PLAIN && cx != 0.0f) {
+                        left = lds_one<ST>(Pc + s * PEB - EB);
+                        right = lds_one<ST>(Pc + s * PEB + kVEC * EB);
+                    }
+                    species19<PLAIN>(sd, s, k6[s], c_0[s], lap6, inc[s], cx, left, right,
+                                     src_here, px, xs, o);
+                    if constexpr (!PLAIN) held_layers_at(sd, s, faces, xs, y, q, o);
+                    if (computes) Store<ST>::store(gst + s * fstride, o);
+                }
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+#pragma unroll
+                    for (int e = 0; e < kVEC; ++e) {
+                        zsum_m[s][e] = zsum_0[s][e];
+                        zsum_0[s][e] = zsum_p[s][e];
+                        wsum_0[s][e] = wsum_p[s][e];
+                        c_0[s][e] = c_p[s][e];
+                    }
+            }
+            gst += plane;
+            sc = sc == RING - 1 ? 0 : sc + 1;
+            if (!pz) zq = q + 1;
+            else if (++zq == nz) zq = 0;
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+}
+
+// Launch helper used by the per-model translation units: single-instance
+// launches, even tile heights (16 TY compute threads, then a whole halo
+// warp).
+template <class M, class ST>
+cudaError_t launch19_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t st, int* occ) {
+    if (!a.use_one || (a.ty & 1) || a.ty < 2) return cudaErrorInvalidValue;
+    void (*k)(const LaunchArgs) =
+        a.plain ? rd_step19_kernel<M, ST, true, true> : rd_step19_kernel<M, ST, true, false>;
+    static size_t configured[2] = {0, 0};
+    size_t& conf = configured[a.plain ? 1 : 0];
+    if (smem > conf) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        conf = smem;
+    }
+    const int threads = Layout19<M, ST>::threads(a.ty);
+    if (threads > kMaxThreads) return cudaErrorInvalidConfiguration;
+    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, threads, smem);
+    k<<<grid, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class M>
+cudaError_t launch19_model(int storage, const LaunchArgs& a, int grid, size_t smem,
+                           cudaStream_t st, int* occ) {
+    if (storage == RD_STORE_F32) return launch19_one<M, float>(a, grid, smem, st, occ);
+    if (storage == RD_STORE_BF16) return launch19_one<M, __nv_bfloat16>(a, grid, smem, st, occ);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace rdk

@@ -50,6 +50,7 @@ def make_config(cfg, storage="f32", force=False, no_alloc=False) -> L.RdConfig:
         c.src_rate = src["rate"]
     else:
         c.src_species = -1
+    c.stencil = cfg.get("stencil", 7)
     c.flags = (L.FLAG_FORCE if force else 0) | (L.FLAG_NO_ALLOC if no_alloc else 0)
     return c
 

@@ -195,6 +195,12 @@ def cfg_brusselator_256():
     return brusselator(256, steps=10000, dt=0.005, seed=1)
 
 
+def cfg_brusselator_256_19pt():
+    """The 256^3 Brusselator with the paper's 19-point Laplacian (eqs. (3)-(4))."""
+    return with_(cfg_brusselator_256(), stencil=19,
+                 name="brusselator_256x256x256_19pt")
+
+
 def batch_sizes_ch(count=32, lo=48, hi=192, seed=2):
     """Uneven cube edges for the batched front workload (seeded)."""
     rng = np.random.default_rng(seed)

@@ -43,9 +43,10 @@ def test_struct_layout_matches_c(tmp_path):
 #include <stddef.h>
 #include "rd.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rd_config), offsetof(rd_config, D),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rd_config), offsetof(rd_config, D),
          offsetof(rd_config, bc), offsetof(rd_config, bc_value), offsetof(rd_config, params),
-         offsetof(rd_config, wind_u0), offsetof(rd_config, src_rate), sizeof(rd_tuning));
+         offsetof(rd_config, wind_u0), offsetof(rd_config, src_rate), sizeof(rd_tuning),
+         offsetof(rd_config, stencil));
   return 0;
 }''')
     exe = tmp_path / "probe"
@@ -56,7 +57,7 @@ int main(void) {
     C = L.RdConfig
     assert vals == [ctypes.sizeof(C), C.D.offset, C.bc.offset, C.bc_value.offset,
                     C.params.offset, C.wind_u0.offset, C.src_rate.offset,
-                    ctypes.sizeof(L.RdTuning)]
+                    ctypes.sizeof(L.RdTuning), C.stencil.offset]
 
 
 def test_status_strings(lib):
@@ -116,6 +117,32 @@ def test_validation_host_only(lib):
     c.src_x = 8                           # source outside the grid
     assert q(c) == L.RD_EINVAL
     assert b"source" in lib.rd_last_error(None)
+
+
+def test_validation_of_the_19_point_stencil(lib):
+    sz = ctypes.c_size_t()
+    q = lambda c: lib.rd_query_sizes(ctypes.byref(c), ctypes.byref(sz), None)
+    b19 = W.with_(W.brusselator(8), stencil=19)
+    assert q(_cfg(b19)) == L.RD_OK
+    assert q(_cfg(b19, stencil=0)) == L.RD_OK       # 0 means the 7-point default
+    assert q(_cfg(b19, stencil=13)) == L.RD_EINVAL
+    # one diffusivity per species
+    c = _cfg(b19)
+    c.D[1][2] = 1.0
+    assert q(c) == L.RD_EINVAL
+    assert b"diffusivity" in lib.rd_last_error(None)
+    # the front model's Cahn-Hilliard kernels are 7-point only
+    assert q(_cfg(W.with_(W.ch_front(8), stencil=19))) == L.RD_EUNSUPPORTED
+    # stability: the update's centre weight is 1 - 4 D dt / h^2 (19-point)
+    # against 1 - 6 D dt / h^2 (7-point)
+    ok = W.with_(W.diffusion_blob(8, dt=0.25), stencil=19)
+    bad = W.with_(W.diffusion_blob(8, dt=0.25 * 1.001), stencil=19)
+    assert q(_cfg(ok)) == L.RD_OK
+    assert q(_cfg(bad)) == L.RD_EUNSTABLE
+    assert q(_cfg(W.with_(ok, stencil=7))) == L.RD_EUNSTABLE
+    # an isotropic air problem with wind and a source is accepted
+    air = W.with_(W.air((16, 16, 8), src=(1, 1, 1), dt=0.2), stencil=19, D=[[0.1] * 3] * 3)
+    assert q(_cfg(air)) == L.RD_OK
 
 
 def test_bf16_rows_are_128_bytes(lib):
