@@ -490,6 +490,15 @@ def run_extras(args, Sim, Batch, torch):
         tun = sim.autotune()
         t = _timed_steps(torch, sim, 2000)
         out["brusselator_256_19pt"] = _entry(W.cell_count(cfg), 2000, t, 16, tun)
+    # the paper's own kernel designs on the same problem (ablation baselines:
+    # Shared method and Moving Tiles, Section 4.1, Tables 4-5)
+    for kern in ("shared", "tiles"):
+        with Sim(cfg) as sim:
+            sim.set_fields(W.initial_fields_torch(cfg, "cuda"))
+            sim.set_kernel(kern)
+            t = _timed_steps(torch, sim, 400)
+            out[f"brusselator_256_19pt_{kern}"] = _entry(W.cell_count(cfg), 400, t, 16,
+                                                         kernel=kern)
     # inert diffusion 64^3, 100 steps (L2-resident: launch-bound, not HBM)
     cfg = W.cfg_diffusion_64()
     with Sim(cfg) as sim:

@@ -242,6 +242,30 @@ rd_status rd_set_tuning(rd_ctx* ctx, const rd_tuning* t);
  * file, in that file (one JSON object per line).  *best may be NULL. */
 rd_status rd_autotune(rd_ctx* ctx, rd_tuning* best);
 
+/* Step kernel of a context.  RD_KERNEL_MARCH (the default) is this
+ * library's z-marching kernel for the context's stencil.  The other two are
+ * the paper's own designs (Section 4.1, Tables 4-5), restated for this GPU
+ * as ablation baselines:
+ *   RD_KERNEL_SHARED  3-D blocks of 32 x 8 x 4 threads, one cell each, over
+ *                     x-y tiles overlapping by one cell; the rim loads but
+ *                     does not update; the block walks up z keeping two
+ *                     planes in shared memory ("Shared" method);
+ *   RD_KERNEL_TILES   blocks of 32 x 8 x 4 threads over overlapping y-z
+ *                     tiles, walking along x in 32-cell windows with the
+ *                     next window preloaded ("Moving Tiles").
+ * Both need the 19-point stencil, FP32 storage, a model without
+ * Cahn-Hilliard and no held layer, point source or wind (else
+ * RD_EUNSUPPORTED); they ignore rd_tuning except `graph`, and rd_autotune
+ * refuses them (RD_EUNSUPPORTED).  Results agree with the march kernel to
+ * rounding (other summation order), not bit for bit. */
+typedef enum rd_kernel {
+    RD_KERNEL_MARCH = 0,
+    RD_KERNEL_SHARED = 1,
+    RD_KERNEL_TILES = 2
+} rd_kernel;
+rd_status rd_set_kernel(rd_ctx* ctx, int32_t kernel);
+int32_t rd_get_kernel(const rd_ctx* ctx);   /* -1 for a NULL context */
+
 /* Launch statistics: kernels this context enqueued since creation. */
 int64_t rd_launch_count(const rd_ctx* ctx);
 

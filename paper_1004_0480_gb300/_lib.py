@@ -15,6 +15,7 @@ BC = {"neumann": 0, "periodic": 1, "dirichlet": 2}
 MODEL = {"diffusion": 0, "brusselator": 1, "ch_front": 2, "air": 3}
 STORAGE = {"f32": 0, "bf16": 1}
 WIND = {None: 0, "log": 1, "const": 2}
+KERNEL = {"march": 0, "shared": 1, "tiles": 2}
 FLAG_NO_ALLOC, FLAG_FORCE = 1, 2
 
 
@@ -74,6 +75,8 @@ SIGNATURES = {
     "rd_get_tuning": (_I, [_P, _TUN]),
     "rd_set_tuning": (_I, [_P, _TUN]),
     "rd_autotune": (_I, [_P, _TUN]),
+    "rd_set_kernel": (_I, [_P, _I32]),
+    "rd_get_kernel": (_I32, [_P]),
     "rd_launch_count": (_I64, [_P]),
     "rd_status_str": (ctypes.c_char_p, [_I]),
     "rd_last_error": (ctypes.c_char_p, [_P]),

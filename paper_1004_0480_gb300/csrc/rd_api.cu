@@ -22,6 +22,7 @@
 
 #include "rd.h"
 #include "rd_internal.h"
+#include "rd_ablation.h"
 #include "rd_step19.h"
 
 using namespace rdk;
@@ -178,6 +179,7 @@ struct rd_ctx {
     bool own_stream = false;
     cudaStream_t capture_stream = nullptr;
     rd_tuning tun{};
+    int kernel = RD_KERNEL_MARCH;  // step kernel (rd_set_kernel)
     bool desc_dirty = true;
     InstDesc desc{};
     Graph graph;
@@ -559,6 +561,13 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     a.regcap = c->tun.regcap;
     a.plain = plain_problem(c->cfg);
     a.ty = c->tun.tile_y;
+    if (c->kernel != RD_KERNEL_MARCH) {   // the paper's designs, one step each
+        if (T != 1) return fail(c, RD_EINVAL, "the ablation kernels step once per launch");
+        cudaError_t e = launch_ablation(c->kernel, c->cfg.model, a, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ablation kernel launch");
+        c->launches++;
+        return RD_OK;
+    }
     const int sten = stencil_of(c->cfg);
     const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty, sten);
     const int occ = std::max(
@@ -573,8 +582,8 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
 
 long long ctx_graph_key(const rd_ctx* c) {
     const rd_tuning& t = c->tun;
-    return (((((long long)t.tsteps * 64 + t.tile_q) * 64 + t.tile_y) * 100000 + t.zchunk) * 2 +
-            t.regcap);
+    return ((((((long long)t.tsteps * 64 + t.tile_q) * 64 + t.tile_y) * 100000 + t.zchunk) * 2 +
+             t.regcap) * 4 + c->kernel);
 }
 
 constexpr int kGraphLaunches = 16;
@@ -890,6 +899,25 @@ rd_status rd_get_tuning(const rd_ctx* c, rd_tuning* out) {
     return RD_OK;
 }
 
+rd_status rd_set_kernel(rd_ctx* c, int32_t kernel) {
+    if (!c) return fail(nullptr, RD_EINVAL, "null context");
+    if (kernel < RD_KERNEL_MARCH || kernel > RD_KERNEL_TILES)
+        return fail(c, RD_EINVAL, "unknown kernel %d", kernel);
+    if (kernel != RD_KERNEL_MARCH) {
+        const rd_config& g = c->cfg;
+        if (stencil_of(g) != 19 || g.storage != RD_STORE_F32 || g.model == RD_MODEL_CH_FRONT ||
+            !plain_problem(g))
+            return fail(c, RD_EUNSUPPORTED,
+                        "the Shared and Moving Tiles kernels need the 19-point stencil, FP32 "
+                        "state, no Cahn-Hilliard and no held layer, source or wind");
+        if (c->tun.tsteps != 1) return fail(c, RD_EINVAL, "tsteps must be 1");
+    }
+    c->kernel = kernel;
+    return RD_OK;
+}
+
+int32_t rd_get_kernel(const rd_ctx* c) { return c ? c->kernel : -1; }
+
 rd_status rd_set_tuning(rd_ctx* c, const rd_tuning* t) {
     if (!c || !t) return fail(c, RD_EINVAL, "null argument");
     rd_status st = check_tuning(c->cfg, *t);
@@ -903,6 +931,8 @@ rd_status rd_set_tuning(rd_ctx* c, const rd_tuning* t) {
 rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
     if (!c) return RD_EINVAL;
     if (!c->state) return fail(c, RD_EINVAL, "no memory attached");
+    if (c->kernel != RD_KERNEL_MARCH)
+        return fail(c, RD_EUNSUPPORTED, "the autotuner tunes the march kernel only");
     const rd_config& g = c->cfg;
     const std::string key = tune_key(g);
     {

@@ -197,6 +197,16 @@ class Sim:
                        cur["graph"], cur.get("regcap", 0))
         self._check(self.lib.rd_set_tuning(self.ctx, ctypes.byref(t)), "rd_set_tuning")
 
+    def set_kernel(self, name):
+        """Step kernel: "march" (default), or the paper's "shared" / "tiles"
+        designs (ablation baselines; 19-point stencil, FP32, plain problems)."""
+        self._check(self.lib.rd_set_kernel(self.ctx, L.KERNEL[name]), "rd_set_kernel")
+
+    @property
+    def kernel(self):
+        code = self.lib.rd_get_kernel(self.ctx)
+        return {v: k for k, v in L.KERNEL.items()}[code]
+
     def autotune(self):
         t = L.RdTuning()
         self._check(self.lib.rd_autotune(self.ctx, ctypes.byref(t)), "rd_autotune")
