@@ -124,6 +124,10 @@ def _rates(cfg, c):
         r[0] = photo - titr
         r[1] = titr - photo
         r[2] = photo - titr
+    elif m == "turing":
+        c1, c2 = c[0], c[1]
+        r[0] = c1 - c1 ** 3 - c2
+        r[1] = P["gamma"] * (c1 - P["alpha"] * c2 - P["beta"])
     return r
 
 

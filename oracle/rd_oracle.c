@@ -138,6 +138,7 @@ static int check(const orc_problem* p)
     case ORC_BRUSSELATOR: if (p->ns != 2) return -1; break;
     case ORC_CH_FRONT: if (p->ns != 3) return -1; break;
     case ORC_AIR: if (p->ns != 3) return -1; break;
+    case ORC_TURING: if (p->ns != 2) return -1; break;
     default: return -1;
     }
     return 0;
@@ -173,6 +174,15 @@ static void reaction(const orc_problem* p, const double* v, double* r)
         r[0] = ph - ti;
         r[1] = -ph + ti;
         r[2] = ph - ti;
+        break;
+    }
+    case ORC_TURING: {
+        /* activator-inhibitor pair of Table 1, row 2:
+         * dc1/dt = c1 - c1^3 - c2 ;  dc2/dt = gamma (c1 - alpha c2 - beta) */
+        double alpha = p->p[0], beta = p->p[1], gamma = p->p[2];
+        double c1 = v[0], c2 = v[1];
+        r[0] = c1 - c1 * c1 * c1 - c2;
+        r[1] = gamma * (c1 - alpha * c2 - beta);
         break;
     }
     default: break;

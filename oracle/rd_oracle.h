@@ -44,7 +44,7 @@ extern "C" {
 #endif
 
 enum { ORC_NEUMANN = 0, ORC_PERIODIC = 1, ORC_DIRICHLET = 2 };
-enum { ORC_DIFFUSION = 0, ORC_BRUSSELATOR = 1, ORC_CH_FRONT = 2, ORC_AIR = 3 };
+enum { ORC_DIFFUSION = 0, ORC_BRUSSELATOR = 1, ORC_CH_FRONT = 2, ORC_AIR = 3, ORC_TURING = 4 };
 enum { ORC_WIND_NONE = 0, ORC_WIND_LOG = 1, ORC_WIND_CONST = 2 };
 
 #define ORC_MAXS 4
@@ -60,7 +60,8 @@ typedef struct orc_problem {
     /* model constants:
      *   BRUSSELATOR  p[0]=a, p[1]=b
      *   CH_FRONT     p[0]=k (a+b->c), p[1]=M (mobility), p[2]=kappa
-     *   AIR          p[0]=j (NO2 -> NO + O3), p[1]=k (NO + O3 -> NO2)      */
+     *   AIR          p[0]=j (NO2 -> NO + O3), p[1]=k (NO + O3 -> NO2)
+     *   TURING       p[0]=alpha, p[1]=beta, p[2]=gamma (Table 1, row 2)    */
     double p[8];
     double wind_u0;                  /* scale of u_x                        */
     int32_t src_x, src_y, src_z, src_species;   /* src_species < 0: none    */

@@ -113,6 +113,20 @@ def ch_front(n=64, steps=2000, dt=0.01, Da=1.0, Db=0.1, k=1.0, M=0.1,
                 steps=steps, seed=seed, init="ch_front")
 
 
+def turing(n=192, steps=20000, dt=5.0e-4, D1=5.0e-5, D2=5.0e-3, h=6.2e-3, alpha=0.5,
+           beta=0.09, gamma=26.0, sigma=5.0e-4, seed=5, shape=None, stencil=7):
+    """Activator-inhibitor Turing system of Table 1, row 2, with its
+    parameters: dc1/dt = D1 Lap c1 + c1 - c1^3 - c2,
+    dc2/dt = D2 Lap c2 + gamma (c1 - alpha c2 - beta); zero flux; both
+    species start at 1 + U(-sigma, sigma)."""
+    nx, ny, nz = shape if shape is not None else (n, n, n)
+    return dict(name=f"turing_{nx}x{ny}x{nz}", model="turing", shape=(nx, ny, nz),
+                nspecies=2, h=h, dt=dt, D=[[D1] * 3, [D2] * 3], bc=_bc(NEU, 2),
+                bc_value=[[0.0] * 6] * 2, params=dict(alpha=alpha, beta=beta, gamma=gamma),
+                source=None, wind=None, steps=steps, seed=seed, init="turing",
+                sigma=sigma, stencil=stencil)
+
+
 def air(shape=(512, 512, 64), steps=5000, dt=0.2, Kh=0.1, Kz=0.02, j=0.5,
         k=2.0, src=(64, 256, 2), src_rate=1.0, h=1.0, seed=3, wind_u0=1.0):
     """NO/NO2/O3 advection-diffusion-reaction (Table 1, row 4 family)."""
@@ -173,6 +187,11 @@ def initial_fields(cfg, seed=None, dtype=np.float32):
         for sp in range(3):
             u = uniform01(s, sp, ncell).reshape(nz, ny, nx)
             out[sp] = base[sp] * (1.0 + 0.01 * (2.0 * u - 1.0))
+    elif kind == "turing":
+        sig = cfg["sigma"]
+        for sp in range(2):
+            u = uniform01(s, sp, ncell).reshape(nz, ny, nx)
+            out[sp] = 1.0 + sig * (2.0 * u - 1.0)
     elif kind == "uniform_noise":
         for sp in range(S):
             out[sp] = uniform01(s, sp, ncell).reshape(nz, ny, nx)
@@ -328,6 +347,11 @@ def initial_fields_torch(cfg, device, seed=None):
         for sp in range(3):
             u = uniform01_torch(s, sp, ncell, device).reshape(nz, ny, nx)
             out[sp] = base[sp] * (1.0 + 0.01 * (2.0 * u - 1.0))
+    elif kind == "turing":
+        sig = cfg["sigma"]
+        for sp in range(2):
+            u = uniform01_torch(s, sp, ncell, device).reshape(nz, ny, nx)
+            out[sp] = 1.0 + sig * (2.0 * u - 1.0)
     elif kind == "uniform_noise":
         for sp in range(S):
             out[sp] = uniform01_torch(s, sp, ncell, device).reshape(nz, ny, nx)

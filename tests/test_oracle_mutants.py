@@ -42,6 +42,9 @@ MUTANTS = {
     "front_reaction_sign": ("r[2] = q;", "r[2] = -q;"),
     "euler_half_step": ("double out = v[s] + p->dt * rate;",
                         "double out = v[s] + 0.5 * p->dt * rate;"),
+    "turing_cubic_term": ("r[0] = c1 - c1 * c1 * c1 - c2;", "r[0] = c1 - c1 * c1 - c2;"),
+    "turing_alpha_dropped": ("(c1 - alpha * c2 - beta)", "(c1 - c2 - beta)"),
+    "turing_gamma_dropped": ("r[1] = gamma * (", "r[1] = ("),
     "stencil19_centre_weight": ("{{1, 2, 1}, {2, -24, 2}, {1, 2, 1}}",
                                 "{{1, 2, 1}, {2, -26, 2}, {1, 2, 1}}"),
     "stencil19_diagonals_doubled": ("{{1, 2, 1}, {2, -24, 2}, {1, 2, 1}}",

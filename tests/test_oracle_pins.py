@@ -220,6 +220,41 @@ def test_brusselator_linearised_mode(orc):
     np.testing.assert_allclose(got, amp, rtol=2e-5)
 
 
+@pytest.mark.parametrize("stencil", [7, 19])
+def test_turing_linearised_mode(orc, stencil):
+    # small x-y mode about the homogeneous steady state of the Table 1
+    # activator-inhibitor system: per step the amplitudes follow
+    # I + dt (J - lam diag(D1, D2)) with the textbook Jacobian
+    # J = [[1 - 3 c1^2, -1], [gamma, -gamma alpha]] and lam the stencil's
+    # symbol (7-point: sum of 4 sin^2(theta/2) / h^2; 19-point: eq. (3)'s)
+    n = 12
+    cfg = W.turing(shape=(n, n, 3), stencil=stencil)
+    cfg["bc"] = [["periodic"] * 6] * 2
+    al, be, ga = (cfg["params"][k] for k in ("alpha", "beta", "gamma"))
+    D1, D2 = cfg["D"][0][0], cfg["D"][1][0]
+    h, dt = cfg["h"], cfg["dt"]
+    # steady state: c2 = (c1 - beta) / alpha and c1 - c1^3 - c2 = 0
+    roots = np.roots([1.0, 0.0, 1.0 / al - 1.0, -be / al])
+    c1 = float(roots[np.abs(roots.imag) < 1e-12].real[0])
+    c2 = (c1 - be) / al
+    mx, my = 2, 1
+    z, y, x = np.meshgrid(np.arange(3), np.arange(n), np.arange(n), indexing="ij")
+    th = (2 * np.pi * mx / n, 2 * np.pi * my / n)
+    mode = np.cos(th[0] * x + th[1] * y)
+    eps = np.array([1e-7, -3e-7])
+    c0 = np.stack([c1 + eps[0] * mode, c2 + eps[1] * mode])
+    steps = 40
+    out = orc.run(cfg, c0, steps)
+    if stencil == 7:
+        lam = sum(4.0 * math.sin(t / 2) ** 2 for t in th) / h ** 2
+    else:
+        lam = -_symbol19((th[0], th[1], 0.0)) / (6.0 * h ** 2)
+    J = np.array([[1.0 - 3.0 * c1 * c1, -1.0], [ga, -ga * al]]) - lam * np.diag([D1, D2])
+    amp = np.linalg.matrix_power(np.eye(2) + dt * J, steps) @ eps
+    got = np.array([(out[0] - c1)[0, 0, 0], (out[1] - c2)[0, 0, 0]])
+    np.testing.assert_allclose(got, amp, rtol=2e-5)
+
+
 def test_air_photostationary_state_bitwise(orc):
     # j NO2 = k NO O3 is a steady state of NO2 <-> NO + O3
     cfg = W.air((5, 4, 3), src=(0, 0, 0), src_rate=0.0, j=0.5, k=2.0)
@@ -328,7 +363,7 @@ def test_dirichlet_linear_profile_is_steady(orc):
     np.testing.assert_allclose(out, c0, rtol=0, atol=1e-6)
 
 
-@pytest.mark.parametrize("model", ["brusselator", "air", "ch_front"])
+@pytest.mark.parametrize("model", ["brusselator", "air", "ch_front", "turing"])
 def test_uniform_state_follows_the_scalar_ode(orc, model):
     # with every face periodic and no wind or source, a uniform state stays
     # uniform and each cell follows the forward-Euler map of the model's
@@ -351,6 +386,14 @@ def test_uniform_state_follows_the_scalar_ode(orc, model):
             no, no2, o3 = y
             net = j * no2 - k * no * o3          # NO2 -> NO + O3 minus NO + O3 -> NO2
             return [net, -net, net]
+    elif model == "turing":
+        cfg = W.turing(shape=(5, 4, 6))
+        y0 = [0.7, 0.4]
+        al, be, ga = (cfg["params"][k] for k in ("alpha", "beta", "gamma"))
+
+        def rate(y):
+            # activator-inhibitor kinetics of Table 1, row 2
+            return [y[0] - y[0] ** 3 - y[1], ga * (y[0] - al * y[1] - be)]
     else:
         cfg = W.ch_front(shape=(5, 4, 6))
         y0 = [0.9, 0.6, 0.3]
@@ -568,7 +611,8 @@ def test_oracles_agree_on_every_family(orc):
              W.with_(W.brusselator(shape=(7, 9, 6), bc="neumann"), stencil=19),
              W.with_(W.brusselator(8), stencil=19),
              W.with_(W.air((9, 7, 6), src=(8, 1, 3)), stencil=19, D=[[0.1] * 3] * 3),
-             W.with_(W.ch_front(shape=(8, 7, 9)), stencil=19)]
+             W.with_(W.ch_front(shape=(8, 7, 9)), stencil=19),
+             W.turing(shape=(9, 8, 7)), W.turing(shape=(7, 9, 8), stencil=19)]
     for cfg in cases:
         f = W.initial_fields(cfg)
         a = orc.run(cfg, f, 9)
