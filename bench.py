@@ -490,6 +490,16 @@ def run_extras(args, Sim, Batch, torch):
         tun = sim.autotune()
         t = _timed_steps(torch, sim, 2000)
         out["brusselator_256_19pt"] = _entry(W.cell_count(cfg), 2000, t, 16, tun)
+    # the Turing system of Table 1 with its parameters on the paper's 192^3
+    # grid and its 19-point stencil (2 levels x 2 species x 28 MiB: the
+    # working set fits the 129 MB L2), and on 256^3 (beyond L2)
+    for n in (192, 256):
+        tcfg = W.turing(n, stencil=19)
+        with Sim(tcfg) as sim:
+            sim.set_fields(W.initial_fields_torch(tcfg, "cuda"))
+            tun = sim.autotune()
+            t = _timed_steps(torch, sim, 2000)
+            out[f"turing_{n}_19pt"] = _entry(W.cell_count(tcfg), 2000, t, 16, tun)
     # the paper's own kernel designs on the same problem (ablation baselines:
     # Shared method and Moving Tiles, Section 4.1, Tables 4-5)
     for kern in ("shared", "tiles"):

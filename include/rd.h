@@ -70,9 +70,13 @@ typedef enum rd_model {
                                  biharmonic as two chained Laplacians,
                                  Section 4.1); params[0]=k, [1]=M, [2]=kappa;
                                  species c has no Fickian term (D[2] = 0)    */
-    RD_MODEL_AIR = 3          /* 3 species NO, NO2, O3: NO2 -> NO + O3 at
+    RD_MODEL_AIR = 3,         /* 3 species NO, NO2, O3: NO2 -> NO + O3 at
                                  j NO2, NO + O3 -> NO2 at k NO O3;
                                  params[0]=j, [1]=k                          */
+    RD_MODEL_TURING = 4       /* 2 species, the activator-inhibitor system of
+                                 Table 1 (row 2): R_1 = c1 - c1^3 - c2,
+                                 R_2 = gamma (c1 - alpha c2 - beta);
+                                 params[0]=alpha, [1]=beta, [2]=gamma        */
 } rd_model;
 
 typedef enum rd_storage {

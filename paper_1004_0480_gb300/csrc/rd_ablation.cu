@@ -22,6 +22,7 @@
 // one after.  The paper's BW = 16 matched the half-warp coalescing rules of
 // its first-generation GPUs; here BW = 32, one warp per row.
 #include "rd_ablation.h"
+#include "rd_model_turing.h"
 #include "rd_step_kernel.cuh"
 
 namespace rdk {
@@ -199,6 +200,7 @@ cudaError_t launch_ablation(int kernel, int model, const LaunchArgs& a, cudaStre
     case RD_MODEL_DIFFUSION: return launch_ablation_model<MDiffusion>(kernel, a, st);
     case RD_MODEL_BRUSSELATOR: return launch_ablation_model<MBrusselator>(kernel, a, st);
     case RD_MODEL_AIR: return launch_ablation_model<MAir>(kernel, a, st);
+    case RD_MODEL_TURING: return launch_ablation_model<MTuring>(kernel, a, st);
     }
     return cudaErrorInvalidValue;
 }

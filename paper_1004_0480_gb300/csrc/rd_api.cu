@@ -23,6 +23,7 @@
 #include "rd.h"
 #include "rd_internal.h"
 #include "rd_ablation.h"
+#include "rd_model_turing.h"
 #include "rd_step19.h"
 
 using namespace rdk;
@@ -75,7 +76,11 @@ int elem_bytes(int storage) { return storage == RD_STORE_BF16 ? 2 : 4; }
 int stencil_of(const rd_config& g) { return g.stencil == 19 ? 19 : 7; }
 
 int species_of(int model) {
-    return model == RD_MODEL_DIFFUSION ? 1 : model == RD_MODEL_BRUSSELATOR ? 2 : 3;
+    switch (model) {
+    case RD_MODEL_DIFFUSION: return 1;
+    case RD_MODEL_BRUSSELATOR: case RD_MODEL_TURING: return 2;
+    default: return 3;
+    }
 }
 
 size_t smem_of(int model, int storage, int T, int ty, int stencil = 7) {
@@ -85,6 +90,7 @@ size_t smem_of(int model, int storage, int T, int ty, int stencil = 7) {
     case RD_MODEL_BRUSSELATOR: return smem_brusselator(storage, T, ty);
     case RD_MODEL_CH_FRONT: return smem_ch_front(storage, T, ty);
     case RD_MODEL_AIR: return smem_air(storage, T, ty);
+    case RD_MODEL_TURING: return smem_turing(storage, T, ty);
     }
     return 0;
 }
@@ -111,6 +117,7 @@ cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int
         case RD_MODEL_DIFFUSION: return launch19_diffusion(storage, a, grid, smem, st, occ);
         case RD_MODEL_BRUSSELATOR: return launch19_brusselator(storage, a, grid, smem, st, occ);
         case RD_MODEL_AIR: return launch19_air(storage, a, grid, smem, st, occ);
+        case RD_MODEL_TURING: return launch19_turing(storage, a, grid, smem, st, occ);
         }
         return cudaErrorInvalidValue;
     }
@@ -119,6 +126,7 @@ cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int
     case RD_MODEL_BRUSSELATOR: return launch_brusselator(storage, T, a, grid, smem, st, occ);
     case RD_MODEL_CH_FRONT: return launch_ch_front(storage, T, a, grid, smem, st, occ);
     case RD_MODEL_AIR: return launch_air(storage, T, a, grid, smem, st, occ);
+    case RD_MODEL_TURING: return launch_turing(storage, T, a, grid, smem, st, occ);
     }
     return cudaErrorInvalidValue;
 }
@@ -246,6 +254,7 @@ rd_status validate(const rd_config* c) {
     case RD_MODEL_BRUSSELATOR: want = 2; break;
     case RD_MODEL_CH_FRONT: want = 3; break;
     case RD_MODEL_AIR: want = 3; break;
+    case RD_MODEL_TURING: want = 2; break;
     default: return fail(nullptr, RD_EINVAL, "unknown model %d", c->model);
     }
     if (c->nspecies != want) {
@@ -482,6 +491,11 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
     case RD_MODEL_AIR:
         d.p[0] = (float)g.params[0];
         d.p[1] = (float)g.params[1];
+        break;
+    case RD_MODEL_TURING:
+        d.p[0] = (float)g.params[0];
+        d.p[1] = (float)g.params[1];
+        d.p[2] = (float)g.params[2];
         break;
     default: break;
     }
@@ -1065,7 +1079,8 @@ const char* rd_last_error(const rd_ctx* c) { return c ? c->err : g_err; }
 rd_status rd_batch_create(int32_t model, int32_t storage, rd_batch** out) {
     if (!out) return RD_EINVAL;
     *out = nullptr;
-    if (model < RD_MODEL_DIFFUSION || model > RD_MODEL_AIR) return fail(nullptr, RD_EINVAL, "bad model");
+    if (model < RD_MODEL_DIFFUSION || model > RD_MODEL_TURING)
+        return fail(nullptr, RD_EINVAL, "bad model");
     if (storage != RD_STORE_F32 && storage != RD_STORE_BF16) return fail(nullptr, RD_EINVAL, "bad storage");
     rd_batch* b = new (std::nothrow) rd_batch();
     if (!b) return RD_ENOMEM;

@@ -18,6 +18,7 @@ _PARAM_ORDER = {
     "brusselator": ("a", "b"),
     "ch_front": ("k", "M", "kappa"),
     "air": ("j", "k"),
+    "turing": ("alpha", "beta", "gamma"),
 }
 
 

@@ -74,6 +74,7 @@ def family_cases():
         "ch_front_aniso_source": (ch_src, TOL_NONLIN),
         "air_neumann": (W.air(SHAPE, src=(5, 17, 2)), TOL_NONLIN),
         "air_periodic": (per_air, TOL_NONLIN),
+        "turing_table1": (W.turing(shape=SHAPE), TOL_NONLIN),
     }
 
 
@@ -195,13 +196,14 @@ def test_checkpoint_resume_is_bitwise(rd):
     assert np.array_equal(full, resumed)
 
 
-@pytest.mark.parametrize("model", ["diffusion", "brusselator", "ch_front", "air"])
+@pytest.mark.parametrize("model", ["diffusion", "brusselator", "ch_front", "air", "turing"])
 def test_batch_matches_standalone_bitwise(rd, model):
     sizes = [(23, 17, 11), (140, 9, 14), (16, 33, 25), (70, 20, 8)]
     mk = {"diffusion": lambda s, i: W.diffusion_blob(shape=s, seed=i),
           "brusselator": lambda s, i: W.brusselator(shape=s, seed=i),
           "ch_front": lambda s, i: W.ch_front(shape=s, seed=i),
-          "air": lambda s, i: W.air(s, src=(1, 2, 3), seed=i)}[model]
+          "air": lambda s, i: W.air(s, src=(1, 2, 3), seed=i),
+          "turing": lambda s, i: W.turing(shape=s, seed=i)}[model]
     cfgs = [mk(s, i) for i, s in enumerate(sizes)]
     steps = 15
     tun = dict(tsteps=1, tile_q=16, tile_y=4, zchunk=6, graph=1)
@@ -391,6 +393,15 @@ def test_air_200_steps(rd, orc):
     f = W.initial_fields(cfg)
     ref = orc.run(cfg, f, 200)
     assert rel_err(run_gpu(rd, cfg, 200, fields=f), ref) <= TOL_NONLIN
+
+
+def test_turing_table1_200_steps(rd, orc):
+    # the activator-inhibitor system with the paper's Table 1 parameters
+    for stencil in (7, 19):
+        cfg = W.turing(shape=(48, 40, 36), stencil=stencil)
+        f = W.initial_fields(cfg)
+        ref = orc.run(cfg, f, 200)
+        assert rel_err(run_gpu(rd, cfg, 200, fields=f), ref) <= TOL_NONLIN
 
 
 def test_brusselator_256_full_size_few_steps(rd, orc):

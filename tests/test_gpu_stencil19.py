@@ -70,6 +70,9 @@ def family_cases():
         "brusselator_mixed_bc": (mixed_b, TOL_NONLIN),
         "air_wind_source": (air_iso, TOL_NONLIN),
         "air_held_top_reverse_wind": (air_held, TOL_NONLIN),
+        # Table 1 parameters with larger initial noise (the paper's +-5e-4
+        # would not separate the stencils in 13 steps)
+        "turing_table1": (W.turing(shape=SHAPE, stencil=19, sigma=0.3), TOL_NONLIN),
     }
 
 
