@@ -27,11 +27,12 @@
 //    reads the neighbours of plane z0-1, whose slot the copy of step z0+1
 //    refills; one more barrier after those reads keeps the rule.
 //
-// Boundary rules are those of the 7-point kernels: ghost rows, vectors and
-// planes are copied in under each axis's rule (zero flux: the face value;
-// periodic: wrapped), so an edge ghost composes the rules of the two axes
-// it crosses, as the paper fills its edges after its faces (Section 4.1); a
-// held layer's cell takes its bc value.
+// Boundary rules are those of the 7-point kernels: ghost rows, planes and
+// vectors are copied in under each axis's rule (zero flux: the face value;
+// periodic: wrapped), and a thread at a zero-flux x face reads the cells
+// beyond it from its own column (xface_offsets), so an edge ghost composes
+// the rules of the two axes it crosses, as the paper fills its edges after
+// its faces (Section 4.1); a held layer's cell takes its bc value.
 #pragma once
 
 #include "rd_step19.h"
@@ -52,19 +53,24 @@ template <class M, class ST> struct Layout19 {
 };
 
 // Own vector c and the sums Z, W of one species plane at the thread's 4
-// cells; ``p`` points at the own vector in the ring.
+// cells; ``p`` points at the own vector in the ring, ``loff`` / ``roff``
+// are the byte offsets of the x neighbours beside it (xface_offsets: at a
+// zero-flux x face, the thread's own face cell, also in the rows above and
+// below, where the edge ghost composes both faces' rules).
 template <class ST>
-__device__ __forceinline__ void plane_sums19(const unsigned char* p, float (&c)[kVEC],
-                                             float (&zs)[kVEC], float (&ws)[kVEC]) {
-    constexpr int EB = (int)sizeof(ST);
-    constexpr int RWB = kRW * EB;
+__device__ __forceinline__ void plane_sums19(const unsigned char* p, int loff, int roff,
+                                             float (&c)[kVEC], float (&zs)[kVEC],
+                                             float (&ws)[kVEC]) {
+    constexpr int RWB = kRW * (int)sizeof(ST);
     float ym[kVEC], yp[kVEC];
     lds_vec<ST>(p, c);
     lds_vec<ST>(p - RWB, ym);
     lds_vec<ST>(p + RWB, yp);
-    const float l = lds_one<ST>(p - EB), r = lds_one<ST>(p + kVEC * EB);
-    const float ul = lds_one<ST>(p - RWB - EB), ur = lds_one<ST>(p - RWB + kVEC * EB);
-    const float dl = lds_one<ST>(p + RWB - EB), dr = lds_one<ST>(p + RWB + kVEC * EB);
+    const unsigned char* pl = p + loff;
+    const unsigned char* pr = p + roff;
+    const float l = lds_one<ST>(pl), r = lds_one<ST>(pr);
+    const float ul = lds_one<ST>(pl - RWB), ur = lds_one<ST>(pr - RWB);
+    const float dl = lds_one<ST>(pl + RWB), dr = lds_one<ST>(pr + RWB);
 #pragma unroll
     for (int e = 0; e < kVEC; ++e) {
         const float xm = e ? c[e - 1] : l;
@@ -207,6 +213,8 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
         const unsigned xyf = xy_faces(xs, y, nx, ny);
         const Fetch fo = halo_warp ? Fetch{0, 0, 0, 0}
                                    : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB, true);
+        int loff, roff;                           // x neighbours beside the own vector
+        xface_offsets<ST>(xs, nx, px, loff, roff);
         float k6[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) k6[s] = __fdiv_rn(sd.kx[s], 6.0f);
@@ -262,8 +270,8 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
                         float cm[kVEC], wm[kVEC];
-                        plane_sums19<ST>(Pm + s * PEB, cm, zsum_m[s], wm);
-                        plane_sums19<ST>(Pc + s * PEB, c_0[s], zsum_0[s], wsum_0[s]);
+                        plane_sums19<ST>(Pm + s * PEB, loff, roff, cm, zsum_m[s], wm);
+                        plane_sums19<ST>(Pc + s * PEB, loff, roff, c_0[s], zsum_0[s], wsum_0[s]);
                     }
                 }
                 __syncthreads();   // plane z0 - 1 is refilled at the next step
@@ -272,7 +280,8 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
                 const unsigned char* Pp = ring + sp * SLOTB + own_b;
                 float c_p[S][kVEC], zsum_p[S][kVEC], wsum_p[S][kVEC], inc[S][kVEC];
 #pragma unroll
-                for (int s = 0; s < S; ++s) plane_sums19<ST>(Pp + s * PEB, c_p[s], zsum_p[s], wsum_p[s]);
+                for (int s = 0; s < S; ++s)
+                    plane_sums19<ST>(Pp + s * PEB, loff, roff, c_p[s], zsum_p[s], wsum_p[s]);
 #pragma unroll
                 for (int e = 0; e < kVEC; ++e) {
                     float cv[S], iv[S];
@@ -295,8 +304,8 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
                                                       wsum_0[s][e]));
                     float left = 0.0f, right = 0.0f;
                     if (!PLAIN && cx != 0.0f) {
-                        left = lds_one<ST>(Pc + s * PEB - EB);
-                        right = lds_one<ST>(Pc + s * PEB + kVEC * EB);
+                        left = lds_one<ST>(Pc + s * PEB + loff);
+                        right = lds_one<ST>(Pc + s * PEB + roff);
                     }
                     species19<PLAIN>(sd, s, k6[s], c_0[s], lap6, inc[s], cx, left, right,
                                      src_here, px, xs, o);

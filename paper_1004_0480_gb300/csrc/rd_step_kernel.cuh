@@ -641,7 +641,10 @@ template <class M, class ST> struct Layout1 {
 };
 
 // How one vector is fetched: 1 = one async copy, 2 = element by element
-// with wrapped x, 0 = nothing (outside a zero-flux face).
+// (wrapped x, or clamped x for a vector straddling a zero-flux face), 0 =
+// nothing (a vector wholly outside a zero-flux x face, or a row outside a
+// face that is never read: the kernels take the face cell from the
+// thread's own vector instead, see xface_offsets).
 struct Fetch {
     int mode;
     int goff;    // element offset of row + x within a plane
@@ -669,8 +672,10 @@ __device__ __forceinline__ Fetch make_fetch(int yrow, int xs, int nx, int ny, in
         if (xw % kVEC == 0 && xw + kVEC <= nx) { f.mode = 1; f.goff = row + xw; }
         else { f.mode = 2; f.goff = row; }
     } else if (clamp) {
-        f.mode = 2;                               // ghost cells = face cell
-        f.goff = row;
+        if (xs < nx && xs + kVEC > 0) {           // straddles the face: ghost
+            f.mode = 2;                           // cells = face cell
+            f.goff = row;
+        }
     } else if (xs >= 0 && xs < nx) {
         f.mode = 1;                               // last vector: tail in the row padding
         f.goff = row + xs;
@@ -703,6 +708,21 @@ __device__ __forceinline__ void fetch_all(const Fetch& f, unsigned char* plane_b
     }
 }
 
+// Byte offsets, from a thread's own vector in a plane buffer, of the x
+// neighbours beside it: the element left of element 0 and right of element
+// 3.  At a zero-flux x face the ghost there equals the face cell, which is
+// the thread's own element 0 (left face) or 3 (a vector ending at the right
+// face), so those offsets point into the own vector and the vectors outside
+// the face are never copied (element-by-element copies of them had cost a
+// quarter of the step).  A vector straddling the right face (nx not a
+// multiple of 4) holds its clamped ghosts itself.
+template <class ST>
+__device__ __forceinline__ void xface_offsets(int xs, int nx, bool px, int& loff, int& roff) {
+    constexpr int EB = (int)sizeof(ST);
+    loff = (!px && xs == 0) ? 0 : -EB;
+    roff = (!px && xs + kVEC == nx) ? (kVEC - 1) * EB : kVEC * EB;
+}
+
 template <class ST>
 __device__ __forceinline__ void lds_vec(const unsigned char* p, float (&v)[kVEC]) {
     Store<ST>::load(reinterpret_cast<const ST*>(p), v);
@@ -713,11 +733,13 @@ __device__ __forceinline__ float lds_one(const unsigned char* p) {
 }
 
 // Zero-flux ghost cells are copied in as face values at distance one (rows,
-// vectors and planes), as the paper sets its boundary layer before each
-// step; every neighbour then sits at a fixed offset from the thread's own
-// vector.  An upwind inflow face sees a zero gradient, and a held layer's
-// ghost only feeds the held cell's own update, which is replaced by its bc
-// value, so this is exact for every one-step problem.
+// planes, and vectors straddling the face), as the paper sets its boundary
+// layer before each step; a thread at an x face reads its x neighbour
+// beyond the face from its own vector (xface_offsets).  Every other
+// neighbour sits at a fixed offset from the thread's own vector.  An upwind
+// inflow face sees a zero gradient, and a held layer's ghost only feeds the
+// held cell's own update, which is replaced by its bc value, so this is
+// exact for every one-step problem.
 // PLAIN: no held layer, point source or wind, and every species isotropic;
 // the update then needs no per-plane or per-species branches.
 template <class M, class ST, bool ONE, int MINB, bool PLAIN>
@@ -802,6 +824,8 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
         const unsigned xyf = xy_faces(xs, y, nx, ny);
         const Fetch fo = halo_warp ? Fetch{0, 0, 0, 0}
                                    : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB, true);
+        int loff, roff;                           // x neighbours beside the own vector
+        xface_offsets<ST>(xs, nx, px, loff, roff);
         __syncthreads();   // halo descriptors written
 
         // ---- the march: plane nld is fetched P planes ahead into slot sl;
@@ -885,8 +909,8 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                     const float (&zp)[kVEC] = own_p[s];
                     lds_vec<ST>(Ps - RWB, ym);
                     lds_vec<ST>(Ps + RWB, yp);
-                    const float left = lds_one<ST>(Ps - EB);
-                    const float right = lds_one<ST>(Ps + kVEC * EB);
+                    const float left = lds_one<ST>(Ps + loff);
+                    const float right = lds_one<ST>(Ps + roff);
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e) {
                         xm[e] = e ? cen[s][e - 1] : left;
