@@ -145,6 +145,19 @@ def test_validation_of_the_19_point_stencil(lib):
     assert q(_cfg(air)) == L.RD_OK
 
 
+def test_validation_of_the_turing_model(lib):
+    sz = ctypes.c_size_t()
+    q = lambda c: lib.rd_query_sizes(ctypes.byref(c), ctypes.byref(sz), None)
+    cfg = W.turing(shape=(16, 8, 8))
+    assert q(_cfg(cfg)) == L.RD_OK
+    assert sz.value == 2 * 2 * 8 * 8 * 32 * 4      # rows of 16 cells padded to 32
+    assert q(_cfg(cfg, nspecies=3)) == L.RD_EINVAL
+    assert q(_cfg(W.with_(cfg, stencil=19))) == L.RD_OK
+    # the Table 1 time step is inside both stencils' bounds; ten times it is not
+    assert q(_cfg(W.with_(cfg, dt=cfg["dt"] * 10))) == L.RD_EUNSTABLE
+    assert q(_cfg(cfg, model=5)) == L.RD_EINVAL
+
+
 def test_bf16_rows_are_128_bytes(lib):
     from paper_1004_0480_gb300.sim import make_config
     c = make_config(W.diffusion_blob(shape=(70, 3, 2)), storage="bf16")
