@@ -19,6 +19,10 @@ CASES = {
     "brusselator_periodic_8": (W.brusselator(8), 20),
     "ch_front_10x9x8": (W.ch_front(shape=(10, 9, 8)), 20),
     "air_11x7x6": (W.air((11, 7, 6), src=(4, 3, 2)), 20),
+    "brusselator_19pt_neumann_9x8x7": (W.with_(W.brusselator(shape=(9, 8, 7), bc="neumann"),
+                                               stencil=19), 20),
+    "turing_table1_9x8x7": (W.turing(shape=(9, 8, 7), sigma=0.3), 20),
+    "turing_table1_19pt_9x8x7": (W.turing(shape=(9, 8, 7), sigma=0.3, stencil=19), 20),
 }
 SAMPLES = [(0, 0, 0), (1, 2, 3), (5, 4, 2), (6, 6, 5), (3, 0, 1)]   # (x, y, z)
 
