@@ -1,0 +1,104 @@
+"""Z-slab decomposition of one problem over 2 and 3 CPU ranks (gloo): each
+rank steps its slab with the FP64 oracle and exchanges ghost planes after
+every step; the owned planes of all ranks must equal the undivided oracle
+result bit for bit (same neighbours, same arithmetic per cell)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+from paper_1004_0480_gb300 import workloads as W
+from paper_1004_0480_gb300 import zslab as Z
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _cases():
+    per_b = W.brusselator(shape=(9, 7, 13))                       # periodic z: a ring
+    neu_b = W.brusselator(shape=(10, 6, 11), bc="neumann")
+    front = W.ch_front(shape=(8, 7, 14))                          # halo 2, a held at z = 0
+    air = W.air((9, 8, 12), src=(4, 3, 6))                        # source inside a middle slab
+    air["wind"] = dict(kind="const", u0=0.7)
+    air["bc"][0][5] = "dirichlet"                                 # held NO layer on top
+    air["bc_value"] = [[0.0] * 5 + [0.05], [0.0] * 6, [0.0] * 6]
+    tur19 = W.turing(shape=(8, 9, 10), sigma=0.3, stencil=19)
+    per19 = W.with_(W.brusselator(shape=(8, 6, 12)), stencil=19)
+    return {"brusselator_periodic": per_b, "brusselator_neumann": neu_b,
+            "ch_front": front, "air_const_wind_held_top": air,
+            "turing_19pt": tur19, "brusselator_19pt_periodic": per19}
+
+
+CASES = _cases()
+STEPS = 7
+
+
+def _rank(rank, ws, port, names, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    import oracle
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        for name in names:
+            cfg = CASES[name]
+            p = Z.plan(cfg, ws, rank)
+            f = Z.scatter(W.initial_fields(cfg).astype(np.float64), p)
+            f = Z.run(f, p, STEPS, lambda g, n, c=p.cfg: oracle.run(c, g, n), dist, torch)
+            out[(name, rank)] = (p.z0, p.z1, np.array(Z.owned(f, p)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(240)
+@pytest.mark.parametrize("ws", [2, 3])
+def test_slabs_equal_the_undivided_grid(orc, ws):
+    names = sorted(CASES)
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_rank, args=(r, ws, port, names, out)) for r in range(ws)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(200)
+            assert p.exitcode == 0
+        res = dict(out)
+    for name in names:
+        cfg = CASES[name]
+        ref = orc.run(cfg, W.initial_fields(cfg).astype(np.float64), STEPS)
+        got = np.empty_like(ref)
+        covered = 0
+        for r in range(ws):
+            z0, z1, f = res[(name, r)]
+            got[:, z0:z1] = f
+            covered += z1 - z0
+        assert covered == cfg["shape"][2]
+        assert np.array_equal(got, ref), name
+
+
+def test_split_and_plan_host_logic():
+    assert Z.split(10, 3) == [(0, 4), (4, 7), (7, 10)]
+    with pytest.raises(ValueError):
+        Z.split(2, 3)
+    front = W.ch_front(shape=(8, 8, 6))
+    p = Z.plan(front, 3, 1)
+    assert (p.lo, p.hi, p.lo_peer, p.hi_peer) == (2, 2, 0, 2)
+    assert p.cfg["shape"] == (8, 8, 2 + 4)
+    p0 = Z.plan(front, 3, 0)
+    assert (p0.lo, p0.lo_peer) == (0, None)
+    assert p0.cfg["bc"][0][4] == "dirichlet"       # the held layer stays on rank 0
+    per = W.brusselator(shape=(8, 8, 8))
+    q = Z.plan(per, 2, 0)
+    assert (q.lo_peer, q.hi_peer, q.lo, q.hi) == (1, 1, 1, 1)
+    assert q.cfg["bc"][0][4] == q.cfg["bc"][0][5] == "neumann"
+    with pytest.raises(ValueError):
+        Z.plan(W.air((8, 8, 8), src=(1, 1, 1)), 2, 0)  # logarithmic wind
+    with pytest.raises(ValueError):
+        Z.plan(W.ch_front(shape=(8, 8, 5)), 3, 0)      # a slab thinner than the halo
