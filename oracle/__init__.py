@@ -33,7 +33,7 @@ _HDR = os.path.join(_HERE, "rd_oracle.h")
 MAXS = 4
 _BC = {"neumann": 0, "periodic": 1, "dirichlet": 2}
 _MODEL = {"diffusion": 0, "brusselator": 1, "ch_front": 2, "air": 3, "turing": 4}
-_WIND = {None: 0, "log": 1, "const": 2}
+_WIND = {None: 0, "log": 1, "const": 2, "table1": 3}
 
 
 class OrcProblem(ctypes.Structure):
@@ -51,6 +51,8 @@ class OrcProblem(ctypes.Structure):
         ("src_z", ctypes.c_int32), ("src_species", ctypes.c_int32),
         ("src_rate", ctypes.c_double),
         ("stencil", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("w3", ctypes.c_double * 4),
+        ("n0", ctypes.c_int64),
     ]
 
 
@@ -112,7 +114,9 @@ def make_problem(cfg) -> OrcProblem:
         p.p[i] = cfg["params"][name]
     w = cfg.get("wind")
     p.wind_kind = _WIND[w["kind"] if w else None]
-    p.wind_u0 = w["u0"] if w else 0.0
+    p.wind_u0 = w.get("u0", 0.0) if w else 0.0
+    if w and w["kind"] == "table1":
+        p.w3[0], p.w3[1], p.w3[2], p.w3[3] = w["ux"], w["uy"], w["uz_amp"], w["uz_tau"]
     src = cfg.get("source")
     if src:
         p.src_x, p.src_y, p.src_z = src["x"], src["y"], src["z"]
@@ -124,15 +128,17 @@ def make_problem(cfg) -> OrcProblem:
     return p
 
 
-def run(cfg, fields, nsteps) -> np.ndarray:
+def run(cfg, fields, nsteps, n0=0) -> np.ndarray:
     """Advance ``fields`` (S, nz, ny, nx) by ``nsteps`` steps in FP64 with
-    the C oracle; returns a new float64 array."""
+    the C oracle, the first step having index ``n0`` (its time is n0 dt);
+    returns a new float64 array."""
     lib = _load()
     nx, ny, nz = cfg["shape"]
     st = np.ascontiguousarray(np.asarray(fields, dtype=np.float64)).copy()
     if st.shape != (cfg["nspecies"], nz, ny, nx):
         raise ValueError(f"fields shape {st.shape} does not match the problem")
     p = make_problem(cfg)
+    p.n0 = int(n0)
     rc = lib.orc_run(ctypes.byref(p),
                      st.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                      int(nsteps))

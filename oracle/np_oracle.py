@@ -101,7 +101,20 @@ def _wind_profile(cfg):
         return w["u0"] * np.log1p(z) / np.log1p(float(nz))
     if w["kind"] == "const":
         return np.full(nz, float(w["u0"]))
+    if w["kind"] == "table1":
+        return np.zeros(nz)          # the three-axis wind is applied in np_step
     raise ValueError(w["kind"])
+
+
+def _upwind(f, axis_cfg, u, bc_s, h):
+    """-u d f / d(axis), first-order upwind (backward difference for u > 0)."""
+    arr_axis = {0: 2, 1: 1, 2: 0}[axis_cfg]
+    lo, hi = _shifted(f, arr_axis, _periodic_axes(bc_s)[axis_cfg])
+    if u > 0:
+        return -u * (f - lo) / h
+    if u < 0:
+        return -u * (hi - f) / h
+    return np.zeros_like(f)
 
 
 def _rates(cfg, c):
@@ -131,8 +144,9 @@ def _rates(cfg, c):
     return r
 
 
-def np_step(cfg, c):
-    """One step; c has shape (S, nz, ny, nx) float64; returns the new array."""
+def np_step(cfg, c, n=0):
+    """Step number ``n`` (time n dt at its start); c has shape
+    (S, nz, ny, nx) float64; returns the new array."""
     S = cfg["nspecies"]
     h, dt = cfg["h"], cfg["dt"]
     stencil = cfg.get("stencil", 7)
@@ -158,7 +172,12 @@ def np_step(cfg, c):
             dxx, dyy, dzz = _second_diffs(c[s], bc_s, h)
             lap_c = dxx + dyy + dzz
             tend = rates[s] + D[0] * dxx + D[1] * dyy + D[2] * dzz
-        if cfg.get("wind"):
+        w = cfg.get("wind")
+        if w and w["kind"] == "table1":
+            u3 = (w["ux"], w["uy"], w["uz_amp"] * np.sin(n * dt / w["uz_tau"]))
+            for a in range(3):
+                tend = tend + _upwind(c[s], a, u3[a], bc_s, h)
+        elif w:
             per_x = bc_s[0] == "periodic"
             xm, xp = _shifted(c[s], 2, per_x)
             back = (c[s] - xm) / h
@@ -183,9 +202,10 @@ def np_step(cfg, c):
     return out
 
 
-def np_run(cfg, fields, nsteps):
-    """Advance ``fields`` (S, nz, ny, nx) by ``nsteps`` steps in float64."""
+def np_run(cfg, fields, nsteps, n0=0):
+    """Advance ``fields`` (S, nz, ny, nx) by ``nsteps`` steps in float64, the
+    first step having index ``n0``."""
     c = np.asarray(fields, dtype=np.float64).copy()
-    for _ in range(int(nsteps)):
-        c = np_step(cfg, c)
+    for k in range(int(nsteps)):
+        c = np_step(cfg, c, n0 + k)
     return c

@@ -96,8 +96,28 @@ static double laplacian(const orc_problem* p, const double* f, int s,
          + second_diff(p, f, s, x, y, z, 2);
 }
 
+/* Velocity (u_x, u_y, u_z) of ORC_WIND_3D at time t. */
+static void wind3(const orc_problem* p, double t, double u[3])
+{
+    u[0] = p->w3[0];
+    u[1] = p->w3[1];
+    u[2] = p->w3[2] * sin(t / p->w3[3]);
+}
+
+/* First-order upwind term -u d c / d(axis) at one cell: the backward
+ * difference for u > 0, the forward one for u < 0 (Section 4.1). */
+static double upwind(const orc_problem* p, const double* f, int s, int x, int y, int z,
+                     int axis, double u)
+{
+    const double c = f[lin(p, x, y, z)];
+    if (u > 0.0) return -u * (c - nb(p, f, s, x, y, z, axis, -1)) / p->h;
+    if (u < 0.0) return -u * (nb(p, f, s, x, y, z, axis, +1) - c) / p->h;
+    return 0.0;
+}
+
 double orc_wind(const orc_problem* p, int z)
 {
+    if (p->wind_kind == ORC_WIND_3D) return p->w3[0];
     if (p->wind_kind == ORC_WIND_LOG)
         return p->wind_u0 * log(1.0 + (double)z) / log(1.0 + (double)p->nz);
     if (p->wind_kind == ORC_WIND_CONST) return p->wind_u0;
@@ -125,6 +145,7 @@ static int check(const orc_problem* p)
     if (p->nx < 2 || p->ny < 2 || p->nz < 2) return -1;
     if (p->ns < 1 || p->ns > ORC_MAXS) return -1;
     if (!(p->h > 0.0) || !(p->dt > 0.0)) return -1;
+    if (p->wind_kind == ORC_WIND_3D && !(p->w3[3] != 0.0)) return -1;
     for (int s = 0; s < p->ns; ++s)
         for (int a = 0; a < 3; ++a)
             if ((p->bc[s][2 * a] == ORC_PERIODIC) != (p->bc[s][2 * a + 1] == ORC_PERIODIC))
@@ -189,8 +210,8 @@ static void reaction(const orc_problem* p, const double* v, double* r)
     }
 }
 
-/* One forward-Euler step from cur to nxt (Table 3, lines 4-10). */
-static void step(const orc_problem* p, double* cur, double* nxt, double* mu)
+/* One forward-Euler step from cur to nxt (Table 3), step index n. */
+static void step(const orc_problem* p, double* cur, double* nxt, double* mu, int64_t n)
 {
     const int nx = p->nx, ny = p->ny, nz = p->nz, ns = p->ns;
     const int64_t nc = (int64_t)nx * ny * nz;
@@ -225,7 +246,9 @@ static void step(const orc_problem* p, double* cur, double* nxt, double* mu)
                 double v[ORC_MAXS], r[ORC_MAXS];
                 for (int s = 0; s < ns; ++s) v[s] = cur[s * nc + i];
                 reaction(p, v, r);
-                const double u = orc_wind(p, z);
+                const double u = p->wind_kind == ORC_WIND_3D ? 0.0 : orc_wind(p, z);
+                double u3[3] = {0.0, 0.0, 0.0};
+                if (p->wind_kind == ORC_WIND_3D) wind3(p, (double)n * p->dt, u3);
                 for (int s = 0; s < ns; ++s) {
                     const double* f = cur + s * nc;
                     double rate = r[s];
@@ -234,6 +257,8 @@ static void step(const orc_problem* p, double* cur, double* nxt, double* mu)
                     else
                         for (int a = 0; a < 3; ++a)
                             rate += p->D[s][a] * second_diff(p, f, s, x, y, z, a);
+                    if (p->wind_kind == ORC_WIND_3D)
+                        for (int a = 0; a < 3; ++a) rate += upwind(p, f, s, x, y, z, a, u3[a]);
                     if (u != 0.0) {
                         /* first-order upwind: -u dc/dx from the upstream side */
                         if (u > 0.0)
@@ -267,7 +292,7 @@ int orc_run(const orc_problem* p, double* state, int64_t nsteps)
     double* cur = state;
     double* nxt = other;
     for (int64_t t = 0; t < nsteps; ++t) {
-        step(p, cur, nxt, mu);
+        step(p, cur, nxt, mu, p->n0 + t);
         double* tmp = cur; cur = nxt; nxt = tmp;
     }
     if (cur != state) memcpy(state, cur, sizeof(double) * nc * p->ns);

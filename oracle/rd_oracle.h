@@ -15,7 +15,8 @@
  *            the weights of eq. (4) (-24 centre, 2 face, 1 edge, 0
  *            corner); one diffusivity per species (D[s][0..2] equal);
  *   eq. (5)  forward Euler: c(t+dt) = c(t) + dt * [diffusion + R + ...],
- *            every term taken from level t;
+ *            every term taken from level t (the time-dependent wind of
+ *            ORC_WIND_3D too, at t = n dt for step n = 0, 1, ...);
  *   Table 3  host loop: set boundary values, update all points from the
  *            "first" arrays into the "second" arrays, swap.
  *   Section 4.1 (Cahn-Hilliard): the biharmonic term is computed as a
@@ -45,7 +46,7 @@ extern "C" {
 
 enum { ORC_NEUMANN = 0, ORC_PERIODIC = 1, ORC_DIRICHLET = 2 };
 enum { ORC_DIFFUSION = 0, ORC_BRUSSELATOR = 1, ORC_CH_FRONT = 2, ORC_AIR = 3, ORC_TURING = 4 };
-enum { ORC_WIND_NONE = 0, ORC_WIND_LOG = 1, ORC_WIND_CONST = 2 };
+enum { ORC_WIND_NONE = 0, ORC_WIND_LOG = 1, ORC_WIND_CONST = 2, ORC_WIND_3D = 3 };
 
 #define ORC_MAXS 4
 
@@ -68,6 +69,11 @@ typedef struct orc_problem {
     double src_rate;
     int32_t stencil;                 /* 7 (or 0): 7-point; 19: eqs. (3)-(4) */
     int32_t pad0;
+    /* ORC_WIND_3D (Table 1, row 4): u = (w3[0], w3[1], w3[2] sin(t / w3[3]))
+     * with t the time at the start of the step, n dt; first-order upwind
+     * along each axis                                                      */
+    double w3[4];
+    int64_t n0;                      /* index of the first step orc_run takes */
 } orc_problem;
 
 /* Advance ``state`` (ns x nz x ny x nx doubles, x fastest) by nsteps

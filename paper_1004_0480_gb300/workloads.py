@@ -141,6 +141,23 @@ def air(shape=(512, 512, 64), steps=5000, dt=0.2, Kh=0.1, Kz=0.02, j=0.5,
                 init="air")
 
 
+def plume(shape=(144, 144, 384), steps=20000, dt=5.0, D=100.0, h=100.0, ux=5.0, uy=1.0,
+          uz_amp=5.0, uz_tau=500.0, E=10.0, src=None, seed=6):
+    """Inert plume of Table 1, row 4, with its parameters: dc/dt =
+    -div(u c) + D Lap c + E, u = (5, 1, 5 sin(t / 500 s)) m/s, D = 100 m^2/s,
+    h = 100 m, dt = 5 s, a point emission E = 10 per second, c0 = 0, zero
+    flux; the 144 x 144 x 384 grid of Figure 7.  The paper does not place
+    the source: by default a quarter of the way along x, centred in y, an
+    eighth of the way up z."""
+    nx, ny, nz = shape
+    sx, sy, sz = src if src is not None else (nx // 4, ny // 2, nz // 8)
+    return dict(name=f"plume_{nx}x{ny}x{nz}", model="diffusion", shape=(nx, ny, nz),
+                nspecies=1, h=h, dt=dt, D=[[D] * 3], bc=_bc(NEU, 1), bc_value=[[0.0] * 6],
+                params={}, source=dict(x=sx, y=sy, z=sz, species=0, rate=E),
+                wind=dict(kind="table1", ux=ux, uy=uy, uz_amp=uz_amp, uz_tau=uz_tau),
+                steps=steps, seed=seed, init="zero")
+
+
 def with_(cfg, **kw):
     """Copy of a problem with some entries replaced."""
     c = copy.deepcopy(cfg)
@@ -192,6 +209,8 @@ def initial_fields(cfg, seed=None, dtype=np.float32):
         for sp in range(2):
             u = uniform01(s, sp, ncell).reshape(nz, ny, nx)
             out[sp] = 1.0 + sig * (2.0 * u - 1.0)
+    elif kind == "zero":
+        out[:] = 0.0
     elif kind == "uniform_noise":
         for sp in range(S):
             out[sp] = uniform01(s, sp, ncell).reshape(nz, ny, nx)
@@ -352,6 +371,8 @@ def initial_fields_torch(cfg, device, seed=None):
         for sp in range(2):
             u = uniform01_torch(s, sp, ncell, device).reshape(nz, ny, nx)
             out[sp] = 1.0 + sig * (2.0 * u - 1.0)
+    elif kind == "zero":
+        out[:] = 0.0
     elif kind == "uniform_noise":
         for sp in range(S):
             out[sp] = uniform01_torch(s, sp, ncell, device).reshape(nz, ny, nx)

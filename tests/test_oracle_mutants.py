@@ -45,6 +45,11 @@ MUTANTS = {
     "turing_cubic_term": ("r[0] = c1 - c1 * c1 * c1 - c2;", "r[0] = c1 - c1 * c1 - c2;"),
     "turing_alpha_dropped": ("(c1 - alpha * c2 - beta)", "(c1 - c2 - beta)"),
     "turing_gamma_dropped": ("r[1] = gamma * (", "r[1] = ("),
+    "wind3_time_of_step": ("wind3(p, (double)n * p->dt, u3)", "wind3(p, (double)(n + 1) * p->dt, u3)"),
+    "wind3_uz_phase": ("u[2] = p->w3[2] * sin(t / p->w3[3]);", "u[2] = p->w3[2] * cos(t / p->w3[3]);"),
+    "wind3_uy_from_ux": ("u[1] = p->w3[1];", "u[1] = p->w3[0];"),
+    "upwind_forward_difference": ("if (u < 0.0) return -u * (nb(p, f, s, x, y, z, axis, +1) - c) / p->h;",
+                                  "if (u < 0.0) return -u * (c - nb(p, f, s, x, y, z, axis, -1)) / p->h;"),
     "stencil19_centre_weight": ("{{1, 2, 1}, {2, -24, 2}, {1, 2, 1}}",
                                 "{{1, 2, 1}, {2, -26, 2}, {1, 2, 1}}"),
     "stencil19_diagonals_doubled": ("{{1, 2, 1}, {2, -24, 2}, {1, 2, 1}}",
@@ -68,10 +73,11 @@ class _Shim:
         self._lib = lib
         self.np_run = oracle.np_run
 
-    def run(self, cfg, fields, nsteps):
+    def run(self, cfg, fields, nsteps, n0=0):
         nx, ny, nz = cfg["shape"]
         st = np.ascontiguousarray(np.asarray(fields, dtype=np.float64)).copy()
         p = oracle.make_problem(cfg)
+        p.n0 = int(n0)
         rc = self._lib.orc_run(ctypes.byref(p),
                                st.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                int(nsteps))

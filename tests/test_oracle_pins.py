@@ -603,6 +603,107 @@ def test_stencil19_mass_conserved(orc, bc):
     assert not np.allclose(out, c0)
 
 
+# --------------------------------------------------------------------------
+# Table 1, row 4: the plume's three-axis, time-dependent wind
+# --------------------------------------------------------------------------
+def _plume_cfg(shape, **kw):
+    cfg = W.plume(shape=shape, src=(0, 0, 0), **kw)
+    return cfg
+
+
+def test_plume_linear_field_follows_uz_of_t(orc):
+    # c = z h is linear in z and uniform in x, y: away from the z faces the
+    # upwind difference is 1/h for either sign of u_z and the Laplacian is 0,
+    # so each step subtracts dt u_z(t_k) with t_k = k dt at the step's start;
+    # the run crosses a sign change of sin(t / tau)
+    nx, ny, nz = 4, 5, 40
+    dt, h, tau, amp = 5.0, 100.0, 20.0, 5.0
+    cfg = _plume_cfg((nx, ny, nz), dt=dt, h=h, uz_tau=tau, uz_amp=amp, E=0.0)
+    z = np.arange(nz) * h
+    c0 = np.broadcast_to(z[:, None, None], (nz, ny, nx))[None].copy()
+    n0, n = 3, 16
+    out = orc.run(cfg, c0, n, n0=n0)
+    drift = dt * sum(amp * math.sin(k * dt / tau) for k in range(n0, n0 + n))
+    assert any(math.sin(k * dt / tau) < 0 for k in range(n0, n0 + n))
+    inner = slice(n + 1, nz - n - 1)
+    np.testing.assert_allclose(out[0, inner], c0[0, inner] - drift, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("impl", ["c", "np"])
+def test_plume_mass_budget_periodic(orc, impl):
+    # periodic faces: upwind advection along every axis and diffusion move
+    # mass around but conserve it; the point source adds exactly E dt per step
+    cfg = _plume_cfg((6, 5, 7), dt=5.0, E=10.0)
+    cfg["bc"] = [["periodic"] * 6]
+    cfg["source"] = dict(x=2, y=3, z=4, species=0, rate=10.0)
+    c0 = W.uniform01(4, 0, 6 * 5 * 7).reshape(1, 7, 5, 6)
+    run = orc.run if impl == "c" else orc.np_run
+    out = run(cfg, c0, 25, 7)
+    assert out.sum() == pytest.approx(c0.sum() + 25 * 10.0 * 5.0, rel=1e-13)
+
+
+def _upwind_pair(n, periodic, u):
+    # 1-D matrix of -u d/dx, backward difference for u > 0, forward for u < 0,
+    # zero gradient beyond a zero-flux face
+    if u > 0:
+        B = -np.eye(n) + np.eye(n, k=-1)
+        if periodic:
+            B[0, -1] = 1.0
+        else:
+            B[0, 0] = 0.0
+        return u * B
+    if u < 0:
+        F = np.eye(n, k=1) - np.eye(n)
+        if periodic:
+            F[-1, 0] = 1.0
+        else:
+            F[-1, -1] = 0.0
+        return -u * F
+    return np.zeros((n, n))
+
+
+@pytest.mark.parametrize("bc", ["neumann", "periodic"])
+def test_plume_dense_operator_product(orc, bc):
+    # c_{k+1} = (I + dt A(t_k)) c_k + dt E e_src, with A(t) the Kronecker sum
+    # of the 7-point Laplacian and the three upwind matrices of u(t)
+    nx, ny, nz = 3, 4, 5
+    per = bc == "periodic"
+    D, h, dt, tau = 0.3, 1.0, 0.1, 0.25
+    ux, uy, amp = 0.7, -0.4, 0.9
+    cfg = _plume_cfg((nx, ny, nz), D=D, h=h, dt=dt, ux=ux, uy=uy, uz_amp=amp, uz_tau=tau,
+                     E=2.0)
+    cfg["bc"] = [[bc] * 6]
+    cfg["source"] = dict(x=1, y=2, z=3, species=0, rate=2.0)
+    Ix, Iy, Iz = np.eye(nx), np.eye(ny), np.eye(nz)
+    L = (np.kron(Iz, np.kron(Iy, _lap1d(nx, per))) + np.kron(Iz, np.kron(_lap1d(ny, per), Ix))
+         + np.kron(_lap1d(nz, per), np.kron(Iy, Ix))) / h ** 2
+    e = np.zeros(nx * ny * nz)
+    e[(3 * ny + 2) * nx + 1] = 1.0
+    c = W.uniform01(8, 0, nx * ny * nz)
+    c0 = c.copy()
+    n = 12
+    for k in range(n):
+        uz = amp * math.sin(k * dt / tau)
+        A = (D * L + np.kron(Iz, np.kron(Iy, _upwind_pair(nx, per, ux))) / h
+             + np.kron(Iz, np.kron(_upwind_pair(ny, per, uy), Ix)) / h
+             + np.kron(_upwind_pair(nz, per, uz), np.kron(Iy, Ix)) / h)
+        c = c + dt * (A @ c) + dt * 2.0 * e
+    out = orc.run(cfg, c0.reshape(1, nz, ny, nx), n).ravel()
+    np.testing.assert_allclose(out, c, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_plume_courant_one_shifts_along_y(orc, sign):
+    # u_y = +-h/dt, no diffusion, no u_x or u_z: an exact shift of one cell
+    # per step along y, in the direction of the wind
+    cfg = _plume_cfg((4, 9, 3), D=0.0, dt=2.0, h=1.0, ux=0.0, uy=sign * 0.5, uz_amp=0.0,
+                     E=0.0)
+    cfg["bc"] = [["periodic"] * 6]
+    c0 = W.uniform01(2, 0, 4 * 9 * 3).reshape(1, 3, 9, 4)
+    out = orc.run(cfg, c0, 5)
+    np.testing.assert_array_equal(out, np.roll(c0, int(sign) * 5, axis=2))
+
+
 def test_oracles_agree_on_every_family(orc):
     cases = [W.diffusion_blob(8), W.brusselator(8), W.ch_front(8),
              W.air((8, 8, 8), src=(3, 4, 2)),
@@ -612,7 +713,9 @@ def test_oracles_agree_on_every_family(orc):
              W.with_(W.brusselator(8), stencil=19),
              W.with_(W.air((9, 7, 6), src=(8, 1, 3)), stencil=19, D=[[0.1] * 3] * 3),
              W.with_(W.ch_front(shape=(8, 7, 9)), stencil=19),
-             W.turing(shape=(9, 8, 7)), W.turing(shape=(7, 9, 8), stencil=19)]
+             W.turing(shape=(9, 8, 7)), W.turing(shape=(7, 9, 8), stencil=19),
+             W.plume(shape=(9, 8, 10), src=(2, 3, 4)),
+             W.with_(W.plume(shape=(8, 9, 7), src=(5, 1, 2)), stencil=19)]
     for cfg in cases:
         f = W.initial_fields(cfg)
         a = orc.run(cfg, f, 9)
