@@ -32,7 +32,7 @@ _HDR = os.path.join(_HERE, "rd_oracle.h")
 
 MAXS = 4
 _BC = {"neumann": 0, "periodic": 1, "dirichlet": 2}
-_MODEL = {"diffusion": 0, "brusselator": 1, "ch_front": 2, "air": 3, "turing": 4}
+_MODEL = {"diffusion": 0, "brusselator": 1, "ch_front": 2, "air": 3, "turing": 4, "ch_table1": 5}
 _WIND = {None: 0, "log": 1, "const": 2, "table1": 3}
 
 
@@ -94,6 +94,7 @@ _PARAM_ORDER = {
     "ch_front": ("k", "M", "kappa"),
     "air": ("j", "k"),
     "turing": ("alpha", "beta", "gamma"),
+    "ch_table1": ("k1", "k2", "lam", "eps", "gamma", "sigma"),
 }
 
 

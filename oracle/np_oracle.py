@@ -137,6 +137,13 @@ def _rates(cfg, c):
         r[0] = photo - titr
         r[1] = titr - photo
         r[2] = photo - titr
+    elif m == "ch_table1":
+        c1, c2, c3 = c[0], c[1], c[2]
+        q = P["k1"] * c1 * c2
+        sink = P["k2"] * c1 * c3
+        r[0] = -q - sink
+        r[1] = -q
+        r[2] = q - sink
     elif m == "turing":
         c1, c2 = c[0], c[1]
         r[0] = c1 - c1 ** 3 - c2
@@ -193,6 +200,14 @@ def np_step(cfg, c, n=0):
                 mx, my, mz = _second_diffs(mu, bc_s, h)
                 lap_mu = mx + my + mz
             tend = tend + P["M"] * lap_mu
+        if cfg["model"] == "ch_table1" and s == 2:
+            P = cfg["params"]
+            cc = c[2]
+            lap_c = _lap19(cc, bc_s, h) if stencil == 19 else sum(_second_diffs(cc, bc_s, h))
+            bracket = P["eps"] * cc - P["gamma"] * cc ** 3 + P["sigma"] * lap_c
+            lap_b = (_lap19(bracket, bc_s, h) if stencil == 19
+                     else sum(_second_diffs(bracket, bc_s, h)))
+            tend = tend - P["lam"] * lap_b
         src = cfg.get("source")
         if src and src["species"] == s:
             tend[src["z"], src["y"], src["x"]] += src["rate"]

@@ -160,6 +160,7 @@ static int check(const orc_problem* p)
     case ORC_CH_FRONT: if (p->ns != 3) return -1; break;
     case ORC_AIR: if (p->ns != 3) return -1; break;
     case ORC_TURING: if (p->ns != 2) return -1; break;
+    case ORC_CH_TABLE1: if (p->ns != 3) return -1; break;
     default: return -1;
     }
     return 0;
@@ -195,6 +196,16 @@ static void reaction(const orc_problem* p, const double* v, double* r)
         r[0] = ph - ti;
         r[1] = -ph + ti;
         r[2] = ph - ti;
+        break;
+    }
+    case ORC_CH_TABLE1: {
+        /* Table 1, row 3: c1 + c2 -> c3 at rate k1 c1 c2, and the sink
+         * k2 c1 c3 of c1 and c3 (redissolution by the excess of c1) */
+        double k1 = p->p[0], k2 = p->p[1];
+        double c1 = v[0], c2 = v[1], c3 = v[2];
+        r[0] = -k1 * c1 * c2 - k2 * c1 * c3;
+        r[1] = -k1 * c1 * c2;
+        r[2] = k1 * c1 * c2 - k2 * c1 * c3;
         break;
     }
     case ORC_TURING: {
@@ -238,6 +249,19 @@ static void step(const orc_problem* p, double* cur, double* nxt, double* mu, int
                     mu[lin(p, x, y, z)] = fp - kappa * laplacian(p, c, 2, x, y, z);
                 }
     }
+    /* Table 1, row 3: the bracket eps c - gamma c^3 + sigma Lap c over every
+     * cell of species 2, then (below) -lambda Lap of it */
+    if (p->model == ORC_CH_TABLE1) {
+        const double eps = p->p[3], gamma = p->p[4], sigma = p->p[5];
+        const double* c = cur + 2 * nc;
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    double cc = c[lin(p, x, y, z)];
+                    mu[lin(p, x, y, z)] = eps * cc - gamma * cc * cc * cc
+                                        + sigma * laplacian(p, c, 2, x, y, z);
+                }
+    }
 
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
@@ -266,6 +290,8 @@ static void step(const orc_problem* p, double* cur, double* nxt, double* mu, int
                         else
                             rate -= u * (nb(p, f, s, x, y, z, 0, +1) - v[s]) / p->h;
                     }
+                    if (p->model == ORC_CH_TABLE1 && s == 2)
+                        rate -= p->p[2] * laplacian(p, mu, 2, x, y, z);
                     if (p->model == ORC_CH_FRONT && s == 2) {
                         /* second Laplacian pass: M Lap mu, mu taking the
                          * boundary rule of species 2 */

@@ -45,7 +45,8 @@ extern "C" {
 #endif
 
 enum { ORC_NEUMANN = 0, ORC_PERIODIC = 1, ORC_DIRICHLET = 2 };
-enum { ORC_DIFFUSION = 0, ORC_BRUSSELATOR = 1, ORC_CH_FRONT = 2, ORC_AIR = 3, ORC_TURING = 4 };
+enum { ORC_DIFFUSION = 0, ORC_BRUSSELATOR = 1, ORC_CH_FRONT = 2, ORC_AIR = 3, ORC_TURING = 4,
+       ORC_CH_TABLE1 = 5 };
 enum { ORC_WIND_NONE = 0, ORC_WIND_LOG = 1, ORC_WIND_CONST = 2, ORC_WIND_3D = 3 };
 
 #define ORC_MAXS 4
@@ -62,7 +63,10 @@ typedef struct orc_problem {
      *   BRUSSELATOR  p[0]=a, p[1]=b
      *   CH_FRONT     p[0]=k (a+b->c), p[1]=M (mobility), p[2]=kappa
      *   AIR          p[0]=j (NO2 -> NO + O3), p[1]=k (NO + O3 -> NO2)
-     *   TURING       p[0]=alpha, p[1]=beta, p[2]=gamma (Table 1, row 2)    */
+     *   TURING       p[0]=alpha, p[1]=beta, p[2]=gamma (Table 1, row 2)
+     *   CH_TABLE1    p[0]=k1, p[1]=k2, p[2]=lambda, p[3]=eps, p[4]=gamma,
+     *                p[5]=sigma (Table 1, row 3: c3 moves by
+     *                -lambda Lap(eps c3 - gamma c3^3 + sigma Lap c3))     */
     double p[8];
     double wind_u0;                  /* scale of u_x                        */
     int32_t src_x, src_y, src_z, src_species;   /* src_species < 0: none    */

@@ -113,6 +113,28 @@ def ch_front(n=64, steps=2000, dt=0.01, Da=1.0, Db=0.1, k=1.0, M=0.1,
                 steps=steps, seed=seed, init="ch_front")
 
 
+def ch_table1(n=192, steps=20000, dt=0.02, D1=1.0, D2=1.0, k1=0.2, k2=0.005, lam=1.0,
+              eps=1.0, gamma=1.0, sigma=1.0, c1_front=10.0, h=1.0, seed=7, shape=None,
+              stencil=19):
+    """Phase separation behind a chemical front, Table 1, row 3, with its
+    parameters: c1 + c2 -> c3 (k1), the sink k2 c1 c3 of c1 and c3, and
+    dc3/dt += -lambda Lap(eps c3 - gamma c3^3 + sigma Lap c3); c3 has no
+    Fickian term.  c1 is held at 10 on the x = 0 layer, every other face is
+    zero flux; c1 = 0, c2 = 1, c3 = -1 at the start.  The paper's stencil
+    is the 19-point one, and its dt = 0.02 is within the explicit bound only
+    for that stencil."""
+    nx, ny, nz = shape if shape is not None else (n, n, n)
+    bc = _bc(NEU, 3)
+    bcv = [[0.0] * 6 for _ in range(3)]
+    bc[0][0] = DIR
+    bcv[0][0] = c1_front
+    return dict(name=f"ch_table1_{nx}x{ny}x{nz}", model="ch_table1", shape=(nx, ny, nz),
+                nspecies=3, h=h, dt=dt, D=[[D1] * 3, [D2] * 3, [0.0] * 3], bc=bc, bc_value=bcv,
+                params=dict(k1=k1, k2=k2, lam=lam, eps=eps, gamma=gamma, sigma=sigma),
+                source=None, wind=None, steps=steps, seed=seed, init="ch_table1",
+                stencil=stencil)
+
+
 def turing(n=192, steps=20000, dt=5.0e-4, D1=5.0e-5, D2=5.0e-3, h=6.2e-3, alpha=0.5,
            beta=0.09, gamma=26.0, sigma=5.0e-4, seed=5, shape=None, stencil=7):
     """Activator-inhibitor Turing system of Table 1, row 2, with its
@@ -211,6 +233,11 @@ def initial_fields(cfg, seed=None, dtype=np.float32):
             out[sp] = 1.0 + sig * (2.0 * u - 1.0)
     elif kind == "zero":
         out[:] = 0.0
+    elif kind == "ch_table1":
+        out[0] = 0.0
+        out[0, :, :, 0] = cfg["bc_value"][0][0]
+        out[1] = 1.0
+        out[2] = -1.0
     elif kind == "uniform_noise":
         for sp in range(S):
             out[sp] = uniform01(s, sp, ncell).reshape(nz, ny, nx)
@@ -373,6 +400,11 @@ def initial_fields_torch(cfg, device, seed=None):
             out[sp] = 1.0 + sig * (2.0 * u - 1.0)
     elif kind == "zero":
         out[:] = 0.0
+    elif kind == "ch_table1":
+        out[0] = 0.0
+        out[0, :, :, 0] = cfg["bc_value"][0][0]
+        out[1] = 1.0
+        out[2] = -1.0
     elif kind == "uniform_noise":
         for sp in range(S):
             out[sp] = uniform01_torch(s, sp, ncell, device).reshape(nz, ny, nx)

@@ -50,6 +50,12 @@ MUTANTS = {
     "wind3_uy_from_ux": ("u[1] = p->w3[1];", "u[1] = p->w3[0];"),
     "upwind_forward_difference": ("if (u < 0.0) return -u * (nb(p, f, s, x, y, z, axis, +1) - c) / p->h;",
                                   "if (u < 0.0) return -u * (c - nb(p, f, s, x, y, z, axis, -1)) / p->h;"),
+    "ch1_sink_sign": ("r[0] = -k1 * c1 * c2 - k2 * c1 * c3;", "r[0] = -k1 * c1 * c2 + k2 * c1 * c3;"),
+    "ch1_sink_missing_in_c3": ("r[2] = k1 * c1 * c2 - k2 * c1 * c3;", "r[2] = k1 * c1 * c2;"),
+    "ch1_sigma_sign": ("+ sigma * laplacian(p, c, 2, x, y, z);", "- sigma * laplacian(p, c, 2, x, y, z);"),
+    "ch1_lambda_sign": ("rate -= p->p[2] * laplacian(p, mu, 2, x, y, z);",
+                        "rate += p->p[2] * laplacian(p, mu, 2, x, y, z);"),
+    "ch1_cubic_power": ("gamma * cc * cc * cc", "gamma * cc * cc"),
     "stencil19_centre_weight": ("{{1, 2, 1}, {2, -24, 2}, {1, 2, 1}}",
                                 "{{1, 2, 1}, {2, -26, 2}, {1, 2, 1}}"),
     "stencil19_diagonals_doubled": ("{{1, 2, 1}, {2, -24, 2}, {1, 2, 1}}",

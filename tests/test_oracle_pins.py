@@ -363,7 +363,7 @@ def test_dirichlet_linear_profile_is_steady(orc):
     np.testing.assert_allclose(out, c0, rtol=0, atol=1e-6)
 
 
-@pytest.mark.parametrize("model", ["brusselator", "air", "ch_front", "turing"])
+@pytest.mark.parametrize("model", ["brusselator", "air", "ch_front", "turing", "ch_table1"])
 def test_uniform_state_follows_the_scalar_ode(orc, model):
     # with every face periodic and no wind or source, a uniform state stays
     # uniform and each cell follows the forward-Euler map of the model's
@@ -394,6 +394,16 @@ def test_uniform_state_follows_the_scalar_ode(orc, model):
         def rate(y):
             # activator-inhibitor kinetics of Table 1, row 2
             return [y[0] - y[0] ** 3 - y[1], ga * (y[0] - al * y[1] - be)]
+    elif model == "ch_table1":
+        cfg = W.ch_table1(shape=(5, 4, 6), k2=0.05)
+        y0 = [0.9, 0.6, -0.4]
+        k1, k2 = cfg["params"]["k1"], cfg["params"]["k2"]
+
+        def rate(y):
+            # Table 1, row 3: c1 + c2 -> c3 and the sink k2 c1 c3; the
+            # Cahn-Hilliard term vanishes on a uniform state
+            q, sink = k1 * y[0] * y[1], k2 * y[0] * y[2]
+            return [-q - sink, -q, q - sink]
     else:
         cfg = W.ch_front(shape=(5, 4, 6))
         y0 = [0.9, 0.6, 0.3]
@@ -704,6 +714,76 @@ def test_plume_courant_one_shifts_along_y(orc, sign):
     np.testing.assert_array_equal(out, np.roll(c0, int(sign) * 5, axis=2))
 
 
+# --------------------------------------------------------------------------
+# Table 1, row 3: Cahn-Hilliard with lambda, eps, gamma, sigma and a sink
+# --------------------------------------------------------------------------
+def _lam_of(theta, stencil, h):
+    if stencil == 7:
+        return sum(4.0 * math.sin(t / 2) ** 2 for t in theta) / h ** 2
+    return -_symbol19(theta) / (6.0 * h ** 2)
+
+
+@pytest.mark.parametrize("stencil", [7, 19])
+def test_ch_table1_linear_symbol(orc, stencil):
+    # no reaction (c1 = c2 = 0); about cbar the mode's amplitude follows
+    # g = 1 + dt lambda L (eps - 3 gamma cbar^2 - sigma L), L the stencil's
+    # symbol: c3' = -lambda Lap(eps c - gamma c^3 + sigma Lap c) linearised
+    n = 12
+    cbar, dt = 0.3, 0.01
+    cfg = W.ch_table1(shape=(n, n, 4), stencil=stencil, dt=dt, lam=0.8, eps=1.3, gamma=0.9,
+                      sigma=0.6)
+    cfg["bc"] = [["periodic"] * 6 for _ in range(3)]
+    P = cfg["params"]
+    z, y, x = np.meshgrid(np.arange(4), np.arange(n), np.arange(n), indexing="ij")
+    th = (2 * np.pi * 3 / n, 2 * np.pi * 1 / n, 0.0)
+    mode = np.cos(th[0] * x + th[1] * y)
+    amp = 1e-8
+    c0 = np.stack([np.zeros_like(mode), np.zeros_like(mode), cbar + amp * mode])
+    steps = 30
+    out = orc.run(cfg, c0, steps)
+    L = _lam_of(th, stencil, cfg["h"])
+    g = 1.0 + dt * P["lam"] * L * (P["eps"] - 3.0 * P["gamma"] * cbar ** 2 - P["sigma"] * L)
+    # the uniform part follows the scalar map of -lambda Lap(...) = 0: it stays cbar
+    np.testing.assert_allclose(out[2] - cbar, amp * g ** steps * mode, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("stencil,grows", [(7, True), (19, False)])
+def test_ch_table1_time_step_needs_the_19_point_stencil(orc, stencil, grows):
+    # Table 1's dt = 0.02 (h = 1, lambda = eps = gamma = sigma = 1) about
+    # c = 0: the fastest mode of each stencil (7-point: the 3-D checkerboard,
+    # L = 12; 19-point: the x-y checkerboard, L = 16/3) has
+    # g = 1 + dt L (1 - L): -1.64 (grows) and 0.54 (decays)
+    n = 8
+    cfg = W.ch_table1(shape=(n, n, n), stencil=stencil, k1=0.0, k2=0.0)
+    cfg["bc"] = [["periodic"] * 6 for _ in range(3)]
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    mode = (-1.0) ** (x + y + z) if stencil == 7 else (-1.0) ** (x + y)
+    L = 12.0 if stencil == 7 else 16.0 / 3.0
+    amp = 1e-9
+    c0 = np.stack([np.zeros_like(mode), np.zeros_like(mode), amp * mode])
+    steps = 20
+    out = orc.run(cfg, c0, steps)
+    g = 1.0 + cfg["dt"] * L * (1.0 - L)
+    np.testing.assert_allclose(out[2], amp * g ** steps * mode, rtol=1e-9, atol=0)
+    assert (abs(g) > 1.0) == grows
+
+
+def test_ch_table1_budgets(orc):
+    # zero flux everywhere: with k1 = k2 = 0, sum c3 is conserved; with
+    # k2 = 0 and D1 = D2, sum (c1 - c2) and sum (c2 + c3) are conserved
+    cfg = W.ch_table1(shape=(9, 7, 6), stencil=19, dt=0.01)
+    cfg["bc"] = [["neumann"] * 6 for _ in range(3)]
+    c0 = W.initial_fields(W.with_(cfg, init="uniform_noise"), seed=21).astype(np.float64)
+    c0[2] = 2.0 * c0[2] - 1.0
+    a = orc.run(W.with_(cfg, params=dict(cfg["params"], k1=0.0, k2=0.0)), c0, 25)
+    assert a[2].sum() == pytest.approx(c0[2].sum(), rel=1e-12, abs=1e-12)
+    assert not np.allclose(a[2], c0[2])
+    b = orc.run(W.with_(cfg, params=dict(cfg["params"], k2=0.0)), c0, 25)
+    assert (b[0] - b[1]).sum() == pytest.approx((c0[0] - c0[1]).sum(), rel=1e-12, abs=1e-12)
+    assert (b[1] + b[2]).sum() == pytest.approx((c0[1] + c0[2]).sum(), rel=1e-12, abs=1e-12)
+    assert (b[1].sum() - c0[1].sum()) < -1e-3                     # the reaction ran
+
+
 def test_oracles_agree_on_every_family(orc):
     cases = [W.diffusion_blob(8), W.brusselator(8), W.ch_front(8),
              W.air((8, 8, 8), src=(3, 4, 2)),
@@ -715,7 +795,9 @@ def test_oracles_agree_on_every_family(orc):
              W.with_(W.ch_front(shape=(8, 7, 9)), stencil=19),
              W.turing(shape=(9, 8, 7)), W.turing(shape=(7, 9, 8), stencil=19),
              W.plume(shape=(9, 8, 10), src=(2, 3, 4)),
-             W.with_(W.plume(shape=(8, 9, 7), src=(5, 1, 2)), stencil=19)]
+             W.with_(W.plume(shape=(8, 9, 7), src=(5, 1, 2)), stencil=19),
+             W.ch_table1(shape=(9, 8, 7), dt=0.005), W.ch_table1(shape=(8, 7, 9), stencil=7,
+                                                                 dt=0.005)]
     for cfg in cases:
         f = W.initial_fields(cfg)
         a = orc.run(cfg, f, 9)
