@@ -23,6 +23,8 @@ CASES = {
                                                stencil=19), 20),
     "turing_table1_9x8x7": (W.turing(shape=(9, 8, 7), sigma=0.3), 20),
     "turing_table1_19pt_9x8x7": (W.turing(shape=(9, 8, 7), sigma=0.3, stencil=19), 20),
+    "plume_table1_9x8x10": (W.plume(shape=(9, 8, 10), src=(2, 3, 4)), 20),
+    "ch_table1_19pt_10x9x8": (W.ch_table1(shape=(10, 9, 8), dt=0.005), 20),
 }
 SAMPLES = [(0, 0, 0), (1, 2, 3), (5, 4, 2), (6, 6, 5), (3, 0, 1)]   # (x, y, z)
 
