@@ -149,14 +149,16 @@ rd_status rd_config_init(rd_config* cfg);
 rd_status rd_query_sizes(const rd_config* cfg, size_t* state_bytes,
                          size_t* scratch_bytes);
 
-/* Validate ``cfg`` and create a context on the current CUDA device.
+/* Validate ``cfg`` and create a context on the current CUDA device for the
+ * problem of eq. (1), discretised by the method of lines (Section 2).
  * Checks: sizes >= 2, species count for the model, periodic faces paired
  * and the same for every species, Dirichlet only on non-periodic faces and
  * not on the Cahn-Hilliard species, and the explicit stability bound
  *   dt * (sum_a 2 D[s][a] / h^2 + |u|max / h) <= 1 for every species
- * (isotropic diffusion: dt <= h^2 / (6 D)), plus, for the Cahn-Hilliard
- * species, dt * M * L (kappa L + 2) <= 2 with L = 12 / h^2 (the largest
- * 7-point symbol); RD_EUNSTABLE otherwise unless RD_FLAG_FORCE.
+ * (isotropic diffusion: dt <= h^2 / (6 D); the 19-point stencil counts
+ * 4 D / h^2 instead), plus, for the Cahn-Hilliard species,
+ * dt * M * L (kappa L + 2) <= 2 with L = 12 / h^2 (the largest 7-point
+ * symbol); RD_EUNSTABLE otherwise unless RD_FLAG_FORCE.
  * Allocates both levels and scratch unless RD_FLAG_NO_ALLOC.  The state is
  * zero until rd_set_field.  *out receives the context. */
 rd_status rd_create(const rd_config* cfg, rd_ctx** out);
@@ -180,7 +182,8 @@ rd_status rd_destroy(rd_ctx* ctx);
 rd_status rd_set_stream(rd_ctx* ctx, void* stream);
 
 /* Copy ``count`` = nx*ny*nz dense float32 values (host or device pointer)
- * into species ``s`` of the current level, converting to the storage type.
+ * into species ``s`` of the current level, converting to the storage type
+ * (the host loop's copy of the initial state to the GPU, Table 3).
  * Cells of held (Dirichlet) layers are set to their bc_value.  Returns
  * after the source buffer may be reused. */
 rd_status rd_set_field(rd_ctx* ctx, int s, const float* src, size_t count);
@@ -192,7 +195,8 @@ rd_status rd_set_field(rd_ctx* ctx, int s, const float* src, size_t count);
 rd_status rd_step(rd_ctx* ctx, int64_t nsteps);
 
 /* Copy species ``s`` of the current level out as ``count`` = nx*ny*nz dense
- * float32 values (host or device pointer).  Synchronises the stream. */
+ * float32 values (host or device pointer), the copy back of Table 3's host
+ * loop.  Synchronises the stream. */
 rd_status rd_get_field(rd_ctx* ctx, int s, float* dst, size_t count);
 
 /* FP64 reduction of species ``s`` of the current level: out[0] = sum,
@@ -221,9 +225,9 @@ rd_status rd_set_step_count(rd_ctx* ctx, int64_t n);
  *           is 64 cells wide)
  *   tile_y  tile height in rows, >= 1 (even for tsteps = 1 without
  *           Cahn-Hilliard, where the CTA is 16 tile_y compute threads plus
- *           one halo warp, with either stencil); otherwise the CTA has (tile_q + 2) x
- *           (tile_y + 2 L) threads (L = tsteps, 2 tsteps for Cahn-Hilliard);
- *           at most 512 threads
+ *           one halo warp, with either stencil); otherwise the CTA has
+ *           (tile_q + 2) x (tile_y + 2 L) threads (L = tsteps, 2 tsteps for
+ *           Cahn-Hilliard); at most 512 threads
  *   zchunk  z planes per work item, >= 1
  *   graph   1: replay rd_step launches from a captured CUDA graph
  * rd_set_tuning validates; RD_EINVAL if the CTA or its shared memory does
@@ -241,8 +245,8 @@ rd_status rd_set_tuning(rd_ctx* ctx, const rd_tuning* t);
 
 /* Time a built-in list of tunings on this context's problem (launches read
  * the current level and write the spare level, so the state is unchanged)
- * and keep the fastest.  Results are cached per (model, storage, grid, BC, stencil)
- * in-process and, if the environment variable RD_AUTOTUNE_CACHE names a
+ * and keep the fastest.  Results are cached per (model, storage, grid, BC,
+ * stencil) in-process and, if the environment variable RD_AUTOTUNE_CACHE names a
  * file, in that file (one JSON object per line).  *best may be NULL. */
 rd_status rd_autotune(rd_ctx* ctx, rd_tuning* best);
 
@@ -312,7 +316,8 @@ typedef struct rd_batch rd_batch;
 
 /* Create an empty batch for one model and storage kind. */
 rd_status rd_batch_create(int32_t model, int32_t storage, rd_batch** out);
-/* Add ``ctx`` (same model and storage; at most one batch at a time). */
+/* Add ``ctx`` (same model and storage; at most one batch at a time; the
+ * 7-point stencil only: RD_EUNSUPPORTED for a 19-point context). */
 rd_status rd_batch_add(rd_batch* b, rd_ctx* ctx);
 /* Remove ``ctx``; it becomes a standalone context again. */
 rd_status rd_batch_remove(rd_batch* b, rd_ctx* ctx);
