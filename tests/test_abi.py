@@ -60,6 +60,23 @@ int main(void) {
                     ctypes.sizeof(L.RdTuning), C.stencil.offset]
 
 
+def test_binding_constants_match_the_header_enums():
+    text = open(HEADER).read()
+    enum = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"\b(RD_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    prefixed = {"RD_BC_": L.BC, "RD_MODEL_": L.MODEL, "RD_STORE_": L.STORAGE,
+                "RD_WIND_": L.WIND, "RD_KERNEL_": L.KERNEL}
+    for prefix, table in prefixed.items():
+        in_header = {k for k in enum if k.startswith(prefix)}
+        named = {prefix + ("none" if k is None else k).upper(): v for k, v in table.items()}
+        assert set(named) == in_header, prefix
+        for name, value in named.items():
+            assert enum[name] == value, name
+    assert [enum[k] for k in ("RD_OK", "RD_EINVAL", "RD_EUNSTABLE", "RD_EUNSUPPORTED")] == \
+        [L.RD_OK, L.RD_EINVAL, L.RD_EUNSTABLE, L.RD_EUNSUPPORTED]
+    assert (enum["RD_FLAG_NO_ALLOC"], enum["RD_FLAG_FORCE"]) == (L.FLAG_NO_ALLOC, L.FLAG_FORCE)
+
+
 def test_status_strings(lib):
     for st in range(9):
         assert lib.rd_status_str(st)
