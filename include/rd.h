@@ -298,7 +298,11 @@ const char* rd_last_error(const rd_ctx* ctx);
  * sums live in one file-scope device array of 608 x 3 doubles (14,592
  * bytes) that every GPU loading this library keeps until the process exits.
  * The first call on a device looks up that array's address (with the device
- * current), so make a first call before any stream capture.  Calls share
+ * current), so make a first call before any stream capture.  The address is
+ * then kept for the life of the process: after cudaDeviceReset, or after
+ * the device's primary context is released and created again, the library's
+ * module is loaded anew and the kept address is stale, so do not call this
+ * entry point on that device again in the same process.  Calls share
  * the array: two calls that overlap on the GPU (unordered streams) race and
  * may return wrong sums. */
 rd_status rd_moments_noalloc(const void* field, int32_t storage, int32_t nx, int32_t ny,

@@ -13,7 +13,10 @@
 // The array is a fixed 608 x 3 doubles (14,592 bytes) that every GPU which
 // loads this library holds until the process exits.  Its device address is
 // looked up once per device, on the first call made with that device
-// current.  All calls on a device share the array, and each call overwrites
+// current, and kept until the process exits: a device reset (or a release
+// and re-creation of the primary context) reloads the module and leaves the
+// kept address stale, so the entry point must not be used on that device
+// again afterwards.  All calls on a device share the array, and each call overwrites
 // all of it before reading it, so nothing has to be cleared between calls;
 // but two calls whose kernels overlap on the GPU (different streams, no
 // ordering between them) race on the array and may return wrong sums.

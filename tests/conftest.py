@@ -20,3 +20,27 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+def _wants_fullsize(items):
+    return any(os.path.basename(str(it.fspath)) == "test_gpu_fullsize.py" for it in items)
+
+
+def pytest_collection_finish(session):
+    """Start the full-size oracle legs (tests/fullsize_oracle.py) as soon as
+    the session knows it will run them, so they overlap the other tests."""
+    if not _wants_fullsize(session.items):
+        return
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return
+    except ImportError:
+        return
+    from tests import fullsize_oracle
+    fullsize_oracle.start()
+
+
+def pytest_sessionfinish(session, exitstatus):
+    from tests import fullsize_oracle
+    fullsize_oracle.stop()

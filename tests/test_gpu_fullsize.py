@@ -1,0 +1,129 @@
+"""The benchmark workloads at their full sizes against the FP64 oracle, at
+the step count their tolerance is stated for (200 steps of the nonlinear
+problems, before rounding differences are amplified by the instabilities
+the problems are built on), in the launch configurations the benchmark
+times:
+
+  256^3 periodic Brusselator   FP32 <= 1e-4 (autotuned, as benchmarked);
+                               BF16 storage reported against the oracle
+                               from the FP32 and from the BF16-rounded
+                               initial fields
+  512 x 512 x 64 air problem   FP32 <= 1e-4 (autotuned)
+  32 front instances batched   FP32 <= 1e-4 per instance, for the three
+                               smallest and the largest instance (one
+                               batched launch sequence, the benchmark's
+                               tile 12 x 64, 32-plane chunks, graph replay)
+
+The oracle legs run in worker processes started with the session
+(tests/fullsize_oracle.py).  With RD_ERROR_REPORT=<path> the errors are
+appended there as JSON lines, like tests/test_gpu_errors.py.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1004_0480_gb300 import workloads as W
+from tests import fullsize_oracle as FO
+
+pytestmark = pytest.mark.gpu
+
+TOL_NONLIN = 1e-4
+BF16_BOUND = 0.5        # catches a broken path; the value is reported
+
+
+@pytest.fixture(scope="module")
+def rd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1004_0480_gb300 import build as B
+    B.build()
+    from paper_1004_0480_gb300 import sim
+    return sim
+
+
+@pytest.fixture(scope="module")
+def legs():
+    return FO.start()
+
+
+def rel_err(got, ref):
+    return max(float(np.abs(got[s] - ref[s]).max() / max(np.abs(ref[s]).max(), 1e-30))
+               for s in range(ref.shape[0]))
+
+
+def pointwise_err(got, ref):
+    out = 0.0
+    for s in range(ref.shape[0]):
+        floor = 1e-3 * max(np.abs(ref[s]).max(), 1e-30)
+        out = max(out, float((np.abs(got[s] - ref[s]) / np.maximum(np.abs(ref[s]), floor)).max()))
+    return out
+
+
+def report(**kw):
+    path = os.environ.get("RD_ERROR_REPORT")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps(kw) + "\n")
+
+
+def run_autotuned(rd, cfg, storage, steps):
+    with rd.Sim(cfg, storage) as sim:
+        tun = sim.autotune()
+        sim.set_fields(W.initial_fields(cfg))
+        sim.step(steps)
+        return sim.get_fields(), tun
+
+
+def test_brusselator_256_200_steps(rd, legs):
+    cfg = W.cfg_brusselator_256()
+    got, tun = run_autotuned(rd, cfg, "f32", FO.STEPS)
+    got_b, tun_b = run_autotuned(rd, cfg, "bf16", FO.STEPS)
+    ref = legs.result("brusselator_256")
+    ref_b = legs.result("brusselator_256_bf16")
+    err = rel_err(got, ref)
+    err_b = rel_err(got_b, ref)
+    report(case="brusselator_256_periodic", steps=FO.STEPS, fp32_bound=TOL_NONLIN,
+           fp32_rel_err=err, fp32_pointwise_err=pointwise_err(got, ref),
+           bf16_rel_err=err_b, bf16_rel_err_from_bf16_start=rel_err(got_b, ref_b),
+           tuning=tun, tuning_bf16=tun_b)
+    assert err <= TOL_NONLIN, f"FP32 rel err {err:.3e} (tuning {tun})"
+    assert err_b <= BF16_BOUND
+
+
+def test_air_512_200_steps(rd, legs):
+    cfg = W.cfg_air_512()
+    got, tun = run_autotuned(rd, cfg, "f32", FO.STEPS)
+    ref = legs.result("air_512")
+    err = rel_err(got, ref)
+    report(case="air_512x512x64", steps=FO.STEPS, fp32_bound=TOL_NONLIN, fp32_rel_err=err,
+           fp32_pointwise_err=pointwise_err(got, ref), tuning=tun)
+    assert err <= TOL_NONLIN, f"rel err {err:.3e} (tuning {tun})"
+
+
+def test_ch_front_batch_32_200_steps(rd, legs):
+    cfgs = W.cfg_ch_front_batch()
+    sims = [rd.Sim(c) for c in cfgs]
+    try:
+        for c, s in zip(cfgs, sims):
+            s.set_fields(W.initial_fields(c))
+        b = rd.Batch("ch_front")
+        b.set_tuning(tsteps=1, tile_q=16, tile_y=12, zchunk=32, graph=1)
+        for s in sims:
+            b.add(s)
+        b.step(FO.STEPS)
+        b.sync()
+        for i in FO.batch_members():
+            got = sims[i].get_fields()
+            ref = legs.result(f"ch_batch_{i}")
+            err = rel_err(got, ref)
+            report(case=f"ch_front_batch_32[{i}] {cfgs[i]['shape']}", steps=FO.STEPS,
+                   fp32_bound=TOL_NONLIN, fp32_rel_err=err,
+                   fp32_pointwise_err=pointwise_err(got, ref))
+            assert err <= TOL_NONLIN, f"instance {i} {cfgs[i]['shape']}: rel err {err:.3e}"
+        b.close()
+    finally:
+        for s in sims:
+            s.close()

@@ -61,7 +61,17 @@ def family_cases():
     air_held["bc"] = [["neumann", "neumann", "periodic", "periodic", "neumann", "dirichlet"]] * 3
     air_held["bc_value"] = [[0.0] * 5 + [v] for v in (0.0, 0.02, 1.0)]
     air_held["wind"] = dict(kind="const", u0=-0.5)
+    # nx % 4 == 3: the last vector of a row holds three cells, so the +x
+    # diagonals of its cells come from clamped neighbour-row elements; ny a
+    # multiple of the 4- and 6-row tiles puts the last tile's halo row on
+    # the y ghost row
+    neu67 = s19(W.brusselator(shape=(67, 24, 19), bc="neumann"))
+    mixed67 = s19(W.air((67, 24, 19), src=(66, 23, 5)), D=[[0.1] * 3] * 3)
+    mixed67["bc"] = [["neumann", "neumann", "neumann", "neumann", "periodic", "periodic"]] * 3
+    mixed67["wind"] = dict(kind="const", u0=0.4)
     return {
+        "brusselator_neumann_nx67": (neu67, TOL_NONLIN),
+        "air_mixed_bc_nx67": (mixed67, TOL_NONLIN),
         "diffusion_neumann": (s19(W.diffusion_blob(shape=SHAPE)), TOL_DIFF),
         "diffusion_periodic": (per_d, TOL_DIFF),
         "diffusion_noise_neumann": (noise_d, TOL_DIFF),

@@ -90,3 +90,39 @@ def test_noalloc_rejects_bad_sizes(rd):
     assert lib.rd_moments_noalloc(p, 0, 8, 2 ** 16, 2 ** 16, 8, o, None) == L.RD_EINVAL
     assert lib.rd_moments_noalloc(p, 7, 8, 1, 1, 8, o, None) == L.RD_EINVAL
     assert lib.rd_moments_noalloc(None, 0, 8, 1, 1, 8, o, None) == L.RD_EINVAL
+
+
+def test_noalloc_counts_nonfinite_on_a_stream(rd):
+    """A NaN and an Inf in the field: the count is 2 and the sums run over
+    the finite cells only, as rd_mass gives; the call runs on a caller's
+    stream (its handle passed through the ABI), twice in a row."""
+    import torch
+    simmod, L = rd
+    lib = L.load()
+    cfg = W.diffusion_blob(shape=(45, 19, 13), seed=3)
+    nx, ny, nz = cfg["shape"]
+    f = W.initial_fields(cfg)
+    f[0, 4, 7, 11] = np.nan
+    f[0, 12, 18, 44] = np.inf
+    finite = f[0][np.isfinite(f[0])].astype(np.float64)
+    stream = torch.cuda.Stream()
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    with simmod.Sim(cfg, "f32", torch_memory=True) as sim:
+        sim.set_fields(f)
+        ref = sim.mass(0)
+        assert ref[2] == 2
+        torch.cuda.synchronize()
+        for _ in range(2):
+            with torch.cuda.stream(stream):
+                out.zero_()
+            st = lib.rd_moments_noalloc(
+                ctypes.c_void_p(field_pointer(sim, "f32", 0, 0)), L.STORAGE["f32"], nx, ny, nz,
+                pitch_of(nx, "f32"), ctypes.c_void_p(out.data_ptr()),
+                ctypes.c_void_p(stream.cuda_stream))
+            assert st == L.RD_OK
+            stream.synchronize()
+            got = out.cpu().numpy()
+            assert got[2] == 2
+            np.testing.assert_allclose(got[:2], ref[:2], rtol=REL_TOL, atol=0)
+            np.testing.assert_allclose(got[0], finite.sum(), rtol=1e-12)
+            np.testing.assert_allclose(got[1], (finite ** 2).sum(), rtol=1e-12)
