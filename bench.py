@@ -500,6 +500,17 @@ def run_extras(args, Sim, Batch, torch):
             tun = sim.autotune()
             t = _timed_steps(torch, sim, 2000)
             out[f"turing_{n}_19pt"] = _entry(W.cell_count(tcfg), 2000, t, 16, tun)
+    # the Cahn-Hilliard row of Table 1 with its parameters, 19-point stencil
+    # and the paper's 192^3 grid: two launches per step (mu, then the
+    # update), 36 B per cell-step moved by the two launches against the 24 B
+    # algorithmic minimum the fraction is stated at
+    ccfg = W.ch_table1(192)
+    with Sim(ccfg) as sim:
+        sim.set_fields(W.initial_fields_torch(ccfg, "cuda"))
+        tun = sim.autotune()
+        t = _timed_steps(torch, sim, 1000)
+        out["ch_table1_192_19pt"] = _entry(W.cell_count(ccfg), 1000, t, 24, tun,
+                                           launches_per_step=2, moved_bytes_per_cell_step=36)
     # the paper's own kernel designs on the same problem (ablation baselines:
     # Shared method and Moving Tiles, Section 4.1, Tables 4-5)
     for kern in ("shared", "tiles"):

@@ -73,10 +73,19 @@ typedef enum rd_model {
     RD_MODEL_AIR = 3,         /* 3 species NO, NO2, O3: NO2 -> NO + O3 at
                                  j NO2, NO + O3 -> NO2 at k NO O3;
                                  params[0]=j, [1]=k                          */
-    RD_MODEL_TURING = 4       /* 2 species, the activator-inhibitor system of
+    RD_MODEL_TURING = 4,      /* 2 species, the activator-inhibitor system of
                                  Table 1 (row 2): R_1 = c1 - c1^3 - c2,
                                  R_2 = gamma (c1 - alpha c2 - beta);
                                  params[0]=alpha, [1]=beta, [2]=gamma        */
+    RD_MODEL_CH_TABLE1 = 5    /* 3 species c1, c2, c3, the phase separation
+                                 behind a front of Table 1 (row 3):
+                                 c1 + c2 -> c3 at k1 c1 c2, the sink k2 c1 c3
+                                 of c1 and c3, and c3 also moves by
+                                 -lambda Lap(eps c3 - gamma c3^3 + sigma Lap c3)
+                                 (Cahn-Hilliard, as RD_MODEL_CH_FRONT);
+                                 params[0]=k1, [1]=k2, [2]=lambda, [3]=eps,
+                                 [4]=gamma, [5]=sigma; c3 has no Fickian term
+                                 (D[2] = 0)                                  */
 } rd_model;
 
 typedef enum rd_storage {
@@ -117,10 +126,15 @@ enum {
  *                (1/6h^2) (-24 c + 2 x 6 face + 1 x 12 edge neighbours),
  *                edge ghosts taking both crossed faces' rules.  It needs
  *                one diffusivity per species (D[s][0] = D[s][1] = D[s][2],
- *                else RD_EINVAL), steps once per launch (tsteps = 1), is not
- *                available for RD_MODEL_CH_FRONT nor in batches
- *                (RD_EUNSUPPORTED), and its stability check uses the centre
- *                weight 4 D / h^2 in place of 2 sum(D) / h^2.
+ *                else RD_EINVAL), steps once per launch (tsteps = 1), and
+ *                its stability check uses the centre weight 4 D / h^2 in
+ *                place of 2 sum(D) / h^2.  With a Cahn-Hilliard model a
+ *                step is two kernel launches, the paper's "Laplacian,
+ *                boundary rule, Laplacian" (Section 4.1): the first writes
+ *                mu of every cell to a float field in the context's scratch
+ *                (rd_query_sizes counts it), the second updates the state
+ *                with the 19-point Laplacian of mu, whose ghost cells take
+ *                species 2's face rules.
  */
 typedef struct rd_config {
     int32_t nx, ny, nz, nspecies;
@@ -157,8 +171,12 @@ rd_status rd_query_sizes(const rd_config* cfg, size_t* state_bytes,
  *   dt * (sum_a 2 D[s][a] / h^2 + |u|max / h) <= 1 for every species
  * (isotropic diffusion: dt <= h^2 / (6 D); the 19-point stencil counts
  * 4 D / h^2 instead), plus, for the Cahn-Hilliard species,
- * dt * M * L (kappa L + 2) <= 2 with L = 12 / h^2 (the largest 7-point
- * symbol); RD_EUNSTABLE otherwise unless RD_FLAG_FORCE.
+ * dt * Mc * L (K L + gb) <= 2 with L the largest eigenvalue of -Laplacian
+ * (12 / h^2 for the 7-point stencil, 16 / (3 h^2) for the 19-point one),
+ * Mc, K the mobility and gradient coefficient (M, kappa of
+ * RD_MODEL_CH_FRONT with gb = 2; lambda, sigma of RD_MODEL_CH_TABLE1 with
+ * gb = max(0, 3 gamma - eps)); RD_EUNSTABLE otherwise unless
+ * RD_FLAG_FORCE.
  * Allocates both levels and scratch unless RD_FLAG_NO_ALLOC.  The state is
  * zero until rd_set_field.  *out receives the context. */
 rd_status rd_create(const rd_config* cfg, rd_ctx** out);
@@ -220,19 +238,19 @@ rd_status rd_set_step_count(rd_ctx* ctx, int64_t n);
 
 /* Kernel tuning of a context.
  *   tsteps  steps per launch (temporal blocking depth), 1..3 (1..2 for
- *           the Cahn-Hilliard model, 1 for the 19-point stencil)
+ *           the Cahn-Hilliard models, 1 for the 19-point stencil)
  *   tile_q  tile width in 4-cell vectors; this build fixes it at 16 (a tile
  *           is 64 cells wide)
- *   tile_y  tile height in rows, >= 1 (even for tsteps = 1 without
- *           Cahn-Hilliard, where the CTA is 16 tile_y compute threads plus
- *           one halo warp, with either stencil); otherwise the CTA has
- *           (tile_q + 2) x (tile_y + 2 L) threads (L = tsteps, 2 tsteps for
- *           Cahn-Hilliard); at most 512 threads
+ *   tile_y  tile height in rows, >= 1 (even for tsteps = 1 with the
+ *           19-point stencil or without Cahn-Hilliard, where the CTA is 16
+ *           tile_y compute threads plus one halo warp); otherwise the CTA
+ *           has (tile_q + 2) x (tile_y + 2 L) threads (L = tsteps, 2 tsteps
+ *           for Cahn-Hilliard); at most 512 threads
  *   zchunk  z planes per work item, >= 1
  *   graph   1: replay rd_step launches from a captured CUDA graph
  * rd_set_tuning validates; RD_EINVAL if the CTA or its shared memory does
  * not fit one SM.  A new context starts with tsteps 1, tile_y 14 (12 for
- * the Cahn-Hilliard model), graph 1, regcap 0 and the z-chunk whose work
+ * the Cahn-Hilliard models), graph 1, regcap 0 and the z-chunk whose work
  * items fill the resident CTA slots in the fewest waves. */
 typedef struct rd_tuning {
     int32_t tsteps, tile_q, tile_y, zchunk, graph;
@@ -320,8 +338,8 @@ typedef struct rd_batch rd_batch;
 
 /* Create an empty batch for one model and storage kind. */
 rd_status rd_batch_create(int32_t model, int32_t storage, rd_batch** out);
-/* Add ``ctx`` (same model and storage; at most one batch at a time; the
- * 7-point stencil only: RD_EUNSUPPORTED for a 19-point context). */
+/* Add ``ctx`` (same model, storage and stencil as the members already in
+ * the batch, else RD_EINVAL; at most one batch at a time). */
 rd_status rd_batch_add(rd_batch* b, rd_ctx* ctx);
 /* Remove ``ctx``; it becomes a standalone context again. */
 rd_status rd_batch_remove(rd_batch* b, rd_ctx* ctx);

@@ -12,7 +12,8 @@ MAX_S = 4
 RD_OK, RD_EINVAL, RD_ENOMEM, RD_ECUDA, RD_EUNSTABLE, RD_ENONFINITE, RD_ETIMEOUT, \
     RD_EBUDGET, RD_EUNSUPPORTED = range(9)
 BC = {"neumann": 0, "periodic": 1, "dirichlet": 2}
-MODEL = {"diffusion": 0, "brusselator": 1, "ch_front": 2, "air": 3, "turing": 4}
+MODEL = {"diffusion": 0, "brusselator": 1, "ch_front": 2, "air": 3, "turing": 4,
+         "ch_table1": 5}
 STORAGE = {"f32": 0, "bf16": 1}
 WIND = {None: 0, "log": 1, "const": 2}
 KERNEL = {"march": 0, "shared": 1, "tiles": 2}

@@ -75,6 +75,9 @@ int elem_bytes(int storage) { return storage == RD_STORE_BF16 ? 2 : 4; }
 // the stencil of a configuration: 7 (7-point, the default) or 19 (eqs. (3)-(4))
 int stencil_of(const rd_config& g) { return g.stencil == 19 ? 19 : 7; }
 
+// models with a Cahn-Hilliard species (species 2)
+bool is_ch(int model) { return model == RD_MODEL_CH_FRONT || model == RD_MODEL_CH_TABLE1; }
+
 int species_of(int model) {
     switch (model) {
     case RD_MODEL_DIFFUSION: return 1;
@@ -84,11 +87,14 @@ int species_of(int model) {
 }
 
 size_t smem_of(int model, int storage, int T, int ty, int stencil = 7) {
-    if (stencil == 19) return smem19_bytes(species_of(model), elem_bytes(storage), ty);
+    if (stencil == 19)
+        return is_ch(model) ? smem19_ch_bytes(elem_bytes(storage), ty)
+                            : smem19_bytes(species_of(model), elem_bytes(storage), ty);
     switch (model) {
     case RD_MODEL_DIFFUSION: return smem_diffusion(storage, T, ty);
     case RD_MODEL_BRUSSELATOR: return smem_brusselator(storage, T, ty);
     case RD_MODEL_CH_FRONT: return smem_ch_front(storage, T, ty);
+    case RD_MODEL_CH_TABLE1: return smem_ch_table1(storage, T, ty);
     case RD_MODEL_AIR: return smem_air(storage, T, ty);
     case RD_MODEL_TURING: return smem_turing(storage, T, ty);
     }
@@ -103,9 +109,9 @@ int threads_of(int model, int T, int ty, int stencil = 7) {
     // then a whole halo warp); an odd height at one step per launch (the
     // last launch of a call whose tuning steps 2 or 3 per launch) runs the
     // multi-level kernel at T = 1
-    if (T == 1 && model != RD_MODEL_CH_FRONT && !(ty & 1)) return kTileQ * ty + 32;
+    if (T == 1 && !is_ch(model) && !(ty & 1)) return kTileQ * ty + 32;
     if (T == 1) return (kTileQ + 2) * (ty + 2);   // one-step Cahn-Hilliard kernel
-    const int L = (model == RD_MODEL_CH_FRONT ? 2 : 1) * T;
+    const int L = (is_ch(model) ? 2 : 1) * T;
     return (kTileQ + 2) * (ty + 2 * L);
 }
 
@@ -113,6 +119,15 @@ cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int
                          size_t smem, cudaStream_t st, int* occ, int stencil = 7) {
     if (stencil == 19) {
         if (T != 1) return cudaErrorInvalidValue;
+        if (is_ch(model)) {
+            // two launches: mu (pass 1), then the update (pass 2); the CTAs
+            // per SM reported are those of pass 2, the larger one
+            auto pass = model == RD_MODEL_CH_FRONT ? launch19_ch_front : launch19_ch_table1;
+            if (occ) return pass(storage, 2, a, grid, smem, st, occ);
+            cudaError_t e = pass(storage, 1, a, grid, smem, st, nullptr);
+            if (e != cudaSuccess) return e;
+            return pass(storage, 2, a, grid, smem, st, nullptr);
+        }
         switch (model) {
         case RD_MODEL_DIFFUSION: return launch19_diffusion(storage, a, grid, smem, st, occ);
         case RD_MODEL_BRUSSELATOR: return launch19_brusselator(storage, a, grid, smem, st, occ);
@@ -125,17 +140,22 @@ cudaError_t launch_model(int model, int storage, int T, const LaunchArgs& a, int
     case RD_MODEL_DIFFUSION: return launch_diffusion(storage, T, a, grid, smem, st, occ);
     case RD_MODEL_BRUSSELATOR: return launch_brusselator(storage, T, a, grid, smem, st, occ);
     case RD_MODEL_CH_FRONT: return launch_ch_front(storage, T, a, grid, smem, st, occ);
+    case RD_MODEL_CH_TABLE1: return launch_ch_table1(storage, T, a, grid, smem, st, occ);
     case RD_MODEL_AIR: return launch_air(storage, T, a, grid, smem, st, occ);
     case RD_MODEL_TURING: return launch_turing(storage, T, a, grid, smem, st, occ);
     }
     return cudaErrorInvalidValue;
 }
 
+// kernel launches per step of a one-step launch sequence: a 19-point
+// Cahn-Hilliard step is two (mu, then the update)
+int kernels_per_step(const rd_config& g) { return (stencil_of(g) == 19 && is_ch(g.model)) ? 2 : 1; }
+
 // temporal blocking: up to 3 steps per launch (2 with Cahn-Hilliard); the
 // 19-point kernel steps once per launch
 int max_tsteps(const rd_config& g) {
     if (stencil_of(g) == 19) return 1;
-    return g.model == RD_MODEL_CH_FRONT ? 2 : 3;
+    return is_ch(g.model) ? 2 : 3;
 }
 
 // CTAs per SM for a variant (cached).
@@ -182,6 +202,7 @@ struct rd_ctx {
     double* result = nullptr;      // reduction result (3 doubles)
     InstDesc* desc_dev = nullptr;  // this context's descriptor
     float* courant = nullptr;      // u(z) dt / h per plane
+    float* mu = nullptr;           // 19-point Cahn-Hilliard: the mu field
     int cur = 0;                   // current time level
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -199,6 +220,7 @@ struct rd_ctx {
 
 struct rd_batch {
     int model = 0, storage = 0;
+    int stencil = 7;                 // of the members (set by the first one)
     std::vector<rd_ctx*> members;
     InstDesc* desc_dev = nullptr;
     size_t desc_cap = 0;
@@ -255,6 +277,7 @@ rd_status validate(const rd_config* c) {
     case RD_MODEL_CH_FRONT: want = 3; break;
     case RD_MODEL_AIR: want = 3; break;
     case RD_MODEL_TURING: want = 2; break;
+    case RD_MODEL_CH_TABLE1: want = 3; break;
     default: return fail(nullptr, RD_EINVAL, "unknown model %d", c->model);
     }
     if (c->nspecies != want) {
@@ -280,7 +303,7 @@ rd_status validate(const rd_config* c) {
                     return fail(nullptr, RD_EINVAL, "diffusivities must be finite and >= 0");
         }
     }
-    if (c->model == RD_MODEL_CH_FRONT) {
+    if (is_ch(c->model)) {
         for (int f = 0; f < 6; ++f)
             if (c->bc[2][f] == RD_BC_DIRICHLET)
                 return fail(nullptr, RD_EUNSUPPORTED, "no held layer on the Cahn-Hilliard species");
@@ -296,10 +319,6 @@ rd_status validate(const rd_config* c) {
     if (c->stencil != 0 && c->stencil != 7 && c->stencil != 19)
         return fail(nullptr, RD_EINVAL, "stencil must be 7 or 19");
     if (c->stencil == 19) {
-        if (c->model == RD_MODEL_CH_FRONT)
-            return fail(nullptr, RD_EUNSUPPORTED,
-                        "the 19-point kernels of this build cover the models without "
-                        "Cahn-Hilliard");
         for (int s = 0; s < c->nspecies; ++s)
             if (c->D[s][1] != c->D[s][0] || c->D[s][2] != c->D[s][0])
                 return fail(nullptr, RD_EINVAL,
@@ -331,14 +350,32 @@ rd_status validate(const rd_config* c) {
                             "dt too large for species %d: dt*(%s/h^2+|u|/h) = %g > 1", s,
                             s19 ? "4*D" : "2*sum(D)", g);
         }
-        if (c->model == RD_MODEL_CH_FRONT) {
-            const double L = 12.0 / (c->h * c->h);
-            const double g = c->dt * c->params[1] * L * (c->params[2] * L + 2.0);
+        if (is_ch(c->model)) {
+            // the Cahn-Hilliard term's largest decay rate: dt Mc L (K L + gb)
+            // <= 2, L the largest eigenvalue of -Laplacian (12 / h^2 for the
+            // 7-point stencil, 16 / (3 h^2) for the 19-point one), Mc the
+            // mobility, K the gradient coefficient and gb a bound of -g'(c)
+            // over the range of c (front: g = f', f'' >= -1, bounded by 2 as
+            // a margin; Table 1 row 3: g = eps c - gamma c^3, -g' <= 3 gamma
+            // - eps for |c| <= 1)
+            const double L = (stencil_of(*c) == 19 ? 16.0 / 3.0 : 12.0) / (c->h * c->h);
+            const bool front = c->model == RD_MODEL_CH_FRONT;
+            const double mob = front ? c->params[1] : c->params[2];
+            const double kap = front ? c->params[2] : c->params[5];
+            const double gb = front ? 2.0 : std::max(0.0, 3.0 * c->params[4] - c->params[3]);
+            const double g = c->dt * std::fabs(mob) * L * (std::fabs(kap) * L + gb);
             if (g > 2.0 + 1e-12)
                 return fail(nullptr, RD_EUNSTABLE, "dt too large for the Cahn-Hilliard term (%g > 2)", g);
         }
     }
     return RD_OK;
+}
+
+// the mu field of a 19-point Cahn-Hilliard context: one float plane stack
+// with the state's element pitch
+size_t mu_bytes(const rd_ctx* c) {
+    if (kernels_per_step(c->cfg) != 2) return 0;
+    return align_up((size_t)c->plane * c->cfg.nz * sizeof(float), 256);
 }
 
 void layout(rd_ctx* c) {
@@ -357,7 +394,7 @@ void layout(rd_ctx* c) {
     const size_t res = 256;
     const size_t desc = align_up(sizeof(InstDesc), 256);
     const size_t cour = align_up((size_t)g.nz * sizeof(float), 256);
-    c->scratch_bytes = dense + part + res + desc + cour;
+    c->scratch_bytes = dense + part + res + desc + cour + mu_bytes(c);
 }
 
 void carve(rd_ctx* c) {
@@ -372,6 +409,8 @@ void carve(rd_ctx* c) {
     c->desc_dev = reinterpret_cast<InstDesc*>(p);
     p += align_up(sizeof(InstDesc), 256);
     c->courant = reinterpret_cast<float*>(p);
+    p += align_up((size_t)g.nz * sizeof(float), 256);
+    c->mu = mu_bytes(c) ? reinterpret_cast<float*>(p) : nullptr;
 }
 
 char* field_ptr(rd_ctx* c, int level, int s) {
@@ -388,7 +427,7 @@ int auto_zchunk(const rd_config& g, const rd_tuning& t, int occ, int waves) {
     const long long slots = (long long)std::max(occ, 1) * num_sms() * waves;
     long long nzc = std::max<long long>(1, (slots + cols - 1) / cols);
     int zc = (int)std::max<long long>(1, (g.nz + nzc - 1) / nzc);
-    const int L = (g.model == RD_MODEL_CH_FRONT ? 2 : 1) * t.tsteps;
+    const int L = (is_ch(g.model) ? 2 : 1) * t.tsteps;
     zc = std::max(zc, std::min(g.nz, 4 * L));
     return zc;
 }
@@ -400,7 +439,7 @@ rd_status check_tuning(const rd_config& g, const rd_tuning& t) {
         return fail(nullptr, RD_EINVAL, "tile_q must be %d in this build", kTileQ);
     if (t.tile_y < 1 || t.zchunk < 1) return fail(nullptr, RD_EINVAL, "tile out of range");
     if (t.regcap != 0 && t.regcap != 1) return fail(nullptr, RD_EINVAL, "regcap must be 0 or 1");
-    if (t.tsteps == 1 && g.model != RD_MODEL_CH_FRONT && (t.tile_y & 1))
+    if (t.tsteps == 1 && (!is_ch(g.model) || stencil_of(g) == 19) && (t.tile_y & 1))
         return fail(nullptr, RD_EINVAL, "tile_y must be even for one step per launch");
     if (threads_of(g.model, t.tsteps, t.tile_y, stencil_of(g)) > kMaxThreads)
         return fail(nullptr, RD_EINVAL, "tile_y %d too tall for %d steps per launch", t.tile_y,
@@ -437,7 +476,7 @@ int wave_zchunk(const std::vector<std::pair<long long, int>>& cols_nz, long long
 
 // Default tile height of the one-step kernels: 14 rows (12 for the front
 // model, whose kernel keeps more planes) fit two CTAs per SM.
-int default_tile_y(int model) { return model == RD_MODEL_CH_FRONT ? 12 : 14; }
+int default_tile_y(int model) { return is_ch(model) ? 12 : 14; }
 
 rd_tuning default_tuning(const rd_config& g) {
     rd_tuning t{};
@@ -492,6 +531,14 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
         d.p[0] = (float)g.params[0];
         d.p[1] = (float)g.params[1];
         break;
+    case RD_MODEL_CH_TABLE1:
+        d.p[0] = (float)(g.dt * g.params[0]);
+        d.p[1] = (float)(-g.dt * g.params[2] * ih2);
+        d.p[2] = (float)(-g.params[5] * ih2);
+        d.p[3] = (float)(g.dt * g.params[1]);
+        d.p[4] = (float)g.params[3];
+        d.p[5] = (float)g.params[4];
+        break;
     case RD_MODEL_TURING:
         d.p[0] = (float)g.params[0];
         d.p[1] = (float)g.params[1];
@@ -500,6 +547,7 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
     default: break;
     }
     d.courant = g.wind_kind != RD_WIND_NONE ? c->courant : nullptr;
+    d.mu = c->mu;
     d.src_s = g.src_species >= 0 ? g.src_species : -1;
     d.src_x = g.src_x; d.src_y = g.src_y; d.src_z = g.src_z;
     d.src_amt = (float)(g.src_rate * g.dt);
@@ -520,7 +568,7 @@ long long items_of(const InstDesc& d) { return (long long)d.ntx * d.nty * d.nzc;
 bool plain_problem(const rd_config& g) {
     if (g.wind_kind != RD_WIND_NONE || g.src_species >= 0) return false;
     // the front kernel's plain path still applies held layers
-    const bool held_ok = g.model == RD_MODEL_CH_FRONT;
+    const bool held_ok = is_ch(g.model);
     for (int s = 0; s < g.nspecies; ++s) {
         for (int f = 0; f < 6; ++f)
             if (g.bc[s][f] == RD_BC_DIRICHLET && !held_ok) return false;
@@ -590,7 +638,7 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     cudaError_t e =
         launch_model(c->cfg.model, c->cfg.storage, T, a, (int)grid, sm, st, nullptr, sten);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
-    c->launches++;
+    c->launches += kernels_per_step(c->cfg);
     return RD_OK;
 }
 
@@ -609,6 +657,7 @@ rd_status build_ctx_graph(rd_ctx* c) {
     if (!c->capture_stream)
         RD_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
     RD_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = c->launches;
     rd_status st = RD_OK;
     for (int i = 0; i < kGraphLaunches && st == RD_OK; ++i)
         st = launch_ctx(c, c->tun.tsteps, i & 1, c->capture_stream);
@@ -619,8 +668,8 @@ rd_status build_ctx_graph(rd_ctx* c) {
     e = cudaGraphInstantiate(&c->graph.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-    c->launches -= kGraphLaunches;   // captured, not run
-    c->graph.launches = kGraphLaunches;
+    c->graph.launches = (int)(c->launches - before);   // kernels in the graph
+    c->launches = before;                               // captured, not run
     c->graph.tsteps = c->tun.tsteps;
     c->graph.key = key;
     return RD_OK;
@@ -643,7 +692,7 @@ rd_status step_ctx(rd_ctx* c, int64_t n) {
         while (full >= kGraphLaunches) {
             cudaError_t e = cudaGraphLaunch(c->graph.exec, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
-            c->launches += kGraphLaunches;
+            c->launches += c->graph.launches;
             full -= kGraphLaunches;
         }
     }
@@ -919,7 +968,7 @@ rd_status rd_set_kernel(rd_ctx* c, int32_t kernel) {
         return fail(c, RD_EINVAL, "unknown kernel %d", kernel);
     if (kernel != RD_KERNEL_MARCH) {
         const rd_config& g = c->cfg;
-        if (stencil_of(g) != 19 || g.storage != RD_STORE_F32 || g.model == RD_MODEL_CH_FRONT ||
+        if (stencil_of(g) != 19 || g.storage != RD_STORE_F32 || is_ch(g.model) ||
             !plain_problem(g))
             return fail(c, RD_EUNSUPPORTED,
                         "the Shared and Moving Tiles kernels need the 19-point stencil, FP32 "
@@ -966,7 +1015,7 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
     for (int T = 1; T <= max_tsteps(g); ++T)
         for (int ty : {4, 8, 10, 12, 14, 16, 20, 24, 32}) {
           // the register cap is a variant of the 7-point one-step kernel
-          const bool rc_variant = T == 1 && g.model != RD_MODEL_CH_FRONT && sten == 7;
+          const bool rc_variant = T == 1 && !is_ch(g.model) && sten == 7;
           for (int rc = 0; rc <= (rc_variant ? 1 : 0); ++rc) {
             rd_tuning t{};
             t.tsteps = T; t.tile_q = kTileQ; t.tile_y = ty; t.graph = 1; t.zchunk = 1;
@@ -1079,7 +1128,7 @@ const char* rd_last_error(const rd_ctx* c) { return c ? c->err : g_err; }
 rd_status rd_batch_create(int32_t model, int32_t storage, rd_batch** out) {
     if (!out) return RD_EINVAL;
     *out = nullptr;
-    if (model < RD_MODEL_DIFFUSION || model > RD_MODEL_TURING)
+    if (model < RD_MODEL_DIFFUSION || model > RD_MODEL_CH_TABLE1)
         return fail(nullptr, RD_EINVAL, "bad model");
     if (storage != RD_STORE_F32 && storage != RD_STORE_BF16) return fail(nullptr, RD_EINVAL, "bad storage");
     rd_batch* b = new (std::nothrow) rd_batch();
@@ -1102,10 +1151,11 @@ rd_status rd_batch_add(rd_batch* b, rd_ctx* c) {
     if (c->batch) return fail(c, RD_EINVAL, "context already in a batch");
     if (c->cfg.model != b->model || c->cfg.storage != b->storage)
         return fail(c, RD_EINVAL, "model/storage differ from the batch");
-    if (stencil_of(c->cfg) != 7)
-        return fail(c, RD_EUNSUPPORTED, "batches of this build step the 7-point stencil only");
+    if (!b->members.empty() && stencil_of(c->cfg) != b->stencil)
+        return fail(c, RD_EINVAL, "the members of a batch share one stencil");
     if (!c->state) return fail(c, RD_EINVAL, "no memory attached");
     cudaStreamSynchronize(c->stream);
+    if (b->members.empty()) b->stencil = stencil_of(c->cfg);
     b->members.push_back(c);
     c->batch = b;
     b->members_version++;
@@ -1153,7 +1203,7 @@ rd_tuning batch_tuning(rd_batch* b) {
     t.tile_q = kTileQ;
     t.tile_y = default_tile_y(b->model);
     t.graph = 1;
-    const int occ = occupancy(b->model, b->storage, 1, t.tile_y);
+    const int occ = occupancy(b->model, b->storage, 1, t.tile_y, 0, 0, b->stencil);
     std::vector<std::pair<long long, int>> cols_nz;
     for (rd_ctx* c : b->members)
         cols_nz.push_back({(long long)tiles(c->cfg.nx, t.tile_q * vec_of(b->storage)) *
@@ -1204,6 +1254,9 @@ rd_status batch_upload(rd_batch* b, const rd_tuning& t, long long* nitems) {
     return RD_OK;
 }
 
+// launches (of T steps each, alternating parity) captured in a batch's graph
+constexpr int kBatchGraphLaunches = 16;
+
 rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long long nitems,
                        cudaStream_t st) {
     LaunchArgs a{};
@@ -1215,12 +1268,13 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
     a.plain = 1;
     for (rd_ctx* m : b->members) a.plain = a.plain && plain_problem(m->cfg);
     a.ty = t.tile_y;
-    const size_t sm = smem_of(b->model, b->storage, T, a.ty);
-    const int occ = std::max(1, occupancy(b->model, b->storage, T, a.ty, a.regcap, a.plain));
+    const size_t sm = smem_of(b->model, b->storage, T, a.ty, b->stencil);
+    const int occ = std::max(
+        1, occupancy(b->model, b->storage, T, a.ty, a.regcap, a.plain, b->stencil));
     const long long grid = std::min<long long>(nitems, (long long)occ * num_sms());
-    cudaError_t e = launch_model(b->model, b->storage, T, a, (int)grid, sm, st, nullptr);
+    cudaError_t e = launch_model(b->model, b->storage, T, a, (int)grid, sm, st, nullptr, b->stencil);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch step launch");
-    b->launches++;
+    b->launches += kernels_per_step(b->members[0]->cfg);
     return RD_OK;
 }
 
@@ -1251,7 +1305,7 @@ rd_status rd_batch_step(rd_batch* b, int64_t nsteps) {
     const int rem = (int)(nsteps % T);
     int parity = 0;
     const long long key = b->members_version * 1000003LL + nitems;
-    if (t.graph && full >= 2) {
+    if (t.graph && full >= kBatchGraphLaunches) {
         if (!b->graph.exec || b->graph.key != key) {
             b->graph.reset();
             if (!b->capture_stream &&
@@ -1259,8 +1313,9 @@ rd_status rd_batch_step(rd_batch* b, int64_t nsteps) {
                 return fail(nullptr, RD_ECUDA, "capture stream");
             cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_fail(nullptr, e, "begin capture");
-            st = batch_launch(b, t, T, 0, nitems, b->capture_stream);
-            if (st == RD_OK) st = batch_launch(b, t, T, 1, nitems, b->capture_stream);
+            const int64_t before = b->launches;
+            for (int i = 0; i < kBatchGraphLaunches && st == RD_OK; ++i)
+                st = batch_launch(b, t, T, i & 1, nitems, b->capture_stream);
             cudaGraph_t g = nullptr;
             e = cudaStreamEndCapture(b->capture_stream, &g);
             if (st != RD_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -1268,14 +1323,15 @@ rd_status rd_batch_step(rd_batch* b, int64_t nsteps) {
             e = cudaGraphInstantiate(&b->graph.exec, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(nullptr, e, "instantiate");
-            b->launches -= 2;
+            b->graph.launches = (int)(b->launches - before);   // kernels in the graph
+            b->launches = before;                               // captured, not run
             b->graph.key = key;
         }
-        while (full >= 2) {
+        while (full >= kBatchGraphLaunches) {
             cudaError_t e = cudaGraphLaunch(b->graph.exec, b->stream);
             if (e != cudaSuccess) return cuda_fail(nullptr, e, "graph launch");
-            b->launches += 2;
-            full -= 2;
+            b->launches += b->graph.launches;
+            full -= kBatchGraphLaunches;
         }
     }
     for (int64_t i = 0; i < full; ++i) {

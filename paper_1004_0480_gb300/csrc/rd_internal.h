@@ -28,6 +28,10 @@ struct InstDesc {
     float dt;
     float p[8];                // model constants, see the model structs
     const float* courant;      // u_x(z) * dt / h per plane, or nullptr
+    float* mu;                 // 19-point Cahn-Hilliard models: the chemical
+                               // potential of species 2 (float, the state's
+                               // pitch and plane size), written by the first
+                               // of the two launches of a step; else nullptr
     int src_x, src_y, src_z, src_s;          // src_s < 0: no source
     float src_amt;             // emission per step: rate * dt
     int ntx, nty, nzc, zchunk; // work items: ntx * nty * nzc
@@ -59,11 +63,14 @@ cudaError_t launch_ch_front(int storage, int tsteps, const LaunchArgs& a, int gr
                             size_t smem, cudaStream_t st, int* occ);
 cudaError_t launch_air(int storage, int tsteps, const LaunchArgs& a, int grid,
                        size_t smem, cudaStream_t st, int* occ);
+cudaError_t launch_ch_table1(int storage, int tsteps, const LaunchArgs& a, int grid,
+                             size_t smem, cudaStream_t st, int* occ);
 // Dynamic shared memory (bytes) and CTA size of one step kernel variant.
 size_t smem_diffusion(int storage, int tsteps, int ty);
 size_t smem_brusselator(int storage, int tsteps, int ty);
 size_t smem_ch_front(int storage, int tsteps, int ty);
 size_t smem_air(int storage, int tsteps, int ty);
+size_t smem_ch_table1(int storage, int tsteps, int ty);
 int step_threads(int model, int tsteps, int ty);
 
 // Auxiliary kernels (rd_aux.cu).

@@ -20,6 +20,13 @@ __host__ __device__ inline int plane_elems19(int ty) {
 __host__ __device__ inline size_t smem19_bytes(int nspecies, int ebytes, int ty) {
     return (size_t)kRing19 * nspecies * plane_elems19(ty) * ebytes + 96 * 16;
 }
+// The same with ``mu_plane``: one more float plane per slot (the second
+// launch of a Cahn-Hilliard step, which reads mu beside the state).
+__host__ __device__ inline size_t smem19_pass_bytes(int nfields, int ebytes, bool mu_plane,
+                                                    int ty) {
+    return smem19_bytes(nfields, ebytes, ty) +
+           (mu_plane ? (size_t)kRing19 * plane_elems19(ty) * 4 : 0);
+}
 inline int threads19(int ty) { return kTileQ * ty + 32; }
 
 // Single-instance launchers (one translation unit per model).  With
@@ -30,5 +37,14 @@ cudaError_t launch19_brusselator(int storage, const LaunchArgs& a, int grid, siz
                                  cudaStream_t st, int* occ);
 cudaError_t launch19_air(int storage, const LaunchArgs& a, int grid, size_t smem,
                          cudaStream_t st, int* occ);
+// The two launches of a 19-point Cahn-Hilliard step (pass 1: mu, pass 2: the
+// update); ``smem`` is the larger of the two passes' needs (smem19_ch_bytes).
+cudaError_t launch19_ch_front(int storage, int pass, const LaunchArgs& a, int grid, size_t smem,
+                              cudaStream_t st, int* occ);
+cudaError_t launch19_ch_table1(int storage, int pass, const LaunchArgs& a, int grid, size_t smem,
+                               cudaStream_t st, int* occ);
+inline size_t smem19_ch_bytes(int ebytes, int ty) {
+    return smem19_pass_bytes(3, ebytes, true, ty);
+}
 
 }  // namespace rdk

@@ -40,14 +40,25 @@
 
 namespace rdk {
 
-template <class M, class ST> struct Layout19 {
+// PASS 0: one step of a model without Cahn-Hilliard.  For the models with a
+// Cahn-Hilliard species (species 2, c) a step is two launches, the paper's
+// "Laplacian, boundary rule, Laplacian" (Section 4.1): PASS 1 writes the
+// chemical potential mu = g(c) - p[2] h^2 Lap c of every cell to the
+// instance's mu field, PASS 2 then updates a, b and c, reading mu as one more
+// field of the ring (its ghost cells copied in under the same rules, which
+// is the paper's "boundary rule" applied to mu) and adding p[1] h^2 Lap mu
+// to c.  The ring of PASS 1 holds species 2 only.
+template <class M, class ST, int PASS> struct Layout19 {
     static constexpr int S = M::S;
+    static constexpr int NS = PASS == 1 ? 1 : S;    // state fields per slot
+    static constexpr bool MUF = PASS == 2;          // plus one float mu plane
     static constexpr int RING = kRing19;
     static constexpr int P = 5;
     static_assert(RING == P + 1, "the copy of step q refills the slot of plane q - 2");
+    static_assert(PASS == 0 || M::CH, "passes 1 and 2 are for Cahn-Hilliard models");
     __host__ __device__ static int plane_elems(int ty) { return plane_elems19(ty); }
     __host__ __device__ static size_t total(int ty) {
-        return smem19_bytes(S, (int)sizeof(ST), ty);
+        return smem19_pass_bytes(NS, (int)sizeof(ST), MUF, ty);
     }
     __host__ __device__ static int threads(int ty) { return kTileQ * ty + 32; }
 };
@@ -124,12 +135,35 @@ __device__ __forceinline__ void species19(const InstDesc& sd, int s, float k6,
     for (int e = 0; e < kVEC; ++e) o[e] = __fadd_rn(c[e], __fmaf_rn(k6, lap6[e], in[e]));
 }
 
-// PLAIN: no held layer, point source or wind.
-template <class M, class ST, bool ONE, bool PLAIN>
+// One float field of a plane (the mu plane of PASS 2), fetched with the
+// state's descriptor: the same rows, pitch and ghost rules.  ``mu0`` is the
+// address of the mu plane's element 0.
+template <class ST>
+__device__ __forceinline__ void fetch_mu(const Fetch& f, unsigned char* mu0,
+                                         const float* gplane, int nx, bool elems, bool px) {
+    float* d = reinterpret_cast<float*>(mu0 + f.soff / (int)sizeof(ST) * 4);
+    Store<float>::cp_async_if(d, gplane + f.goff, f.mode == 1);
+    if (elems && f.mode == 2) {
+#pragma unroll
+        for (int e = 0; e < kVEC; ++e) {
+            const int x = f.xs + e;
+            const int xi = px ? wrapi(x, nx) : (x < 0 ? 0 : (x >= nx ? nx - 1 : x));
+            Store<float>::cp_async_elem(d + e, gplane + f.goff + xi);
+        }
+    }
+}
+
+// PLAIN: no held layer, point source or wind.  PASS: see Layout19.
+template <class M, class ST, bool ONE, bool PLAIN, int PASS>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
-    using LY = Layout19<M, ST>;
+    using LY = Layout19<M, ST, PASS>;
     constexpr int S = M::S;
+    constexpr int NS = LY::NS;
+    constexpr bool MUF = LY::MUF;
+    // fields whose plane sums are formed: every state field (PASS 0), c
+    // (PASS 1), a, b and mu (PASS 2; c needs only its own cells there)
+    constexpr int NSUM = PASS == 2 ? 3 : NS;
     constexpr int P = LY::P;
     constexpr int RING = LY::RING;
     constexpr int EB = (int)sizeof(ST);
@@ -140,15 +174,21 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
 
     const int tid = threadIdx.x;
     const int TY = a.ty;
-    const int PEB = LY::plane_elems(TY) * EB;                // bytes per species plane
-    const int SLOTB = S * PEB;                               // bytes per ring slot
-    unsigned char* const ring = smem + kVEC * EB;            // slot 0, species 0
+    const int PE = LY::plane_elems(TY);
+    const int PEB = PE * EB;                                 // bytes per state plane
+    const int SLOTB = NS * PEB + (MUF ? PE * 4 : 0);         // bytes per ring slot
+    unsigned char* const ring = smem + kVEC * EB;            // slot 0, field 0
     int4* const hfetch = reinterpret_cast<int4*>(smem + RING * SLOTB);
     const int ncomp = kTileQ * TY;
     const bool halo_warp = tid >= ncomp;
     const int r = tid / kTileQ;
     const int v = tid - r * kTileQ;
-    const int own_b = ((r + 1) * kRW + (v + 1) * kVEC) * EB;
+    const int own_e = (r + 1) * kRW + (v + 1) * kVEC;        // element offset in a plane
+    const int own_b = own_e * EB;
+    // the mu plane of a slot (PASS 2) starts at NS * PEB; its guard is
+    // kVEC floats, the state planes' kVEC elements of ST
+    const int mu0_b = NS * PEB + kVEC * (4 - EB);            // element 0, from a slot
+    const int mu_own_b = mu0_b + own_e * 4;
 
     int cur_inst = -1;
     if (tid == 0) s_inst = 0;
@@ -167,9 +207,10 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
         const int z0 = zc * sd.zchunk;
         const int z1 = min(z0 + sd.zchunk, nz);
         const int lin = sd.par ^ a.parity;
-        const ST* const gin = reinterpret_cast<const ST*>(sd.base[lin][0]);
+        const ST* const gin = reinterpret_cast<const ST*>(sd.base[lin][PASS == 1 ? 2 : 0]);
         ST* const gout = reinterpret_cast<ST*>(sd.base[lin ^ 1][0]);
-        const long long fstride = S > 1 ? reinterpret_cast<const ST*>(sd.base[lin][1]) - gin : 0;
+        const long long fstride =
+            NS > 1 ? reinterpret_cast<const ST*>(sd.base[lin][1]) - gin : 0;
         const long long plane = sd.plane;
 
         // ---- halo lanes: 2 TY side vectors, 2 x 16 row vectors, then the 4
@@ -212,12 +253,18 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
         const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
         const unsigned xyf = xy_faces(xs, y, nx, ny);
         const Fetch fo = halo_warp ? Fetch{0, 0, 0, 0}
-                                   : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB, true);
+                                   : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_e, true);
         int loff, roff;                           // x neighbours beside the own vector
         xface_offsets<ST>(xs, nx, px, loff, roff);
+        int loff_f = 0, roff_f = 0;               // the same in the float mu plane
+        if constexpr (MUF) xface_offsets<float>(xs, nx, px, loff_f, roff_f);
+        // k6: D dt / (6 h^2) per species; PASS 1: p[2] / 6 (mu); PASS 2:
+        // k6[2] = p[1] / 6 (the mobility term of c)
         float k6[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) k6[s] = __fdiv_rn(sd.kx[s], 6.0f);
+        if constexpr (PASS == 1) k6[0] = __fdiv_rn(sd.p[2], 6.0f);
+        if constexpr (PASS == 2) k6[2] = __fdiv_rn(sd.p[1], 6.0f);
         __syncthreads();   // halo descriptors written
 
         // ---- the march: plane nld is fetched P planes ahead into slot sl;
@@ -229,17 +276,21 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
             if (nld <= z1) {
                 const int zs = in_z ? zld : (nld < 0 ? 0 : nz - 1);
                 const ST* gld = gin + (long long)zs * plane;
+                const float* gmu = nullptr;
+                if constexpr (MUF) gmu = sd.mu + (long long)zs * plane;
                 unsigned char* buf = ring + sl * SLOTB;
                 if (halo_warp) {
                     const int hl = tid - ncomp;
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const int4 h = hfetch[hl + 32 * k];
-                        fetch_all<ST, S>(Fetch{h.x, h.y, h.z, h.w}, buf, PEB, gld, fstride, nx,
-                                         elems, px);
+                        const Fetch f{h.x, h.y, h.z, h.w};
+                        fetch_all<ST, NS>(f, buf, PEB, gld, fstride, nx, elems, px);
+                        if constexpr (MUF) fetch_mu<ST>(f, buf + mu0_b, gmu, nx, elems, px);
                     }
                 } else {
-                    fetch_all<ST, S>(fo, buf, PEB, gld, fstride, nx, elems, px);
+                    fetch_all<ST, NS>(fo, buf, PEB, gld, fstride, nx, elems, px);
+                    if constexpr (MUF) fetch_mu<ST>(fo, buf + mu0_b, gmu, nx, elems, px);
                 }
             }
             ++nld;
@@ -247,14 +298,25 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
             else if (++zld == nz) zld = 0;
             cp_async_commit();
         };
+        // plane sums of field f of the slot at ``base`` (own vector address)
+        auto sums = [&](const unsigned char* base, int f, float (&c)[kVEC], float (&zs)[kVEC],
+                        float (&ws)[kVEC]) {
+            if (MUF && f == NSUM - 1)
+                plane_sums19<float>(base - own_b + mu_own_b, loff_f, roff_f, c, zs, ws);
+            else
+                plane_sums19<ST>(base + f * PEB, loff, roff, c, zs, ws);
+        };
 #pragma unroll 1
         for (int j = 0; j < P; ++j) issue(j);
         int zq = pz ? wrapi(z0, nz) : z0;
         ST* gst = gout + (long long)z0 * plane + (long long)y * pitch + xs;
+        float* gmu_st = nullptr;
+        if constexpr (PASS == 1) gmu_st = sd.mu + (long long)z0 * plane + (long long)y * pitch + xs;
         const float* courant = sd.courant;
         int sc = 1;                               // ring slot of plane q
         // sums of planes q-1 and q, and the own vector of plane q
-        float zsum_m[S][kVEC], zsum_0[S][kVEC], wsum_0[S][kVEC], c_0[S][kVEC];
+        float zsum_m[NSUM][kVEC], zsum_0[NSUM][kVEC], wsum_0[NSUM][kVEC], c_0[NSUM][kVEC];
+        float cc_0[kVEC];                         // PASS 2: own c of plane q
 #pragma unroll 1
         for (int q = z0; q < z1; ++q) {
             const int sm = sc == 0 ? RING - 1 : sc - 1;
@@ -268,61 +330,90 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
                 if (!halo_warp) {
                     const unsigned char* Pm = ring + sm * SLOTB + own_b;
 #pragma unroll
-                    for (int s = 0; s < S; ++s) {
+                    for (int f = 0; f < NSUM; ++f) {
                         float cm[kVEC], wm[kVEC];
-                        plane_sums19<ST>(Pm + s * PEB, loff, roff, cm, zsum_m[s], wm);
-                        plane_sums19<ST>(Pc + s * PEB, loff, roff, c_0[s], zsum_0[s], wsum_0[s]);
+                        sums(Pm, f, cm, zsum_m[f], wm);
+                        sums(Pc, f, c_0[f], zsum_0[f], wsum_0[f]);
                     }
+                    if constexpr (PASS == 2) lds_vec<ST>(Pc + 2 * PEB, cc_0);
                 }
                 __syncthreads();   // plane z0 - 1 is refilled at the next step
             }
             if (!halo_warp) {
                 const unsigned char* Pp = ring + sp * SLOTB + own_b;
-                float c_p[S][kVEC], zsum_p[S][kVEC], wsum_p[S][kVEC], inc[S][kVEC];
+                float c_p[NSUM][kVEC], zsum_p[NSUM][kVEC], wsum_p[NSUM][kVEC];
+                float cc_p[kVEC];
 #pragma unroll
-                for (int s = 0; s < S; ++s)
-                    plane_sums19<ST>(Pp + s * PEB, loff, roff, c_p[s], zsum_p[s], wsum_p[s]);
+                for (int f = 0; f < NSUM; ++f) sums(Pp, f, c_p[f], zsum_p[f], wsum_p[f]);
+                if constexpr (PASS == 2) lds_vec<ST>(Pp + 2 * PEB, cc_p);
+                // 6 h^2 Lap of each summed field on plane q
+                float lap6[NSUM][kVEC];
 #pragma unroll
-                for (int e = 0; e < kVEC; ++e) {
-                    float cv[S], iv[S];
-#pragma unroll
-                    for (int s = 0; s < S; ++s) cv[s] = c_0[s][e];
-                    M::react(sd, cv, iv);
-#pragma unroll
-                    for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
-                }
-                const float cx = (!PLAIN && courant) ? courant[zq] : 0.0f;
-                const bool src_here = src_col && zq == sd.src_z;
-                const unsigned faces = xyf | z_faces(q, nz);
-#pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    float lap6[kVEC], o[kVEC];
+                for (int f = 0; f < NSUM; ++f)
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e)
-                        lap6[e] = __fmaf_rn(-24.0f, c_0[s][e],
-                                            __fadd_rn(__fadd_rn(zsum_m[s][e], zsum_p[s][e]),
-                                                      wsum_0[s][e]));
-                    float left = 0.0f, right = 0.0f;
-                    if (!PLAIN && cx != 0.0f) {
-                        left = lds_one<ST>(Pc + s * PEB + loff);
-                        right = lds_one<ST>(Pc + s * PEB + roff);
-                    }
-                    species19<PLAIN>(sd, s, k6[s], c_0[s], lap6, inc[s], cx, left, right,
-                                     src_here, px, xs, o);
-                    if constexpr (!PLAIN) held_layers_at(sd, s, faces, xs, y, q, o);
-                    if (computes) Store<ST>::store(gst + s * fstride, o);
-                }
+                        lap6[f][e] = __fmaf_rn(-24.0f, c_0[f][e],
+                                               __fadd_rn(__fadd_rn(zsum_m[f][e], zsum_p[f][e]),
+                                                         wsum_0[f][e]));
+                if constexpr (PASS == 1) {
+                    // mu = g(c) - (p[2] / 6) 6 h^2 Lap c
+                    float mu[kVEC];
 #pragma unroll
-                for (int s = 0; s < S; ++s)
+                    for (int e = 0; e < kVEC; ++e)
+                        mu[e] = __fmaf_rn(-k6[0], lap6[0][e], M::g(sd, c_0[0][e]));
+                    if (computes) Store<float>::store(gmu_st, mu);
+                } else {
+                    // state of plane q: a, b (and every PASS 0 species) from
+                    // the summed fields, c of PASS 2 from its own vector
+                    float cen[S][kVEC], inc[S][kVEC];
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int e = 0; e < kVEC; ++e)
+                            cen[s][e] = (PASS == 2 && s == 2) ? cc_0[e] : c_0[s][e];
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e) {
-                        zsum_m[s][e] = zsum_0[s][e];
-                        zsum_0[s][e] = zsum_p[s][e];
-                        wsum_0[s][e] = wsum_p[s][e];
-                        c_0[s][e] = c_p[s][e];
+                        float cv[S], iv[S];
+#pragma unroll
+                        for (int s = 0; s < S; ++s) cv[s] = cen[s][e];
+                        M::react(sd, cv, iv);
+#pragma unroll
+                        for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
                     }
+                    const float cx = (!PLAIN && courant) ? courant[zq] : 0.0f;
+                    const bool src_here = src_col && zq == sd.src_z;
+                    const unsigned faces = xyf | z_faces(q, nz);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        float o[kVEC];
+                        // PASS 2, c: the Laplacian is that of mu (summed field 2)
+                        const float(&ls)[kVEC] = lap6[(PASS == 2 && s == 2) ? 2 : (s < NSUM ? s : 0)];
+                        float left = 0.0f, right = 0.0f;
+                        if (!PLAIN && cx != 0.0f) {
+                            left = lds_one<ST>(Pc + s * PEB + loff);
+                            right = lds_one<ST>(Pc + s * PEB + roff);
+                        }
+                        species19<PLAIN>(sd, s, k6[s], cen[s], ls, inc[s], cx, left, right,
+                                         src_here, px, xs, o);
+                        if constexpr (!PLAIN) held_layers_at(sd, s, faces, xs, y, q, o);
+                        if (computes) Store<ST>::store(gst + s * fstride, o);
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < NSUM; ++f)
+#pragma unroll
+                    for (int e = 0; e < kVEC; ++e) {
+                        zsum_m[f][e] = zsum_0[f][e];
+                        zsum_0[f][e] = zsum_p[f][e];
+                        wsum_0[f][e] = wsum_p[f][e];
+                        c_0[f][e] = c_p[f][e];
+                    }
+                if constexpr (PASS == 2)
+#pragma unroll
+                    for (int e = 0; e < kVEC; ++e) cc_0[e] = cc_p[e];
             }
             gst += plane;
+            if constexpr (PASS == 1) gmu_st += plane;
             sc = sc == RING - 1 ? 0 : sc + 1;
             if (!pz) zq = q + 1;
             else if (++zq == nz) zq = 0;
@@ -332,23 +423,29 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
     }
 }
 
-// Launch helper used by the per-model translation units: single-instance
-// launches, even tile heights (16 TY compute threads, then a whole halo
-// warp).
-template <class M, class ST>
-cudaError_t launch19_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t st, int* occ) {
-    if (!a.use_one || (a.ty & 1) || a.ty < 2) return cudaErrorInvalidValue;
-    void (*k)(const LaunchArgs) =
-        a.plain ? rd_step19_kernel<M, ST, true, true> : rd_step19_kernel<M, ST, true, false>;
-    static size_t configured[2] = {0, 0};
-    size_t& conf = configured[a.plain ? 1 : 0];
+// Launch helper used by the per-model translation units: even tile heights
+// (16 TY compute threads, then a whole halo warp); single instances (the
+// descriptor in the kernel parameters) or batches (a device array of
+// descriptors).
+template <class M, class ST, int PASS>
+cudaError_t launch19_pass(const LaunchArgs& a, int grid, size_t smem, cudaStream_t st, int* occ) {
+    if ((a.ty & 1) || a.ty < 2) return cudaErrorInvalidValue;
+    void (*k)(const LaunchArgs);
+    if (a.use_one)
+        k = a.plain ? rd_step19_kernel<M, ST, true, true, PASS>
+                    : rd_step19_kernel<M, ST, true, false, PASS>;
+    else
+        k = a.plain ? rd_step19_kernel<M, ST, false, true, PASS>
+                    : rd_step19_kernel<M, ST, false, false, PASS>;
+    static size_t configured[4] = {0, 0, 0, 0};
+    size_t& conf = configured[(a.plain ? 1 : 0) + (a.use_one ? 2 : 0)];
     if (smem > conf) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         conf = smem;
     }
-    const int threads = Layout19<M, ST>::threads(a.ty);
+    const int threads = Layout19<M, ST, PASS>::threads(a.ty);
     if (threads > kMaxThreads) return cudaErrorInvalidConfiguration;
     if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, threads, smem);
     k<<<grid, threads, smem, st>>>(a);
@@ -358,8 +455,25 @@ cudaError_t launch19_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_
 template <class M>
 cudaError_t launch19_model(int storage, const LaunchArgs& a, int grid, size_t smem,
                            cudaStream_t st, int* occ) {
-    if (storage == RD_STORE_F32) return launch19_one<M, float>(a, grid, smem, st, occ);
-    if (storage == RD_STORE_BF16) return launch19_one<M, __nv_bfloat16>(a, grid, smem, st, occ);
+    if (storage == RD_STORE_F32) return launch19_pass<M, float, 0>(a, grid, smem, st, occ);
+    if (storage == RD_STORE_BF16)
+        return launch19_pass<M, __nv_bfloat16, 0>(a, grid, smem, st, occ);
+    return cudaErrorInvalidValue;
+}
+
+// The two launches of a Cahn-Hilliard step: pass 1 (mu), pass 2 (update).
+// ``smem`` is pass 2's size; pass 1 takes the smaller ring of its own layout.
+template <class M>
+cudaError_t launch19_ch_model(int storage, int pass, const LaunchArgs& a, int grid, size_t smem,
+                              cudaStream_t st, int* occ) {
+    if (storage == RD_STORE_F32)
+        return pass == 1 ? launch19_pass<M, float, 1>(a, grid, Layout19<M, float, 1>::total(a.ty),
+                                                      st, occ)
+                         : launch19_pass<M, float, 2>(a, grid, smem, st, occ);
+    if (storage == RD_STORE_BF16)
+        return pass == 1 ? launch19_pass<M, __nv_bfloat16, 1>(
+                               a, grid, Layout19<M, __nv_bfloat16, 1>::total(a.ty), st, occ)
+                         : launch19_pass<M, __nv_bfloat16, 2>(a, grid, smem, st, occ);
     return cudaErrorInvalidValue;
 }
 

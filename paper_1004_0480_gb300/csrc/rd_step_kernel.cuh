@@ -173,6 +173,20 @@ struct MAir {
     }
 };
 
+// Models with a Cahn-Hilliard species (species 2, c) share one shape: the
+// chemical potential mu = g(c) - p[2] Lap_h c, where Lap_h c = (sum of the
+// 6 neighbours - 6 c) is the Laplacian times h^2, and the update
+// c += p[1] Lap_h mu + dt R_c, with no Fickian term for c (the biharmonic
+// as "Laplacian, boundary rule, Laplacian", Section 4.1).
+
+// mu from g(c) and the 6 neighbours of c
+__device__ __forceinline__ float ch_mu(float g, float pk, float c, float xm, float xp, float ym,
+                                       float yp, float zm, float zp) {
+    const float s6 = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
+    const float lap = __fmaf_rn(-6.0f, c, s6);
+    return __fmaf_rn(-pk, lap, g);
+}
+
 // Front a + b -> c with Cahn-Hilliard c.
 // p[0] = dt k, p[1] = dt M / h^2, p[2] = kappa / h^2.
 struct MChFront {
@@ -184,15 +198,40 @@ struct MChFront {
         inc[1] = -q;
         inc[2] = q;
     }
-    // mu = f'(c) - (kappa/h^2) (sum of 6 neighbours - 6 c), f'(c) = 2c(c-1)(2c-1)
+    // g(c) = f'(c) = 2c(c-1)(2c-1), the derivative of the double well
+    __device__ __forceinline__ static float g(const InstDesc&, float c) {
+        const float c2 = __fadd_rn(c, c);
+        return __fmul_rn(__fmul_rn(c2, __fsub_rn(c, 1.0f)), __fsub_rn(c2, 1.0f));
+    }
+    // mu = f'(c) - (kappa/h^2) (sum of 6 neighbours - 6 c)
     __device__ __forceinline__ static float mu(const InstDesc& d, float c, float xm, float xp,
                                                float ym, float yp, float zm, float zp) {
-        const float c2 = __fadd_rn(c, c);
-        const float fp = __fmul_rn(__fmul_rn(c2, __fsub_rn(c, 1.0f)), __fsub_rn(c2, 1.0f));
-        const float s6 = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)),
-                                   __fadd_rn(zm, zp));
-        const float lap = __fmaf_rn(-6.0f, c, s6);
-        return __fmaf_rn(-d.p[2], lap, fp);
+        return ch_mu(g(d, c), d.p[2], c, xm, xp, ym, yp, zm, zp);
+    }
+};
+
+// The phase separation behind a front of Table 1 (row 3): c1 + c2 -> c3 at
+// k1 c1 c2, the sink k2 c1 c3 taken from c1 and c3, and
+// dc3/dt += -lambda Lap(eps c3 - gamma c3^3 + sigma Lap c3).
+// p[0] = dt k1, p[1] = -dt lambda / h^2, p[2] = -sigma / h^2, p[3] = dt k2,
+// p[4] = eps, p[5] = gamma.
+struct MChTable1 {
+    static constexpr int S = 3;
+    static constexpr bool CH = true;
+    __device__ __forceinline__ static void react(const InstDesc& d, const float* c, float* inc) {
+        const float q1 = __fmul_rn(__fmul_rn(d.p[0], c[0]), c[1]);
+        const float q2 = __fmul_rn(__fmul_rn(d.p[3], c[0]), c[2]);
+        inc[0] = -__fadd_rn(q1, q2);
+        inc[1] = -q1;
+        inc[2] = __fsub_rn(q1, q2);
+    }
+    // g(c) = eps c - gamma c^3
+    __device__ __forceinline__ static float g(const InstDesc& d, float c) {
+        return __fmul_rn(c, __fmaf_rn(-d.p[5], __fmul_rn(c, c), d.p[4]));
+    }
+    __device__ __forceinline__ static float mu(const InstDesc& d, float c, float xm, float xp,
+                                               float ym, float yp, float zm, float zp) {
+        return ch_mu(g(d, c), d.p[2], c, xm, xp, ym, yp, zm, zp);
     }
 };
 
@@ -544,17 +583,19 @@ __global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const __grid_co
                 // z neighbours: the face plane itself at a zero-flux z face
                 const int qm = (!pz && q == 0) ? q : q - 1;
                 const int qp = (!pz && q == nz - 1) ? q : q + 1;
-                if (LY::is_mu(l)) {
-                    // mu of the Cahn-Hilliard species from state level l-1
-                    float c[kVEC], xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC];
-                    gather7<ST>(state_plane(l - 1, 2, q), state_plane(l - 1, 2, qm),
-                                state_plane(l - 1, 2, qp), ps, c, xm, xp, ym, yp, zm, zp);
-                    float mo[kVEC];
+                if constexpr (CH) {
+                    if (LY::is_mu(l)) {
+                        // mu of the Cahn-Hilliard species from state level l-1
+                        float c[kVEC], xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC];
+                        gather7<ST>(state_plane(l - 1, 2, q), state_plane(l - 1, 2, qm),
+                                    state_plane(l - 1, 2, qp), ps, c, xm, xp, ym, yp, zm, zp);
+                        float mo[kVEC];
 #pragma unroll
-                    for (int e = 0; e < kVEC; ++e)
-                        mo[e] = MChFront::mu(sd, c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e]);
-                    Store<float>::store(mu_plane(l, q) + ps.own, mo);
-                    continue;
+                        for (int e = 0; e < kVEC; ++e)
+                            mo[e] = M::mu(sd, c[e], xm[e], xp[e], ym[e], yp[e], zm[e], zp[e]);
+                        Store<float>::store(mu_plane(l, q) + ps.own, mo);
+                        continue;
+                    }
                 }
                 // state update from level ls (and, for Cahn-Hilliard, mu at l-1)
                 const int ls = CH ? l - 2 : l - 1;
@@ -1050,7 +1091,7 @@ __device__ __forceinline__ void fetch_all_mirror(const FetchM& f, unsigned char*
 
 // PLAIN: no point source or wind and isotropic D for a and b (held layers
 // are still applied); the update of a and b then needs no per-plane tests.
-template <class ST, bool ONE, bool PLAIN>
+template <class MC, class ST, bool ONE, bool PLAIN>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
     using LY = LayoutCH<ST>;
@@ -1187,7 +1228,7 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                 for (int e = 0; e < kVEC; ++e) {
                     const float xm = e ? c[e - 1] : left;
                     const float xp = (e < kVEC - 1) ? c[e + 1] : right;
-                    mu_p[e] = MChFront::mu(sd, c[e], xm, xp, ym[e], yp[e], zm[e], zp[e]);
+                    mu_p[e] = MC::mu(sd, c[e], xm, xp, ym[e], yp[e], zm[e], zp[e]);
                 }
                 Store<float>::store(muring + ((p + 1) & 1) * PE + own, mu_p);
             }
@@ -1207,7 +1248,7 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                     float cv[S], iv[S];
 #pragma unroll
                     for (int s = 0; s < S; ++s) cv[s] = cen[s][e];
-                    MChFront::react(sd, cv, iv);
+                    MC::react(sd, cv, iv);
 #pragma unroll
                     for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
                 }
@@ -1288,7 +1329,7 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
     constexpr bool lean_ch = (T == 1 && M::CH);
     void (*k)(const LaunchArgs);
     if constexpr (lean_ch) {
-        k = a.plain ? rd_stepch_kernel<ST, ONE, true> : rd_stepch_kernel<ST, ONE, false>;
+        k = a.plain ? rd_stepch_kernel<M, ST, ONE, true> : rd_stepch_kernel<M, ST, ONE, false>;
     } else if (lean) {
         // register budget of the one-step kernel: 128 (regcap 0) or 64 (regcap 1)
         if (a.plain)

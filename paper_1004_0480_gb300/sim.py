@@ -19,6 +19,7 @@ _PARAM_ORDER = {
     "ch_front": ("k", "M", "kappa"),
     "air": ("j", "k"),
     "turing": ("alpha", "beta", "gamma"),
+    "ch_table1": ("k1", "k2", "lam", "eps", "gamma", "sigma"),
 }
 
 

@@ -148,8 +148,15 @@ def test_validation_of_the_19_point_stencil(lib):
     c.D[1][2] = 1.0
     assert q(c) == L.RD_EINVAL
     assert b"diffusivity" in lib.rd_last_error(None)
-    # the front model's Cahn-Hilliard kernels are 7-point only
-    assert q(_cfg(W.with_(W.ch_front(8), stencil=19))) == L.RD_EUNSUPPORTED
+    # the Cahn-Hilliard models take the 19-point stencil too; their scratch
+    # then holds one more float field, mu (rows of 8 cells padded to 32)
+    xb7, xb19 = ctypes.c_size_t(), ctypes.c_size_t()
+    for model in (W.ch_front(8), W.ch_table1(shape=(8, 8, 8))):
+        assert lib.rd_query_sizes(ctypes.byref(_cfg(W.with_(model, stencil=19))), None,
+                                  ctypes.byref(xb19)) == L.RD_OK
+        assert lib.rd_query_sizes(ctypes.byref(_cfg(W.with_(model, stencil=7, dt=0.005))),
+                                  None, ctypes.byref(xb7)) == L.RD_OK
+        assert xb19.value - xb7.value == 8 * 8 * 32 * 4
     # stability: the update's centre weight is 1 - 4 D dt / h^2 (19-point)
     # against 1 - 6 D dt / h^2 (7-point)
     ok = W.with_(W.diffusion_blob(8, dt=0.25), stencil=19)
@@ -172,7 +179,7 @@ def test_validation_of_the_turing_model(lib):
     assert q(_cfg(W.with_(cfg, stencil=19))) == L.RD_OK
     # the Table 1 time step is inside both stencils' bounds; ten times it is not
     assert q(_cfg(W.with_(cfg, dt=cfg["dt"] * 10))) == L.RD_EUNSTABLE
-    assert q(_cfg(cfg, model=5)) == L.RD_EINVAL
+    assert q(_cfg(cfg, model=6)) == L.RD_EINVAL
 
 
 def test_bf16_rows_are_128_bytes(lib):
@@ -182,3 +189,22 @@ def test_bf16_rows_are_128_bytes(lib):
     assert lib.rd_query_sizes(ctypes.byref(c), ctypes.byref(sz), None) == L.RD_OK
     # 70 cells pad to 128 bf16 per row: 2 levels * 1 species * 128*3*2 * 2 bytes
     assert sz.value == 2 * ((128 * 3 * 2 * 2 + 255) // 256 * 256)
+
+
+def test_validation_of_the_table1_cahn_hilliard_model(lib):
+    sz = ctypes.c_size_t()
+    q = lambda c: lib.rd_query_sizes(ctypes.byref(c), ctypes.byref(sz), None)
+    cfg = W.ch_table1(shape=(16, 8, 8))          # the paper's dt = 0.02, 19-point
+    assert q(_cfg(cfg)) == L.RD_OK
+    # dt lambda L (sigma L + 3 gamma - eps) <= 2: 0.78 with L = 16/3 (19-point),
+    # 3.36 with L = 12 (7-point), which needs dt <= 2 / 168
+    assert q(_cfg(W.with_(cfg, stencil=7))) == L.RD_EUNSTABLE
+    assert q(_cfg(W.with_(cfg, stencil=7, dt=2.0 / 168))) == L.RD_OK
+    assert q(_cfg(W.with_(cfg, stencil=7, dt=2.0 / 168 * 1.001))) == L.RD_EUNSTABLE
+    assert q(_cfg(cfg, nspecies=2)) == L.RD_EINVAL
+    c = _cfg(cfg)
+    c.D[2][0] = c.D[2][1] = c.D[2][2] = 0.5      # c3 has no Fickian term
+    assert q(c) == L.RD_EUNSUPPORTED
+    c = _cfg(cfg)
+    c.bc[2][0] = L.BC["dirichlet"]               # no held layer on c3
+    assert q(c) == L.RD_EUNSUPPORTED
