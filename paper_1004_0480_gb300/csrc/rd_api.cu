@@ -562,13 +562,14 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
 
 long long items_of(const InstDesc& d) { return (long long)d.ntx * d.nty * d.nzc; }
 
-// No point source or wind, every species isotropic and, except for the front
-// model (whose one-step kernel applies held layers on this path too), no
-// held layer: the one-step kernels' branch-free update applies.
+// No point source or wind, every species isotropic and, except for the
+// 7-point Cahn-Hilliard models (whose one-step kernel applies held layers on
+// this path too), no held layer: the one-step kernels' branch-free update
+// applies.
 bool plain_problem(const rd_config& g) {
     if (g.wind_kind != RD_WIND_NONE || g.src_species >= 0) return false;
-    // the front kernel's plain path still applies held layers
-    const bool held_ok = is_ch(g.model);
+    // the 7-point Cahn-Hilliard kernel's plain path still applies held layers
+    const bool held_ok = is_ch(g.model) && stencil_of(g) == 7;
     for (int s = 0; s < g.nspecies; ++s) {
         for (int f = 0; f < 6; ++f)
             if (g.bc[s][f] == RD_BC_DIRICHLET && !held_ok) return false;
