@@ -511,6 +511,15 @@ def run_extras(args, Sim, Batch, torch):
         t = _timed_steps(torch, sim, 1000)
         out["ch_table1_192_19pt"] = _entry(W.cell_count(ccfg), 1000, t, 24, tun,
                                            launches_per_step=2, moved_bytes_per_cell_step=36)
+    # the plume of Table 1 (row 4) on its 144 x 144 x 384 grid with the
+    # 19-point stencil: upwind along three axes, u_z = 5 sin(t / 500 s) read
+    # from the device step counter (1 species, 8 B per cell-step)
+    pcfg = W.with_(W.plume(), stencil=19)
+    with Sim(pcfg) as sim:
+        sim.set_fields(W.initial_fields_torch(pcfg, "cuda"))
+        tun = sim.autotune()
+        t = _timed_steps(torch, sim, 2000)
+        out["plume_144x144x384_19pt"] = _entry(W.cell_count(pcfg), 2000, t, 8, tun)
     # the paper's own kernel designs on the same problem (ablation baselines:
     # Shared method and Moving Tiles, Section 4.1, Tables 4-5)
     for kern in ("shared", "tiles"):

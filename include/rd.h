@@ -99,7 +99,16 @@ typedef enum rd_wind {
     RD_WIND_NONE = 0,
     RD_WIND_LOG = 1,      /* u_x(z) = wind_u0 * ln(1+z) / ln(1+nz), z the
                              cell index 0..nz-1                              */
-    RD_WIND_CONST = 2     /* u_x = wind_u0 everywhere                       */
+    RD_WIND_CONST = 2,    /* u_x = wind_u0 everywhere                       */
+    RD_WIND_3D = 3        /* the plume wind of Table 1 (row 4): first-order
+                             upwind along all three axes with
+                             u = (wind_vel[0], wind_vel[1],
+                                  wind_vel[2] * sin(t / wind_tau)),
+                             t = n dt at the start of step n (every term of
+                             the explicit step is taken at level n); the
+                             step index is kept on the device per context,
+                             so captured launch sequences stay valid.  One
+                             step per launch (tsteps = 1); wind_tau > 0     */
 } rd_wind;
 
 enum {
@@ -117,7 +126,8 @@ enum {
  *                with D diagonal, per axis where a problem needs it
  *   bc, bc_value per species and face (-x,+x,-y,+y,-z,+z)
  *   params       model constants (see rd_model)
- *   wind_*       advection (see rd_wind); applies to every species
+ *   wind_*       advection (see rd_wind); applies to every species; the
+ *                time of RD_WIND_3D is rd_step_count() * dt
  *   src_*        point emission: species src_species gains src_rate per
  *                unit time at cell (src_x, src_y, src_z); src_species < 0
  *                means none
@@ -149,6 +159,8 @@ typedef struct rd_config {
     int32_t src_x, src_y, src_z, src_species;
     double src_rate;
     int32_t flags, reserved1;
+    double wind_vel[3];   /* RD_WIND_3D: velocity scales along x, y, z      */
+    double wind_tau;      /* RD_WIND_3D: time scale of u_z                  */
 } rd_config;
 
 typedef struct rd_ctx rd_ctx;

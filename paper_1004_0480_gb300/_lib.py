@@ -15,7 +15,7 @@ BC = {"neumann": 0, "periodic": 1, "dirichlet": 2}
 MODEL = {"diffusion": 0, "brusselator": 1, "ch_front": 2, "air": 3, "turing": 4,
          "ch_table1": 5}
 STORAGE = {"f32": 0, "bf16": 1}
-WIND = {None: 0, "log": 1, "const": 2}
+WIND = {None: 0, "log": 1, "const": 2, "3d": 3}
 KERNEL = {"march": 0, "shared": 1, "tiles": 2}
 FLAG_NO_ALLOC, FLAG_FORCE = 1, 2
 
@@ -34,6 +34,7 @@ class RdConfig(ctypes.Structure):
         ("src_x", ctypes.c_int32), ("src_y", ctypes.c_int32), ("src_z", ctypes.c_int32),
         ("src_species", ctypes.c_int32), ("src_rate", ctypes.c_double),
         ("flags", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("wind_vel", ctypes.c_double * 3), ("wind_tau", ctypes.c_double),
     ]
 
 

@@ -154,7 +154,7 @@ int kernels_per_step(const rd_config& g) { return (stencil_of(g) == 19 && is_ch(
 // temporal blocking: up to 3 steps per launch (2 with Cahn-Hilliard); the
 // 19-point kernel steps once per launch
 int max_tsteps(const rd_config& g) {
-    if (stencil_of(g) == 19) return 1;
+    if (stencil_of(g) == 19 || g.wind_kind == RD_WIND_3D) return 1;
     return is_ch(g.model) ? 2 : 3;
 }
 
@@ -203,6 +203,8 @@ struct rd_ctx {
     InstDesc* desc_dev = nullptr;  // this context's descriptor
     float* courant = nullptr;      // u(z) dt / h per plane
     float* mu = nullptr;           // 19-point Cahn-Hilliard: the mu field
+    long long* stepn = nullptr;    // 3-D wind: step index per time level
+    bool stepn_dirty = true;       // the host's step count is not on the device
     int cur = 0;                   // current time level
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -324,10 +326,17 @@ rd_status validate(const rd_config* c) {
                 return fail(nullptr, RD_EINVAL,
                             "the 19-point Laplacian takes one diffusivity per species");
     }
-    if (c->wind_kind < RD_WIND_NONE || c->wind_kind > RD_WIND_CONST)
+    if (c->wind_kind < RD_WIND_NONE || c->wind_kind > RD_WIND_3D)
         return fail(nullptr, RD_EINVAL, "unknown wind kind");
-    if (c->wind_kind != RD_WIND_NONE && !std::isfinite(c->wind_u0))
+    if (c->wind_kind != RD_WIND_NONE && c->wind_kind != RD_WIND_3D && !std::isfinite(c->wind_u0))
         return fail(nullptr, RD_EINVAL, "wind speed must be finite");
+    if (c->wind_kind == RD_WIND_3D) {
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(c->wind_vel[a]))
+                return fail(nullptr, RD_EINVAL, "wind speed must be finite");
+        if (!(c->wind_tau > 0) || !std::isfinite(c->wind_tau))
+            return fail(nullptr, RD_EINVAL, "wind_tau must be finite and > 0");
+    }
     if (c->src_species >= 0) {
         if (c->src_species >= c->nspecies || c->src_x < 0 || c->src_x >= c->nx || c->src_y < 0 ||
             c->src_y >= c->ny || c->src_z < 0 || c->src_z >= c->nz)
@@ -337,6 +346,10 @@ rd_status validate(const rd_config* c) {
         double umax = 0.0;
         if (c->wind_kind == RD_WIND_LOG) umax = std::fabs(c->wind_u0) * std::log1p((double)c->nz - 1) / std::log1p((double)c->nz);
         if (c->wind_kind == RD_WIND_CONST) umax = std::fabs(c->wind_u0);
+        // upwind along every axis: the centre coefficient loses dt |u_a| / h
+        // per axis
+        if (c->wind_kind == RD_WIND_3D)
+            umax = std::fabs(c->wind_vel[0]) + std::fabs(c->wind_vel[1]) + std::fabs(c->wind_vel[2]);
         // the centre coefficient of the update stays >= 0: it is
         // 1 - dt (w D / h^2 + |u| / h), w = 2 per axis (7-point) or
         // 24 / 6 = 4 (19-point)
@@ -394,7 +407,7 @@ void layout(rd_ctx* c) {
     const size_t res = 256;
     const size_t desc = align_up(sizeof(InstDesc), 256);
     const size_t cour = align_up((size_t)g.nz * sizeof(float), 256);
-    c->scratch_bytes = dense + part + res + desc + cour + mu_bytes(c);
+    c->scratch_bytes = dense + part + res + desc + cour + 256 + mu_bytes(c);
 }
 
 void carve(rd_ctx* c) {
@@ -410,6 +423,8 @@ void carve(rd_ctx* c) {
     p += align_up(sizeof(InstDesc), 256);
     c->courant = reinterpret_cast<float*>(p);
     p += align_up((size_t)g.nz * sizeof(float), 256);
+    c->stepn = g.wind_kind == RD_WIND_3D ? reinterpret_cast<long long*>(p) : nullptr;
+    p += 256;
     c->mu = mu_bytes(c) ? reinterpret_cast<float*>(p) : nullptr;
 }
 
@@ -548,6 +563,12 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
     }
     d.courant = g.wind_kind != RD_WIND_NONE ? c->courant : nullptr;
     d.mu = c->mu;
+    d.stepn = c->stepn;
+    if (g.wind_kind == RD_WIND_3D) {
+        d.cy = (float)(g.wind_vel[1] * g.dt / g.h);
+        d.wz_amp = g.wind_vel[2] * g.dt / g.h;
+        d.wz_omega = g.dt / g.wind_tau;
+    }
     d.src_s = g.src_species >= 0 ? g.src_species : -1;
     d.src_x = g.src_x; d.src_y = g.src_y; d.src_z = g.src_z;
     d.src_amt = (float)(g.src_rate * g.dt);
@@ -595,6 +616,7 @@ rd_status write_courant(rd_ctx* c) {
     for (int z = 0; z < g.nz; ++z) {
         double u = 0.0;
         if (g.wind_kind == RD_WIND_LOG) u = g.wind_u0 * std::log1p((double)z) / std::log1p((double)g.nz);
+        else if (g.wind_kind == RD_WIND_3D) u = g.wind_vel[0];
         else u = g.wind_u0;
         cz[z] = (float)(u * g.dt / g.h);
     }
@@ -605,6 +627,7 @@ rd_status write_courant(rd_ctx* c) {
 rd_status finish_setup(rd_ctx* c) {
     carve(c);
     RD_CUDA(c, cudaMemsetAsync(c->state, 0, c->state_bytes, c->stream));
+    if (c->stepn) RD_CUDA(c, cudaMemsetAsync(c->stepn, 0, 2 * sizeof(long long), c->stream));
     RD_CUDA(c, cudaStreamSynchronize(c->stream));
     rd_status st = write_courant(c);
     if (st != RD_OK) return st;
@@ -676,9 +699,22 @@ rd_status build_ctx_graph(rd_ctx* c) {
     return RD_OK;
 }
 
+// Put the host's step count on the device as the step index of the current
+// level (3-D wind), after creation or rd_set_step_count.  The copy is from
+// pageable memory, so the value is taken before the call returns.
+rd_status sync_stepn(rd_ctx* c, cudaStream_t st) {
+    if (!c->stepn || !c->stepn_dirty) return RD_OK;
+    const long long n = c->steps;
+    RD_CUDA(c, cudaMemcpyAsync(c->stepn + c->cur, &n, sizeof(n), cudaMemcpyHostToDevice, st));
+    RD_CUDA(c, cudaStreamSynchronize(st));
+    c->stepn_dirty = false;
+    return RD_OK;
+}
+
 rd_status step_ctx(rd_ctx* c, int64_t n) {
     rd_status st = upload_desc(c);
     if (st != RD_OK) return st;
+    if ((st = sync_stepn(c, c->stream)) != RD_OK) return st;
     const int T = c->tun.tsteps;
     int64_t full = n / T;
     const int rem = (int)(n % T);
@@ -952,6 +988,7 @@ int64_t rd_step_count(const rd_ctx* c) { return c ? c->steps : -1; }
 rd_status rd_set_step_count(rd_ctx* c, int64_t n) {
     if (!c) return RD_EINVAL;
     c->steps = n;
+    c->stepn_dirty = true;
     return RD_OK;
 }
 
@@ -1009,6 +1046,10 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
             if (best_out) *best_out = c->tun;
             return RD_OK;
         }
+    }
+    {
+        rd_status st = sync_stepn(c, c->stream);
+        if (st != RD_OK) return st;
     }
     const rd_tuning saved = c->tun;
     std::vector<rd_tuning> cands;
@@ -1300,6 +1341,8 @@ rd_status rd_batch_step(rd_batch* b, int64_t nsteps) {
     rd_status st = check_tuning(b->members[0]->cfg, t);
     if (st != RD_OK) return st;
     long long nitems = 0;
+    for (rd_ctx* c : b->members)
+        if ((st = sync_stepn(c, b->stream)) != RD_OK) return st;
     if ((st = batch_upload(b, t, &nitems)) != RD_OK) return st;
     const int T = t.tsteps;
     int64_t full = nsteps / T;

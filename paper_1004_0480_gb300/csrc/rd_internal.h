@@ -28,6 +28,14 @@ struct InstDesc {
     float dt;
     float p[8];                // model constants, see the model structs
     const float* courant;      // u_x(z) * dt / h per plane, or nullptr
+    // 3-D wind (Table 1, row 4): Courant number along y, and along z
+    // wz_amp * sin(n * wz_omega) at step n, computed in double precision;
+    // stepn[l] is the step index of the state held in time level l (the
+    // launch reading level l writes stepn[l ^ 1] = stepn[l] + 1); nullptr
+    // without a 3-D wind.  The x Courant number is the courant table.
+    long long* stepn;
+    double wz_amp, wz_omega;
+    float cy;
     float* mu;                 // 19-point Cahn-Hilliard models: the chemical
                                // potential of species 2 (float, the state's
                                // pitch and plane size), written by the first

@@ -265,6 +265,8 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
         for (int s = 0; s < S; ++s) k6[s] = __fdiv_rn(sd.kx[s], 6.0f);
         if constexpr (PASS == 1) k6[0] = __fdiv_rn(sd.p[2], 6.0f);
         if constexpr (PASS == 2) k6[2] = __fdiv_rn(sd.p[1], 6.0f);
+        float cy = 0.0f, cz = 0.0f;               // 3-D wind
+        if constexpr (!PLAIN && PASS == 0) wind3d(sd, lin, local, cy, cz);
         __syncthreads();   // halo descriptors written
 
         // ---- the march: plane nld is fetched P planes ahead into slot sl;
@@ -379,6 +381,21 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
                         M::react(sd, cv, iv);
 #pragma unroll
                         for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
+                    }
+                    if (!PLAIN && (cy != 0.0f || cz != 0.0f)) {
+                        // upwind along y and z (3-D wind): y neighbours from
+                        // plane q, z neighbours from the thread's own column
+                        // in planes q - 1 (still in the ring) and q + 1
+                        const unsigned char* Pm = ring + sm * SLOTB + own_b;
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+                            float ym[kVEC], yp[kVEC], zm[kVEC];
+                            lds_vec<ST>(Pc + s * PEB - kRW * EB, ym);
+                            lds_vec<ST>(Pc + s * PEB + kRW * EB, yp);
+                            lds_vec<ST>(Pm + s * PEB, zm);
+                            upwind_axis(cy, cen[s], ym, yp, inc[s]);
+                            upwind_axis(cz, cen[s], zm, c_p[s < NSUM ? s : 0], inc[s]);
+                        }
                     }
                     const float cx = (!PLAIN && courant) ? courant[zq] : 0.0f;
                     const bool src_here = src_col && zq == sd.src_z;

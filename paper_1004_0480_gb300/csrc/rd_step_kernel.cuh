@@ -398,6 +398,36 @@ __device__ __forceinline__ void held_layers_at(const InstDesc& sd, int s, unsign
     if (sd.held_mask[s] & faces) held_layers(sd, s, xs, y, q, o);
 }
 
+// First-order upwind along one axis with Courant number cu = u dt / h:
+// in -= cu (c - c[-1]) for cu > 0, cu (c[+1] - c) for cu < 0 (Section 4.1).
+__device__ __forceinline__ void upwind_axis(float cu, const float (&c)[kVEC],
+                                            const float (&cm)[kVEC], const float (&cp)[kVEC],
+                                            float (&in)[kVEC]) {
+    if (cu > 0.0f) {
+#pragma unroll
+        for (int e = 0; e < kVEC; ++e) in[e] = __fmaf_rn(-cu, __fsub_rn(c[e], cm[e]), in[e]);
+    } else if (cu < 0.0f) {
+#pragma unroll
+        for (int e = 0; e < kVEC; ++e) in[e] = __fmaf_rn(-cu, __fsub_rn(cp[e], c[e]), in[e]);
+    }
+}
+
+// Courant numbers along y and z of the 3-D wind for the launch reading time
+// level ``lin`` (zero without it): u_z = wz_amp sin(n wz_omega) at the step
+// index n of that level, evaluated in double precision.  The CTA taking an
+// instance's first work item also records n + 1 as the step index of the
+// level it writes (read by the next launch, never by this one).
+__device__ __forceinline__ void wind3d(const InstDesc& sd, int lin, long long local, float& cy,
+                                       float& cz) {
+    cy = 0.0f;
+    cz = 0.0f;
+    if (!sd.stepn) return;
+    const long long n = sd.stepn[lin];
+    cy = sd.cy;
+    cz = (float)(sd.wz_amp * sin((double)n * sd.wz_omega));
+    if (local == 0 && threadIdx.x == 0) sd.stepn[lin ^ 1] = n + 1;
+}
+
 // New value of one species on the thread's 4 cells (eq. (5)): reaction
 // increment ``inc`` (dt R), point source, upwind advection, Fickian
 // transport; held layers are applied by the caller.  Shared by every
@@ -407,7 +437,8 @@ __device__ __forceinline__ void species_core(const InstDesc& sd, int s, const fl
                                              const float (&ym)[kVEC], const float (&yp)[kVEC],
                                              const float (&zm)[kVEC], const float (&zp)[kVEC],
                                              const float (&inc)[kVEC], float cx, bool src_here,
-                                             bool px, int xs, float (&o)[kVEC]) {
+                                             bool px, int xs, float (&o)[kVEC], float cy = 0.0f,
+                                             float cz = 0.0f) {
     const float kx = sd.kx[s], ky = sd.ky[s], kz = sd.kz[s];
     const bool src_s = src_here && s == sd.src_s;
     const bool iso = kx == ky && kx == kz;
@@ -428,6 +459,9 @@ __device__ __forceinline__ void species_core(const InstDesc& sd, int s, const fl
 #pragma unroll
         for (int e = 0; e < kVEC; ++e) in[e] = __fmaf_rn(-cx, __fsub_rn(xp[e], c[e]), in[e]);
     }
+    // the same along y and z (the 3-D wind of Table 1, row 4)
+    upwind_axis(cy, c, ym, yp, in);
+    upwind_axis(cz, c, zm, zp, in);
     if (iso) {
 #pragma unroll
         for (int e = 0; e < kVEC; ++e)
@@ -867,6 +901,8 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                                    : make_fetch<ST>(y, xs, nx, ny, pitch, px, py, own_b / EB, true);
         int loff, roff;                           // x neighbours beside the own vector
         xface_offsets<ST>(xs, nx, px, loff, roff);
+        float cy = 0.0f, cz = 0.0f;               // 3-D wind
+        if constexpr (!PLAIN) wind3d(sd, lin, local, cy, cz);
         __syncthreads();   // halo descriptors written
 
         // ---- the march: plane nld is fetched P planes ahead into slot sl;
@@ -966,7 +1002,7 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                                                   zp[e], k, inc[s][e]);
                     } else {
                         species_core(sd, s, cen[s], xm, xp, ym, yp, zm, zp, inc[s], cx, src_here,
-                                     px, xs, o);
+                                     px, xs, o, cy, cz);
                         held_layers_at(sd, s, faces, xs, y, q, o);
                     }
                     if (computes) Store<ST>::store(gst + s * fstride, o);

@@ -43,8 +43,14 @@ def make_config(cfg, storage="f32", force=False, no_alloc=False) -> L.RdConfig:
     for i, name in enumerate(_PARAM_ORDER[cfg["model"]]):
         c.params[i] = cfg["params"][name]
     w = cfg.get("wind")
-    c.wind_kind = L.WIND[w["kind"] if w else None]
-    c.wind_u0 = w["u0"] if w else 0.0
+    # the problem dictionaries name the plume's wind of Table 1 "table1"
+    c.wind_kind = L.WIND[(("3d" if w["kind"] == "table1" else w["kind"]) if w else None)]
+    if w and w["kind"] == "table1":
+        # u = (ux, uy, uz_amp sin(t / uz_tau)), Table 1 row 4
+        c.wind_vel[0], c.wind_vel[1], c.wind_vel[2] = w["ux"], w["uy"], w["uz_amp"]
+        c.wind_tau = w["uz_tau"]
+    else:
+        c.wind_u0 = w["u0"] if w else 0.0
     src = cfg.get("source")
     if src:
         c.src_x, c.src_y, c.src_z = src["x"], src["y"], src["z"]

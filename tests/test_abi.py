@@ -43,10 +43,11 @@ def test_struct_layout_matches_c(tmp_path):
 #include <stddef.h>
 #include "rd.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rd_config), offsetof(rd_config, D),
-         offsetof(rd_config, bc), offsetof(rd_config, bc_value), offsetof(rd_config, params),
-         offsetof(rd_config, wind_u0), offsetof(rd_config, src_rate), sizeof(rd_tuning),
-         offsetof(rd_config, stencil));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rd_config),
+         offsetof(rd_config, D), offsetof(rd_config, bc), offsetof(rd_config, bc_value),
+         offsetof(rd_config, params), offsetof(rd_config, wind_u0), offsetof(rd_config, src_rate),
+         sizeof(rd_tuning), offsetof(rd_config, stencil), offsetof(rd_config, wind_vel),
+         offsetof(rd_config, wind_tau));
   return 0;
 }''')
     exe = tmp_path / "probe"
@@ -57,7 +58,8 @@ int main(void) {
     C = L.RdConfig
     assert vals == [ctypes.sizeof(C), C.D.offset, C.bc.offset, C.bc_value.offset,
                     C.params.offset, C.wind_u0.offset, C.src_rate.offset,
-                    ctypes.sizeof(L.RdTuning), C.stencil.offset]
+                    ctypes.sizeof(L.RdTuning), C.stencil.offset, C.wind_vel.offset,
+                    C.wind_tau.offset]
 
 
 def test_binding_constants_match_the_header_enums():

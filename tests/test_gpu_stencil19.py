@@ -165,12 +165,16 @@ def test_stencil19_tuning_rules(rd):
             sim.set_tuning(tile_y=5)          # whole halo warp: even heights
         with pytest.raises(Exception):
             sim.set_tuning(tile_y=32)         # at most 512 threads
+        # a batch takes 19-point members (of one stencil: a 7-point context
+        # cannot join them)
         b = rd.Batch("brusselator")
+        other = rd.Sim(W.brusselator(shape=(64, 16, 8)))
         try:
-            st = sim.lib.rd_batch_add(b.b, sim.ctx)
-            assert st == L.RD_EUNSUPPORTED
+            assert sim.lib.rd_batch_add(b.b, sim.ctx) == L.RD_OK
+            assert sim.lib.rd_batch_add(b.b, other.ctx) == L.RD_EINVAL
         finally:
             b.close()
+            other.close()
 
 
 def test_stencil19_autotune_and_full_size_step(rd, orc):
