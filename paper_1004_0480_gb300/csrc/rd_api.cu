@@ -160,6 +160,10 @@ int max_tsteps(const rd_config& g) {
 
 // CTAs per SM for a variant (cached).
 bool plain_problem(const rd_config& g);
+// kernel variant of a problem: 1 branch-free, 2 with the 3-D wind, else 0
+int variant_code(const rd_config& g) {
+    return plain_problem(g) ? 1 : g.wind_kind == RD_WIND_3D ? 2 : 0;
+}
 
 int occupancy(int model, int storage, int T, int ty, int regcap = 0, int plain = 0,
               int stencil = 7) {
@@ -173,7 +177,9 @@ int occupancy(int model, int storage, int T, int ty, int regcap = 0, int plain =
     LaunchArgs dummy{};
     dummy.use_one = 1;
     dummy.regcap = regcap;
-    dummy.plain = plain;
+    // plain: 0 the general variant, 1 the branch-free one, 2 the 3-D wind one
+    dummy.plain = plain == 1;
+    dummy.wind3 = plain == 2;
     dummy.ty = ty;
     const size_t smem = smem_of(model, storage, T, ty, stencil);
     if (launch_model(model, storage, T, dummy, 0, smem, nullptr, &occ, stencil) != cudaSuccess)
@@ -499,7 +505,7 @@ rd_tuning default_tuning(const rd_config& g) {
     t.tile_q = kTileQ;
     t.tile_y = default_tile_y(g.model);
     t.graph = 1;
-    const int occ = occupancy(g.model, g.storage, t.tsteps, t.tile_y, 0, plain_problem(g),
+    const int occ = occupancy(g.model, g.storage, t.tsteps, t.tile_y, 0, variant_code(g),
                               stencil_of(g));
     const long long cols = (long long)tiles(g.nx, t.tile_q * vec_of(g.storage)) * tiles(g.ny, t.tile_y);
     t.zchunk = wave_zchunk({{cols, g.nz}}, (long long)std::max(occ, 1) * num_sms());
@@ -646,6 +652,7 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     a.one = c->desc;
     a.regcap = c->tun.regcap;
     a.plain = plain_problem(c->cfg);
+    a.wind3 = c->cfg.wind_kind == RD_WIND_3D;
     a.ty = c->tun.tile_y;
     if (c->kernel != RD_KERNEL_MARCH) {   // the paper's designs, one step each
         if (T != 1) return fail(c, RD_EINVAL, "the ablation kernels step once per launch");
@@ -657,7 +664,8 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     const int sten = stencil_of(c->cfg);
     const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty, sten);
     const int occ = std::max(
-        1, occupancy(c->cfg.model, c->cfg.storage, T, a.ty, a.regcap, a.plain, sten));
+        1, occupancy(c->cfg.model, c->cfg.storage, T, a.ty, a.regcap,
+                     a.plain ? 1 : a.wind3 ? 2 : 0, sten));
     const long long grid = std::min<long long>(a.nitems, (long long)occ * num_sms());
     cudaError_t e =
         launch_model(c->cfg.model, c->cfg.storage, T, a, (int)grid, sm, st, nullptr, sten);
@@ -1063,7 +1071,7 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
             t.tsteps = T; t.tile_q = kTileQ; t.tile_y = ty; t.graph = 1; t.zchunk = 1;
             t.regcap = rc;
             if (check_tuning(g, t) != RD_OK) continue;
-            const int occ = occupancy(g.model, g.storage, T, ty, rc, plain_problem(g), sten);
+            const int occ = occupancy(g.model, g.storage, T, ty, rc, variant_code(g), sten);
             if (occ < 1) continue;
             // z-chunks for 1, 2, 4, 8 waves of CTAs; for one step per launch
             // also every split of z into 1..16 chunks, since how evenly the
@@ -1308,11 +1316,15 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
     a.nitems = nitems;
     a.regcap = t.regcap;
     a.plain = 1;
-    for (rd_ctx* m : b->members) a.plain = a.plain && plain_problem(m->cfg);
+    for (rd_ctx* m : b->members) {
+        a.plain = a.plain && plain_problem(m->cfg);
+        a.wind3 = a.wind3 || m->cfg.wind_kind == RD_WIND_3D;
+    }
     a.ty = t.tile_y;
     const size_t sm = smem_of(b->model, b->storage, T, a.ty, b->stencil);
     const int occ = std::max(
-        1, occupancy(b->model, b->storage, T, a.ty, a.regcap, a.plain, b->stencil));
+        1, occupancy(b->model, b->storage, T, a.ty, a.regcap, a.plain ? 1 : a.wind3 ? 2 : 0,
+                     b->stencil));
     const long long grid = std::min<long long>(nitems, (long long)occ * num_sms());
     cudaError_t e = launch_model(b->model, b->storage, T, a, (int)grid, sm, st, nullptr, b->stencil);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch step launch");

@@ -58,6 +58,8 @@ struct LaunchArgs {
     int regcap;                // one-step kernel: 1 = at most 64 registers
     int plain;                 // every instance has no held layer, source or
                                // wind, and isotropic diffusivities
+    int wind3;                 // some instance has the 3-D wind (kernels take
+                               // the variant with upwind along y and z)
     InstDesc one;              // the instance of a single-instance launch
 };
 

@@ -153,8 +153,9 @@ __device__ __forceinline__ void fetch_mu(const Fetch& f, unsigned char* mu0,
     }
 }
 
-// PLAIN: no held layer, point source or wind.  PASS: see Layout19.
-template <class M, class ST, bool ONE, bool PLAIN, int PASS>
+// PLAIN: no held layer, point source or wind.  PASS: see Layout19.  W3:
+// the 3-D wind (upwind along y and z too; never with PLAIN, PASS 0 only).
+template <class M, class ST, bool ONE, bool PLAIN, int PASS, bool W3 = false>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
     using LY = Layout19<M, ST, PASS>;
@@ -266,7 +267,7 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
         if constexpr (PASS == 1) k6[0] = __fdiv_rn(sd.p[2], 6.0f);
         if constexpr (PASS == 2) k6[2] = __fdiv_rn(sd.p[1], 6.0f);
         float cy = 0.0f, cz = 0.0f;               // 3-D wind
-        if constexpr (!PLAIN && PASS == 0) wind3d(sd, lin, local, cy, cz);
+        if constexpr (W3 && PASS == 0) wind3d(sd, lin, local, cy, cz);
         __syncthreads();   // halo descriptors written
 
         // ---- the march: plane nld is fetched P planes ahead into slot sl;
@@ -382,7 +383,7 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
 #pragma unroll
                         for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
                     }
-                    if (!PLAIN && (cy != 0.0f || cz != 0.0f)) {
+                    if (W3 && (cy != 0.0f || cz != 0.0f)) {
                         // upwind along y and z (3-D wind): y neighbours from
                         // plane q, z neighbours from the thread's own column
                         // in planes q - 1 (still in the ring) and q + 1
@@ -448,14 +449,17 @@ template <class M, class ST, int PASS>
 cudaError_t launch19_pass(const LaunchArgs& a, int grid, size_t smem, cudaStream_t st, int* occ) {
     if ((a.ty & 1) || a.ty < 2) return cudaErrorInvalidValue;
     void (*k)(const LaunchArgs);
+    const bool w3 = PASS == 0 && !a.plain && a.wind3;
     if (a.use_one)
         k = a.plain ? rd_step19_kernel<M, ST, true, true, PASS>
+            : w3    ? rd_step19_kernel<M, ST, true, false, PASS, PASS == 0>
                     : rd_step19_kernel<M, ST, true, false, PASS>;
     else
         k = a.plain ? rd_step19_kernel<M, ST, false, true, PASS>
+            : w3    ? rd_step19_kernel<M, ST, false, false, PASS, PASS == 0>
                     : rd_step19_kernel<M, ST, false, false, PASS>;
-    static size_t configured[4] = {0, 0, 0, 0};
-    size_t& conf = configured[(a.plain ? 1 : 0) + (a.use_one ? 2 : 0)];
+    static size_t configured[6] = {0, 0, 0, 0, 0, 0};
+    size_t& conf = configured[(a.plain ? 1 : w3 ? 2 : 0) + (a.use_one ? 3 : 0)];
     if (smem > conf) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

@@ -816,8 +816,9 @@ __device__ __forceinline__ float lds_one(const unsigned char* p) {
 // held cell's own update, which is replaced by its bc value, so this is
 // exact for every one-step problem.
 // PLAIN: no held layer, point source or wind, and every species isotropic;
-// the update then needs no per-plane or per-species branches.
-template <class M, class ST, bool ONE, int MINB, bool PLAIN>
+// the update then needs no per-plane or per-species branches.  W3: the
+// 3-D wind (upwind along y and z too; never with PLAIN).
+template <class M, class ST, bool ONE, int MINB, bool PLAIN, bool W3>
 __global__ void __launch_bounds__(kMaxThreads, MINB)
 rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
     using LY = Layout1<M, ST>;
@@ -902,7 +903,7 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
         int loff, roff;                           // x neighbours beside the own vector
         xface_offsets<ST>(xs, nx, px, loff, roff);
         float cy = 0.0f, cz = 0.0f;               // 3-D wind
-        if constexpr (!PLAIN) wind3d(sd, lin, local, cy, cz);
+        if constexpr (W3) wind3d(sd, lin, local, cy, cz);
         __syncthreads();   // halo descriptors written
 
         // ---- the march: plane nld is fetched P planes ahead into slot sl;
@@ -1369,19 +1370,23 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
     } else if (lean) {
         // register budget of the one-step kernel: 128 (regcap 0) or 64 (regcap 1)
         if (a.plain)
-            k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, true> : rd_step1_kernel<M, ST, ONE, 1, true>;
+            k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, true, false>
+                         : rd_step1_kernel<M, ST, ONE, 1, true, false>;
+        else if (a.wind3)
+            k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, false, true>
+                         : rd_step1_kernel<M, ST, ONE, 1, false, true>;
         else
-            k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, false>
-                         : rd_step1_kernel<M, ST, ONE, 1, false>;
+            k = a.regcap ? rd_step1_kernel<M, ST, ONE, 2, false, false>
+                         : rd_step1_kernel<M, ST, ONE, 1, false, false>;
     } else {
         k = rd_step_kernel<M, ST, T, ONE>;
     }
     // dynamic shared memory granted so far, per kernel variant (4: the
-    // multi-level kernel at T = 1)
-    static size_t configured[5] = {0, 0, 0, 0, 0};
-    const int variant = (T == 1 && !M::CH && !lean)
-                            ? 4
-                            : (lean && a.regcap ? 1 : 0) + ((lean || lean_ch) && a.plain ? 2 : 0);
+    // multi-level kernel at T = 1; 5, 6: the one-step kernel with 3-D wind)
+    static size_t configured[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int variant = (T == 1 && !M::CH && !lean) ? 4
+                        : (lean && !a.plain && a.wind3) ? 5 + (a.regcap ? 1 : 0)
+                        : (lean && a.regcap ? 1 : 0) + ((lean || lean_ch) && a.plain ? 2 : 0);
     size_t& conf = configured[variant];
     if (smem > conf) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
