@@ -387,6 +387,8 @@ def run_ours(args, ws, rank, local):
     extras = {}
     if rank == 0 and not args.no_extras:
         extras = run_extras(args, Sim, Batch, torch)
+        if args.bench_serve_requests > 0:
+            extras["serving"] = serving_extra(args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -598,22 +600,16 @@ def run_extras(args, Sim, Batch, torch):
     return out
 
 
-def run_serving(args):
-    """Serving workload: seeded Poisson stream of mixed requests, served by
-    continuous batching and by the plain one-request-at-a-time stepper."""
+def serving_setup(args, SV, count):
+    """The seeded request mix, every family warmed up once (first use of a
+    kernel and of the device field generator costs seconds of one-time
+    loading per process), and the plain stepper's capacity measured on the
+    first few requests of the mix (cell-steps per second, each request's
+    context creation and upload included)."""
     import torch
-
-    from paper_1004_0480_gb300 import build as B
-    B.build()
-    from paper_1004_0480_gb300 import serving as SV
-
-    torch.cuda.set_device(0)
-    specs = W.serving_requests(count=args.serve_requests, rate_per_s=1.0, seed=4)
+    specs = W.serving_requests(count=count, rate_per_s=1.0, seed=4)
     reqs = SV.requests_from_workload(specs)
     mean_work = float(np.mean([r.cells * r.steps for r in reqs]))
-    # warm up every family once (first use of each kernel and of the device
-    # field generator costs seconds of one-time loading per process), then
-    # calibrate the plain stepper's capacity on a few requests of the mix
     warm = [SV.Request(-1 - i, 0.0, mk(16, steps=4))
             for i, mk in enumerate((W.diffusion_blob, W.brusselator, W.ch_front))]
     eng = SV.CudaEngine()
@@ -630,11 +626,57 @@ def run_serving(args):
         eng.run_alone(r, False)
     torch.cuda.synchronize()
     cap = sum(r.cells * r.steps for r in probe) / (time.perf_counter() - t0)
-    base_reqs = reqs
-    rate = args.serve_load * cap / mean_work
-    reqs = SV.with_rate(reqs, rate, seed=4)
+    return reqs, cap, mean_work
+
+
+def serving_pack(st):
+    return {"p50_s": st.p50, "p99_s": st.p99, "mean_s": st.mean, "glups": st.glups,
+            "makespan_s": st.makespan, "max_active": st.max_active,
+            "max_running": st.max_running, "max_device_bytes": st.max_bytes,
+            "gpu_launches": st.launches}
+
+
+def serving_at_load(args, SV, reqs, cap, mean_work, load, progress=None):
+    """Both servers on the same Poisson stream at ``load`` x the plain
+    capacity: (continuous batching stats, plain stats, arrival rate)."""
+    rate = load * cap / mean_work
+    rr = SV.with_rate(reqs, rate, seed=4)
+    server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
+                       quantum=args.serve_quantum, run_cells=args.serve_run_cells,
+                       progress=progress)
+    _, st_b = server.run(rr)
+    server.engine.shutdown()
+    _, st_p = SV.serve_plain(SV.CudaEngine(), rr, progress=progress)
+    return st_b, st_p, rate
+
+
+def serving_extra(args):
+    """The reduced serving run of the default bench line: the first
+    ``--bench-serve-requests`` requests of the mix at ``--serve-load``."""
+    from paper_1004_0480_gb300 import serving as SV
+    reqs, cap, mean_work = serving_setup(args, SV, args.bench_serve_requests)
+    st_b, st_p, rate = serving_at_load(args, SV, reqs, cap, mean_work, args.serve_load)
+    return {"requests": len(reqs), "offered_load": args.serve_load,
+            "arrival_rate_per_s": rate, "plain_capacity_glups": cap / 1e9,
+            "continuous_batching": serving_pack(st_b), "plain": serving_pack(st_p),
+            "p99_speedup": st_p.p99 / st_b.p99 if st_b.p99 > 0 else None,
+            "p50_speedup": st_p.p50 / st_b.p50 if st_b.p50 > 0 else None}
+
+
+def run_serving(args):
+    """Serving workload: seeded Poisson stream of mixed requests, served by
+    continuous batching and by the plain one-request-at-a-time stepper."""
+    import torch
+
+    from paper_1004_0480_gb300 import build as B
+    B.build()
+    from paper_1004_0480_gb300 import serving as SV
+
+    torch.cuda.set_device(0)
+    reqs, cap, mean_work = serving_setup(args, SV, args.serve_requests)
     if args.serve_loads:
-        return serving_sweep(args, SV, base_reqs, cap, mean_work)
+        return serving_sweep(args, SV, reqs, cap, mean_work)
+    rate = args.serve_load * cap / mean_work
     if args.serve_progress:
         print(f"serve plain capacity {cap / 1e9:.1f} GLUPS, arrival rate {rate:.3f}/s",
               file=sys.stderr, flush=True)
@@ -646,26 +688,17 @@ def run_serving(args):
             last[0] = t
             print(f"serve t={t:.1f}s admitted={n_adm} running={n_run} done={n_done}",
                   file=sys.stderr, flush=True)
-    server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
-                       quantum=args.serve_quantum, run_cells=args.serve_run_cells,
-                       progress=progress)
-    res_b, st_b = server.run(reqs)
-    server.engine.shutdown()
-    res_p, st_p = SV.serve_plain(SV.CudaEngine(), reqs, progress=progress)
+    st_b, st_p, rate = serving_at_load(args, SV, reqs, cap, mean_work, args.serve_load,
+                                       progress)
+    rr = SV.with_rate(reqs, rate, seed=4)
     # capacity: the first requests of the stream all arriving at once
-    sat = [SV.Request(r.id, 0.0, r.cfg) for r in reqs[: args.serve_sat_requests]]
+    sat = [SV.Request(r.id, 0.0, r.cfg) for r in rr[: args.serve_sat_requests]]
     server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
                        quantum=args.serve_quantum, run_cells=args.serve_run_cells,
                        progress=progress)
     _, sat_b = server.run(sat)
     server.engine.shutdown()
     _, sat_p = SV.serve_plain(SV.CudaEngine(), sat, progress=progress)
-
-    def pack(st):
-        return {"p50_s": st.p50, "p99_s": st.p99, "mean_s": st.mean, "glups": st.glups,
-                "makespan_s": st.makespan, "max_active": st.max_active,
-                "max_running": st.max_running,
-                "max_device_bytes": st.max_bytes, "gpu_launches": st.launches}
     line = {
         "metric": "serving latency p50/p99 (s) and aggregate GLUPS", "unit": "s",
         "requests": len(reqs), "arrival_rate_per_s": rate, "offered_load": args.serve_load,
@@ -674,10 +707,10 @@ def run_serving(args):
         "data": "synthetic",
         "config": {"workload": "serving: Poisson arrivals, diffusion/brusselator/ch_front "
                                "kinetics, edges {32..384}^3, 100..5000 steps", "seed": 4},
-        "continuous_batching": pack(st_b), "plain": pack(st_p),
+        "continuous_batching": serving_pack(st_b), "plain": serving_pack(st_p),
         "p99_speedup": st_p.p99 / st_b.p99 if st_b.p99 > 0 else None,
-        "saturated": {"requests": len(sat), "continuous_batching": pack(sat_b),
-                      "plain": pack(sat_p),
+        "saturated": {"requests": len(sat), "continuous_batching": serving_pack(sat_b),
+                      "plain": serving_pack(sat_p),
                       "glups_speedup": sat_b.glups / sat_p.glups if sat_p.glups > 0 else None},
     }
     print(json.dumps(line), flush=True)
@@ -689,13 +722,7 @@ def serving_sweep(args, SV, reqs, cap, mean_work):
     plain stepper's measured capacity); one JSON line."""
     rows = []
     for load in (float(x) for x in args.serve_loads.split(",")):
-        rate = load * cap / mean_work
-        rr = SV.with_rate(reqs, rate, seed=4)
-        server = SV.Server(SV.CudaEngine(), budget_bytes=args.serve_budget_gb * 1e9,
-                           quantum=args.serve_quantum, run_cells=args.serve_run_cells)
-        _, st_b = server.run(rr)
-        server.engine.shutdown()
-        _, st_p = SV.serve_plain(SV.CudaEngine(), rr)
+        st_b, st_p, rate = serving_at_load(args, SV, reqs, cap, mean_work, load)
         rows.append({"offered_load": load, "arrival_rate_per_s": rate,
                      "continuous_batching": {"p50_s": st_b.p50, "p99_s": st_b.p99,
                                              "mean_s": st_b.mean, "glups": st_b.glups},
@@ -742,6 +769,9 @@ def main():
                     help="cells the running requests hold together (inf: all admitted run)")
     ap.add_argument("--serve-sat-requests", type=int, default=100,
                     help="requests of the saturated (all arrive at once) capacity run")
+    ap.add_argument("--bench-serve-requests", type=int, default=100,
+                    help="requests of the reduced serving run in the default line's "
+                         "extras (0: none)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.serve:

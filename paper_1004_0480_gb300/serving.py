@@ -129,6 +129,7 @@ class CudaEngine:
         self.batches = {}
         self.streams = {}
         self.on_high = {}
+        self.events = {}
         self.running = set()
 
     def bytes_for(self, req):
@@ -164,19 +165,39 @@ class CudaEngine:
         self.batches[family].add(handle)
         self.running.add(id(handle))
 
-    def prioritize(self, family):
-        """The next tick of ``family`` runs on its high-priority stream and
-        every other family's on its normal one: where kernels of several
-        families compete for SMs, the one holding the oldest running request
-        is scheduled first.  Called between ticks (streams are idle)."""
-        for fam, b in self.batches.items():
-            want = fam == family
-            if self.on_high[fam] != want:
-                b.set_stream(self.streams[fam][1 if want else 0])
-                self.on_high[fam] = want
+    def _stream_for(self, family, high):
+        """Put ``family``'s batch on its high- or normal-priority stream.  Only
+        called while the family is idle, so the switch waits for nothing."""
+        if self.on_high[family] != high:
+            self.batches[family].set_stream(self.streams[family][1 if high else 0])
+            self.on_high[family] = high
 
-    def step(self, family, n):
+    def step(self, family, n, high=False):
+        """Enqueue n steps of the family's batch and record an event after
+        them; returns at once.  ``high``: on the family's high-priority
+        stream (the family holding the oldest running request), so where
+        families compete for SMs its kernels are scheduled first."""
+        self._stream_for(family, high)
         self.batches[family].step(n)
+        ev = self._torch.cuda.Event()
+        ev.record(self.streams[family][1 if high else 0])
+        self.events[family] = ev
+
+    def busy(self, family):
+        """True while the family's last enqueued steps have not completed
+        (cudaEventQuery: no synchronisation)."""
+        ev = self.events.get(family)
+        return ev is not None and not ev.query()
+
+    def wait_any(self, families, timeout_s):
+        """Return when one of ``families`` is idle or after timeout_s."""
+        deadline = time.perf_counter() + max(timeout_s, 0.0)
+        while True:
+            if any(not self.busy(f) for f in families):
+                return
+            if time.perf_counter() >= deadline:
+                return
+            time.sleep(5e-5)
 
     def sync(self, family=None):
         fams = [family] if family else list(self.batches)
@@ -216,7 +237,14 @@ class CudaEngine:
 class Server:
     """Continuous batching under a device-memory budget.
 
-    ``quantum``    steps per tick for a family batch (a tick never steps a
+    Each kinetics family's running requests form one batch on its own
+    stream, and the families run asynchronously: whenever a family's last
+    chunk has completed (its event, polled without synchronising the
+    device), the server retires that family's finished requests, lets the
+    next admitted requests join it, and enqueues its next chunk, while the
+    other families keep running.  Arrivals are admitted between polls.
+
+    ``quantum``    steps per chunk of a family batch (a chunk never steps a
                    request past its count: the batch advances by the smallest
                    remaining count if that is smaller)
     ``budget``     bytes of device memory the admitted requests may hold
@@ -228,7 +256,7 @@ class Server:
     """
 
     def __init__(self, engine, budget_bytes=120e9, quantum=200, run_cells=48e6,
-                 clock=time.perf_counter, sleep=time.sleep, progress=None):
+                 clock=time.perf_counter, sleep=time.sleep, progress=None, poll_s=0.02):
         self.progress = progress     # called as progress(t, admitted, running, done)
         self.engine = engine
         self.budget = float(budget_bytes)
@@ -236,6 +264,7 @@ class Server:
         self.run_cells = float(run_cells)
         self.clock = clock
         self.sleep = sleep
+        self.poll_s = float(poll_s)  # longest wait before new arrivals are looked at
 
     def run(self, requests, collect_fields=False):
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.id)))
@@ -264,49 +293,72 @@ class Server:
                 admitted.append(dict(req=req, handle=handle, left=req.steps, bytes=need,
                                      admitted=self.clock() - t0, running=False))
             max_active = max(max_active, len(admitted))
+            # ---- which families are idle: one snapshot per pass, so a family
+            # that completes during the pass is not relaunched before its
+            # finished requests have left the batch
+            idle = {}
+            for s in admitted:
+                f = s["req"].family
+                if f not in idle:
+                    idle[f] = not self.engine.busy(f)
+            # ---- retire the finished requests of idle families
+            done_at = self.clock() - t0
+            for s in [s for s in admitted if s["running"] and s["left"] == 0
+                      and idle[s["req"].family]]:
+                req = s["req"]
+                fields = self.engine.result(s["handle"]) if collect_fields else None
+                results.append(Result(req.id, req.arrival, s["admitted"], done_at, req.steps,
+                                      req.cells, fields))
+                self.engine.close(req.family, s["handle"])
+                used -= s["bytes"]
+                admitted.remove(s)
             if not admitted:
                 if pending:
                     wait = pending[0].arrival - (self.clock() - t0)
                     if wait > 0:
                         self.sleep(wait)
                 continue
-            # ---- the running set: the oldest admitted requests up to run_cells
+            # ---- the running set: the oldest admitted requests up to
+            # run_cells; a request joins its family when the family is idle
             cells = 0
             for s in admitted:
                 if cells >= self.run_cells:
                     break
                 if not s["running"]:
+                    if not idle[s["req"].family]:
+                        cells += s["req"].cells
+                        continue
                     self.engine.start(s["req"].family, s["handle"])
                     s["running"] = True
                 cells += s["req"].cells
             running = [s for s in admitted if s["running"]]
             max_running = max(max_running, len(running))
-            # the oldest running request's family is scheduled first
-            if hasattr(self.engine, "prioritize"):
-                self.engine.prioritize(running[0]["req"].family)
-            # ---- one tick: every family's running batch advances (asynchronously)
+            # ---- every idle family with unfinished running requests gets its
+            # next chunk; the family of the oldest running request goes on its
+            # high-priority stream
             by_family = collections.OrderedDict()
             for s in running:
-                by_family.setdefault(s["req"].family, []).append(s)
+                if s["left"] > 0:
+                    by_family.setdefault(s["req"].family, []).append(s)
+            oldest = running[0]["req"].family if running else None
             for fam, slots in by_family.items():
+                if not idle[fam]:
+                    continue
                 n = min(self.quantum, min(s["left"] for s in slots))
-                self.engine.step(fam, n)
+                self.engine.step(fam, n, high=(fam == oldest))
                 for s in slots:
                     s["left"] -= n
-            # ---- end of tick: wait for the device (the host admits the next
-            # arrivals between ticks), then retire what is done
-            self.engine.sync()
-            finished = self.clock() - t0
             if self.progress:
-                self.progress(finished, len(admitted), len(running), len(results))
-            for s in [s for s in running if s["left"] == 0]:
-                req = s["req"]
-                fields = self.engine.result(s["handle"]) if collect_fields else None
-                results.append(Result(req.id, req.arrival, s["admitted"], finished, req.steps,
-                                      req.cells, fields))
-                self.engine.close(req.family, s["handle"])
-                used -= s["bytes"]
-                admitted.remove(s)
+                self.progress(self.clock() - t0, len(admitted), len(running), len(results))
+            # ---- wait for a family to go idle (or the next arrival)
+            fams = {s["req"].family for s in running}
+            busy = [f for f in fams if self.engine.busy(f)]
+            if busy and len(busy) == len(fams):
+                timeout = self.poll_s
+                ahead = pending[0].arrival - (self.clock() - t0) if pending else 0.0
+                if ahead > 0:            # wake up for an arrival still to come
+                    timeout = min(timeout, ahead)
+                self.engine.wait_any(busy, timeout)
         self.engine.sync()
         makespan = self.clock() - t0
         launches = self.engine.launches()

@@ -19,14 +19,15 @@ class FakeClock:
 
 
 class FakeEngine:
-    """Steps cost cells * steps / rate seconds; families run concurrently
-    (a tick costs the slowest family's work)."""
+    """Steps cost cells * steps / rate seconds; families run concurrently and
+    independently: a family's chunk completes at its own time on the fake
+    clock."""
 
     def __init__(self, clock, rate=1e6):
         self.clock, self.rate = clock, rate
         self.members = {}        # family -> running requests
         self.step_log = []       # (family, n, ids of the running requests)
-        self.pending = {}
+        self.done_at = {}        # family -> fake time its last chunk completes
         self.used = 0
         self.peak = 0
         self.budget_seen = []
@@ -47,18 +48,25 @@ class FakeEngine:
     def start(self, fam, handle):
         self.members.setdefault(fam, []).append(handle)
 
-    def step(self, fam, n):
+    def step(self, fam, n, high=False):
+        assert not self.busy(fam), "a family is stepped only when idle"
         self.step_log.append((fam, n, sorted(r.id for r in self.members[fam])))
         work = sum(r.cells for r in self.members[fam]) * n
-        self.pending[fam] = self.pending.get(fam, 0.0) + work / self.rate
+        self.done_at[fam] = self.clock.t + work / self.rate
         for r in self.members[fam]:
             self.steps_done[r.id] += n
         self.nlaunch += n
 
+    def busy(self, fam):
+        return self.clock.t < self.done_at.get(fam, float("-inf"))
+
+    def wait_any(self, fams, timeout):
+        nxt = min(self.done_at[f] for f in fams)
+        self.clock.t = max(self.clock.t, min(nxt, self.clock.t + max(timeout, 0.0)))
+
     def sync(self, fam=None):
-        if self.pending:
-            self.clock.t += max(self.pending.values())
-            self.pending.clear()
+        if self.done_at:
+            self.clock.t = max(self.clock.t, max(self.done_at.values()))
 
     def result(self, handle):
         return None
@@ -172,3 +180,30 @@ def test_percentiles():
     assert percentile(list(range(101)), 99) == pytest.approx(99.0)
     st = summarize([], 1.0, 0, 0)
     assert st.n == 0
+
+
+def test_families_run_independently():
+    # a large diffusion request runs long chunks; small Brusselator requests
+    # arriving meanwhile finish long before it, without waiting for its
+    # chunks to end
+    clk = FakeClock()
+    eng = FakeEngine(clk)
+    big = mk(0, 0.0, 60, 400, "diffusion")          # 216 000 cells x 400 steps
+    small = [mk(i, 0.01 * i, 8, 20) for i in range(1, 5)]
+    res, st = Server(eng, budget_bytes=1e12, quantum=200, clock=clk, sleep=clk.sleep,
+                     poll_s=0.005).run([big] + small)
+    lat = {r.id: r.latency for r in res}
+    chunk = 216000 * 200 / eng.rate                   # one chunk of the big request
+    assert all(lat[i] < 0.2 * chunk for i in range(1, 5))
+    assert lat[0] >= 2 * chunk
+    assert all(eng.steps_done[r.id] == r.steps for r in [big] + small)
+
+
+def test_a_finished_request_never_takes_more_steps():
+    # members of one family with different step counts: each stops exactly
+    # at its count although the family keeps running
+    clk = FakeClock()
+    eng = FakeEngine(clk)
+    reqs = [mk(i, 0.0, 10, 7 + 11 * i) for i in range(5)]
+    Server(eng, budget_bytes=1e12, quantum=9, clock=clk, sleep=clk.sleep).run(reqs)
+    assert all(eng.steps_done[r.id] == r.steps for r in reqs)
