@@ -45,7 +45,9 @@ typedef enum rd_status {
     RD_ENONFINITE = 5,    /* a reduction found NaN/Inf in the state         */
     RD_ETIMEOUT = 6,      /* rd_wait gave up before the stream finished     */
     RD_EBUDGET = 7,       /* a batch or server memory budget was exceeded   */
-    RD_EUNSUPPORTED = 8   /* valid request this build does not implement    */
+    RD_EUNSUPPORTED = 8,  /* valid request this build does not implement    */
+    RD_EBOUNDS = 9        /* bounds-checked debug build: a kernel met an
+                             out-of-range index (see rd_debug_bounds)       */
 } rd_status;
 
 /* Boundary rule of one face of one species (faces -x,+x,-y,+y,-z,+z). */
@@ -310,6 +312,32 @@ int64_t rd_launch_count(const rd_ctx* ctx);
 /* Text of a status code, and of the last error seen by a context. */
 const char* rd_status_str(rd_status st);
 const char* rd_last_error(const rd_ctx* ctx);
+
+/* The bounds-checked debug build (the paper has no counterpart; a stand-in
+ * for a memory checker).  That variant of this library checks every
+ * shared-memory access the step kernels make through their load, store and
+ * copy helpers against the launch's dynamic shared memory, and every global
+ * access against the instance's state and scratch allocations; an access
+ * out of range is skipped (a load yields 0), never made, and the first one
+ * is recorded in a device word: bit 63 set, bits 40..55 a site code (1
+ * shared load, 2 shared store, 3 copy destination, 4 copy source, 5 state
+ * store, 6 Courant table or step counter, 7 mu field, 8 halo descriptors,
+ * 0xFFFF the self-test), bits 0..39 the byte offset from the start of the
+ * window missed.  rd_sync and rd_batch_sync then return RD_EBOUNDS (and
+ * clear the word), with the site and offset in rd_last_error.
+ *   op 0: *word = the word; 1: the same, then clear it; 2: launch a
+ *   self-test kernel that records a violation at site 0xFFFF without
+ *   touching memory, then as 1.
+ * The normal build returns RD_EUNSUPPORTED. */
+rd_status rd_debug_bounds(uint64_t* word, int32_t op);
+
+/* Testing hook for the failure paths (the paper has no counterpart): with
+ * k > 0, the k-th device or pinned-host allocation this library makes from
+ * now on (rd_create's state and scratch, a batch's descriptor arrays) fails
+ * as if memory were exhausted, and the hook disarms; k = 0 disarms it.
+ * The call that meets the failure returns RD_ENOMEM and frees what it had
+ * obtained.  RD_EINVAL for k < 0. */
+rd_status rd_debug_fail_alloc(int64_t k);
 
 /* FP64 moments of one field held anywhere in device memory, for callers
  * that must not allocate device memory at that point: code that is

@@ -10,7 +10,7 @@ from . import build as _build
 MAX_S = 4
 
 RD_OK, RD_EINVAL, RD_ENOMEM, RD_ECUDA, RD_EUNSTABLE, RD_ENONFINITE, RD_ETIMEOUT, \
-    RD_EBUDGET, RD_EUNSUPPORTED = range(9)
+    RD_EBUDGET, RD_EUNSUPPORTED, RD_EBOUNDS = range(10)
 BC = {"neumann": 0, "periodic": 1, "dirichlet": 2}
 MODEL = {"diffusion": 0, "brusselator": 1, "ch_front": 2, "air": 3, "turing": 4,
          "ch_table1": 5}
@@ -93,12 +93,18 @@ SIGNATURES = {
     "rd_batch_destroy": (_I, [_P]),
     "rd_batch_launch_count": (_I64, [_P]),
     "rd_moments_noalloc": (_I, [_P, _I32, _I32, _I32, _I32, _I64, _P, _P]),
+    "rd_debug_fail_alloc": (_I, [_I64]),
+    "rd_debug_bounds": (_I, [ctypes.POINTER(ctypes.c_uint64), _I32]),
 }
 
 _lib = None
 
 
 def lib_path() -> str:
+    """The library to load: the bounds-checked debug variant when the
+    environment variable RD_BOUNDS_CHECK is 1, else the normal one."""
+    if os.environ.get("RD_BOUNDS_CHECK") == "1":
+        return _build.LIB_DEBUG
     return _build.LIB
 
 

@@ -6,21 +6,25 @@
 // coordinates through the face rules instead, which composes them at edges
 // exactly as the 19-point march does).
 //
-// Shared method (Table 4, Figure 3): a 3-D block of BW x BH x BD threads,
-// one cell each, over an x-y tile that overlaps its neighbours by one cell
-// on every side; the threads on the tile's rim only load.  The block walks
-// up z holding BD planes in shared memory: it updates the BD - 2 inner
-// planes, keeps the top two as the next bottom two and loads BD - 2 new
-// ones.  Every load is a plain coalesced global load (a warp is one
-// 32-cell row).
+// Shared method (Section 4.1, Figure 3): a 3-D block of BW x BH x BD
+// threads, one cell each, over an x-y tile that overlaps its neighbours by
+// one cell on every side; the threads on the tile's rim only load.  The
+// block walks up z keeping a window of planes in shared memory, so each
+// plane is read from global memory once per tile.  Here the window is a
+// ring of BD + 2 plane slots indexed by the plane number: every thread
+// layer updates one plane per iteration (BD planes), then loads one new
+// plane into the slot of a plane no longer needed.  Every load is a plain
+// coalesced global load (a warp is one 32-cell row).
 //
-// Moving Tiles (Table 5, Figure 4): a block of BW x BH x BD threads over a
-// y-z tile (overlapping by one row and plane), walking along x in windows
-// of BW cells: shared memory holds, per row, the cell left of the current
-// window, the window and the next window (2 BW + 1 cells); each step
-// updates the window, slides the next window into its place and loads the
-// one after.  The paper's BW = 16 matched the half-warp coalescing rules of
-// its first-generation GPUs; here BW = 32, one warp per row.
+// Moving Tiles (Section 4.1, Figure 4): a block of BW x BH x BD threads
+// over a y-z tile (overlapping by one row and plane) that walks along x in
+// windows of BW cells.  Here each row keeps a ring of three windows
+// indexed by the window number (the one before, the current one, the next
+// one): the current window is updated with its x neighbours taken across
+// the slot boundaries, then the window after the next one is loaded into
+// the slot of the window before.  The paper's 16-cell window matched the
+// half-warp coalescing rules of its first-generation GPUs; here BW = 32,
+// one warp per row.
 #include "rd_ablation.h"
 #include "rd_model_turing.h"
 #include "rd_step_kernel.cuh"
@@ -28,7 +32,8 @@
 namespace rdk {
 namespace {
 
-constexpr int kShW = 32, kShH = 8, kShD = 4;   // Shared: 30 x 6 x 2 updates per iteration
+constexpr int kShW = 32, kShH = 8, kShD = 4;   // Shared: 30 x 6 x 4 updates per iteration
+constexpr int kShR = kShD + 2;                  // plane slots in the ring
 constexpr int kMtW = 32, kMtH = 8, kMtD = 4;   // Moving Tiles: 32 x 6 x 2 per window
 
 // Coordinate i mapped into [0, n) by an axis's rule: wrapped when periodic,
@@ -67,7 +72,7 @@ template <class M>
 __global__ void __launch_bounds__(kShW * kShH * kShD)
 rd_shared19_kernel(const __grid_constant__ LaunchArgs a) {
     constexpr int S = M::S;
-    __shared__ float cs[S][kShD][kShH][kShW];
+    __shared__ float cs[S][kShR][kShH][kShW];
     const InstDesc& sd = a.one;
     const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
     const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
@@ -79,40 +84,40 @@ rd_shared19_kernel(const __grid_constant__ LaunchArgs a) {
     float* const gout = reinterpret_cast<float*>(sd.base[lin ^ 1][0]);
     const long long fstride = S > 1 ? reinterpret_cast<const float*>(sd.base[lin][1]) - gin : 0;
     const long long plane = sd.plane;
-    // rim threads load only; x, y >= 0 for all others
-    const bool computes = tx > 0 && tx < kShW - 1 && ty > 0 && ty < kShH - 1 && x < nx && y < ny;
+    // the rim loads only; x, y >= 0 elsewhere
+    const bool inner = tx > 0 && tx < kShW - 1 && ty > 0 && ty < kShH - 1 && x < nx && y < ny;
     float k6[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) k6[s] = __fdiv_rn(sd.kx[s], 6.0f);
+    // plane z lives in slot (z + 1) mod kShR (z >= -1)
+    auto slot = [](int z) { return (z + 1) % kShR; };
     auto load = [&](int z) {
         const long long off = (long long)face_rule(z, nz, sd.per_z) * plane + row;
+        const int sl = slot(z);
 #pragma unroll
-        for (int s = 0; s < S; ++s) cs[s][tz][ty][tx] = gin[s * fstride + off];
+        for (int s = 0; s < S; ++s) cs[s][sl][ty][tx] = gin[s * fstride + off];
     };
-    int zb = -1;                       // the plane held by tz = 0
-    load(zb + tz);
-    for (;;) {
+    // planes -1 .. kShD fill the ring
+    for (int z = tz - 1; z <= kShD; z += kShD) load(z);
+    for (int zb = 0; zb < nz; zb += kShD) {
         __syncthreads();
-        const int z = zb + tz;         // tz = 1 .. kShD-2 update planes zb+1 .. zb+kShD-2
-        if (computes && tz > 0 && tz < kShD - 1 && z < nz) {
+        const int z = zb + tz;                 // the plane this layer updates
+        if (inner && z < nz) {
+            const int sm = slot(z - 1), s0 = slot(z), sp = slot(z + 1);
             float o[S];
             update19<M>(sd, k6,
                         [&](int s, int dx, int dy, int dz) {
-                            return cs[s][tz + dz][ty + dy][tx + dx];
+                            const int sl = dz < 0 ? sm : (dz > 0 ? sp : s0);
+                            return cs[s][sl][ty + dy][tx + dx];
                         },
                         o);
 #pragma unroll
-            for (int s = 0; s < S; ++s) gout[s * fstride + z * plane + (long long)y * sd.pitch + x] = o[s];
-        }
-        if (zb + kShD - 1 >= nz) break;   // planes up to nz - 1 are done
-        __syncthreads();
-        if (tz >= kShD - 2) {
-#pragma unroll
-            for (int s = 0; s < S; ++s) cs[s][tz - (kShD - 2)][ty][tx] = cs[s][tz][ty][tx];
+            for (int s = 0; s < S; ++s)
+                gout[s * fstride + z * plane + (long long)y * sd.pitch + x] = o[s];
         }
         __syncthreads();
-        zb += kShD - 2;
-        if (tz >= 2) load(zb + tz);
+        // planes zb + kShD + 1 .. zb + 2 kShD replace zb - 1 .. zb + kShD - 2
+        if (zb + kShD < nz) load(zb + kShD + 1 + tz);
     }
 }
 
@@ -120,8 +125,7 @@ template <class M>
 __global__ void __launch_bounds__(kMtW * kMtH * kMtD)
 rd_tiles19_kernel(const __grid_constant__ LaunchArgs a) {
     constexpr int S = M::S;
-    constexpr int W2 = 2 * kMtW + 1;
-    __shared__ float cs[S][kMtD][kMtH][W2];
+    __shared__ float cs[S][kMtD][kMtH][3][kMtW];
     const InstDesc& sd = a.one;
     const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
     const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
@@ -133,44 +137,43 @@ rd_tiles19_kernel(const __grid_constant__ LaunchArgs a) {
     const long long fstride = S > 1 ? reinterpret_cast<const float*>(sd.base[lin][1]) - gin : 0;
     const long long rowbase = (long long)face_rule(z, nz, sd.per_z) * sd.plane +
                               (long long)face_rule(y, ny, sd.per_y) * sd.pitch;
-    const bool computes = ty > 0 && ty < kMtH - 1 && tz > 0 && tz < kMtD - 1 && y < ny && z < nz;
+    const bool inner = ty > 0 && ty < kMtH - 1 && tz > 0 && tz < kMtD - 1 && y < ny && z < nz;
     const bool px = sd.per_x;
     float k6[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) k6[s] = __fdiv_rn(sd.kx[s], 6.0f);
-    auto ld = [&](int s, int x) { return gin[s * fstride + rowbase + face_rule(x, nx, px)]; };
-    // element 0: the cell left of the window; 1..kMtW: the window; then the next window
+    // window w (cells w kMtW .. w kMtW + kMtW - 1) lives in slot (w + 1) mod 3
+    auto load = [&](int w) {
+        const int sl = (w + 1) % 3;
+        const int xx = face_rule(w * kMtW + tx, nx, px);
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        cs[s][tz][ty][tx + 1] = ld(s, tx);
-        cs[s][tz][ty][kMtW + tx + 1] = ld(s, kMtW + tx);
-        if (tx == 0) cs[s][tz][ty][0] = ld(s, -1);
-    }
+        for (int s = 0; s < S; ++s) cs[s][tz][ty][sl][tx] = gin[s * fstride + rowbase + xx];
+    };
+    load(-1);
+    load(0);
+    load(1);
     const int nwin = (nx + kMtW - 1) / kMtW;
-    for (int k = 0; k < nwin; ++k) {
+    for (int w = 0; w < nwin; ++w) {
         __syncthreads();
-        const int x = k * kMtW + tx;
-        if (computes && x < nx) {
+        const int x = w * kMtW + tx;
+        if (inner && x < nx) {
+            const int sm = w % 3, s0 = (w + 1) % 3, sp = (w + 2) % 3;
             float o[S];
             update19<M>(sd, k6,
                         [&](int s, int dx, int dy, int dz) {
-                            return cs[s][tz + dz][ty + dy][tx + 1 + dx];
+                            // x neighbours across the window boundaries
+                            const int xi = tx + dx;
+                            const int sl = xi < 0 ? sm : (xi >= kMtW ? sp : s0);
+                            const int xe = xi < 0 ? xi + kMtW : (xi >= kMtW ? xi - kMtW : xi);
+                            return cs[s][tz + dz][ty + dy][sl][xe];
                         },
                         o);
 #pragma unroll
             for (int s = 0; s < S; ++s)
                 gout[s * fstride + (long long)z * sd.plane + (long long)y * sd.pitch + x] = o[s];
         }
-        if (k + 1 == nwin) break;
         __syncthreads();
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            if (tx == kMtW - 1) cs[s][tz][ty][0] = cs[s][tz][ty][kMtW];
-            cs[s][tz][ty][tx + 1] = cs[s][tz][ty][kMtW + tx + 1];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int s = 0; s < S; ++s) cs[s][tz][ty][kMtW + tx + 1] = ld(s, (k + 2) * kMtW + tx);
+        if (w + 1 < nwin) load(w + 2);      // into the slot of window w - 1
     }
 }
 

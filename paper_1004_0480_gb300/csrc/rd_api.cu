@@ -32,6 +32,28 @@ namespace {
 
 thread_local char g_err[512] = "";
 
+// Allocation fault injection (rd_debug_fail_alloc): when armed with k > 0,
+// the k-th device or pinned-host allocation from then on fails as if the
+// memory were exhausted, and the hook disarms.
+std::mutex g_fault_mu;
+long long g_fail_alloc = 0;
+
+bool injected_failure() {
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    if (g_fail_alloc <= 0) return false;
+    return --g_fail_alloc == 0;
+}
+
+cudaError_t dev_alloc(void** p, size_t n) {
+    if (injected_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    return cudaMalloc(p, n);
+}
+
+cudaError_t host_alloc(void** p, size_t n) {
+    if (injected_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    return cudaMallocHost(p, n);
+}
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Graph {
@@ -569,6 +591,10 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
     }
     d.courant = g.wind_kind != RD_WIND_NONE ? c->courant : nullptr;
     d.mu = c->mu;
+    d.mem_lo[0] = c->state;
+    d.mem_hi[0] = c->state + c->state_bytes;
+    d.mem_lo[1] = c->scratch;
+    d.mem_hi[1] = c->scratch + c->scratch_bytes;
     d.stepn = c->stepn;
     if (g.wind_kind == RD_WIND_3D) {
         d.cy = (float)(g.wind_vel[1] * g.dt / g.h);
@@ -850,15 +876,17 @@ rd_status rd_create(const rd_config* cfg, rd_ctx** out) {
     c->own_stream = true;
     c->tun = default_tuning(c->cfg);
     if (!(cfg->flags & RD_FLAG_NO_ALLOC)) {
-        e = cudaMalloc(&c->state, c->state_bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&c->scratch, c->scratch_bytes);
+        // owned from the first allocation on, so rd_destroy frees whatever
+        // was obtained when a later one fails
+        c->own_mem = true;
+        e = dev_alloc(reinterpret_cast<void**>(&c->state), c->state_bytes);
+        if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void**>(&c->scratch), c->scratch_bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             const size_t sb = c->state_bytes, xb = c->scratch_bytes;
             rd_destroy(c);
             return fail(nullptr, RD_ENOMEM, "cudaMalloc of %zu + %zu bytes failed", sb, xb);
         }
-        c->own_mem = true;
         st = finish_setup(c);
         if (st != RD_OK) { rd_destroy(c); return st; }
     }
@@ -970,11 +998,23 @@ rd_status rd_mass(rd_ctx* c, int s, double out[3]) {
     return out[2] > 0 ? RD_ENONFINITE : RD_OK;
 }
 
+// The debug build's bounds report after a synchronisation (RD_OK in the
+// normal build, whose word is always 0).
+static rd_status bounds_status(rd_ctx* c) {
+    unsigned long long w = 0;
+    RD_CUDA(c, debug_word(&w, false));
+    if (!w) return RD_OK;
+    RD_CUDA(c, debug_word(&w, true));
+    const long long off = (long long)(w << 24) >> 24;   // sign-extend 40 bits
+    return fail(c, RD_EBOUNDS, "bounds check: out-of-range access at site %d, byte offset %lld",
+                (int)((w >> 40) & 0xFFFF), off);
+}
+
 rd_status rd_sync(rd_ctx* c) {
     if (!c) return RD_EINVAL;
     drain_batch(c);
     RD_CUDA(c, cudaStreamSynchronize(c->stream));
-    return RD_OK;
+    return bounds_status(c);
 }
 
 rd_status rd_wait(rd_ctx* c, int64_t timeout_ms) {
@@ -1168,11 +1208,19 @@ const char* rd_status_str(rd_status st) {
     case RD_ETIMEOUT: return "timed out";
     case RD_EBUDGET: return "memory budget exceeded";
     case RD_EUNSUPPORTED: return "not supported by this build";
+    case RD_EBOUNDS: return "out-of-range access found by the bounds-checked build";
     }
     return "unknown status";
 }
 
 const char* rd_last_error(const rd_ctx* c) { return c ? c->err : g_err; }
+
+rd_status rd_debug_fail_alloc(int64_t k) {
+    if (k < 0) return RD_EINVAL;
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    g_fail_alloc = k;
+    return RD_OK;
+}
 
 // ================================================================ batches
 rd_status rd_batch_create(int32_t model, int32_t storage, rd_batch** out) {
@@ -1273,9 +1321,14 @@ rd_status batch_upload(rd_batch* b, const rd_tuning& t, long long* nitems) {
         b->desc_dev = nullptr;
         b->desc_host = nullptr;
         size_t cap = std::max<size_t>(16, n * 2);
-        if (cudaMalloc(&b->desc_dev, cap * sizeof(InstDesc)) != cudaSuccess ||
-            cudaMallocHost(&b->desc_host, cap * sizeof(InstDesc)) != cudaSuccess) {
+        if (dev_alloc(reinterpret_cast<void**>(&b->desc_dev), cap * sizeof(InstDesc)) != cudaSuccess ||
+            host_alloc(reinterpret_cast<void**>(&b->desc_host), cap * sizeof(InstDesc)) != cudaSuccess) {
             cudaGetLastError();
+            // keep nothing of a half-made pair
+            if (b->desc_dev) cudaFree(b->desc_dev);
+            if (b->desc_host) cudaFreeHost(b->desc_host);
+            b->desc_dev = nullptr;
+            b->desc_host = nullptr;
             b->desc_cap = 0;
             return fail(nullptr, RD_ENOMEM, "batch descriptor allocation failed");
         }
@@ -1410,7 +1463,7 @@ rd_status rd_batch_sync(rd_batch* b) {
     if (!b) return RD_EINVAL;
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch sync");
-    return RD_OK;
+    return bounds_status(nullptr);
 }
 
 rd_status rd_batch_destroy(rd_batch* b) {

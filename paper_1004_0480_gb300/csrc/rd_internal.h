@@ -46,6 +46,8 @@ struct InstDesc {
     int wrap_elems;            // periodic x with nx % 4 != 0: some halo
                                // vectors straddle the wrap point
     long long item_begin;      // first global item index of this instance
+    const char* mem_lo[2];     // the instance's state and scratch allocations,
+    const char* mem_hi[2];     // [lo, hi): the debug build's global bounds
 };
 
 struct LaunchArgs {
@@ -94,5 +96,9 @@ cudaError_t launch_unpack(const char* field, float* dense, int storage, int nx, 
 int reduce_blocks();
 cudaError_t launch_reduce(const char* field, int storage, int nx, int ny, int nz,
                           int pitch, double* partials, double* out, cudaStream_t st);
+
+// The debug build's error word (rd_debug.cu): read it, and reset it with
+// ``clear``; always 0 in the normal build.
+cudaError_t debug_word(unsigned long long* out, bool clear);
 
 }  // namespace rdk

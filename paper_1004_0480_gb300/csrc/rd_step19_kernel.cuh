@@ -140,15 +140,18 @@ __device__ __forceinline__ void species19(const InstDesc& sd, int s, float k6,
 // address of the mu plane's element 0.
 template <class ST>
 __device__ __forceinline__ void fetch_mu(const Fetch& f, unsigned char* mu0,
-                                         const float* gplane, int nx, bool elems, bool px) {
+                                         const float* gplane, int nx, bool elems, bool px,
+                                         const InstDesc& sd) {
     float* d = reinterpret_cast<float*>(mu0 + f.soff / (int)sizeof(ST) * 4);
-    Store<float>::cp_async_if(d, gplane + f.goff, f.mode == 1);
+    const int ok = f.mode == 1 && RD_DBG_GLOBAL(sd, gplane + f.goff, 16, kSiteMu);
+    Store<float>::cp_async_if(d, gplane + f.goff, ok);
     if (elems && f.mode == 2) {
 #pragma unroll
         for (int e = 0; e < kVEC; ++e) {
             const int x = f.xs + e;
             const int xi = px ? wrapi(x, nx) : (x < 0 ? 0 : (x >= nx ? nx - 1 : x));
-            Store<float>::cp_async_elem(d + e, gplane + f.goff + xi);
+            if (RD_DBG_GLOBAL(sd, gplane + f.goff + xi, 4, kSiteMu))
+                Store<float>::cp_async_elem(d + e, gplane + f.goff + xi);
         }
     }
 }
@@ -244,7 +247,8 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
                                        (bottom ? TY + 1 : 0) * kRW + (right ? kNQ - 1 : 0) * kVEC,
                                        true);
                 }
-                hfetch[j] = make_int4(f.mode, f.goff, f.soff, f.xs);
+                if (RD_DBG_SHARED(hfetch + j, 16, kSiteHaloDesc))
+                    hfetch[j] = make_int4(f.mode, f.goff, f.soff, f.xs);
             }
         }
         // ---- compute threads: own vector
@@ -286,14 +290,16 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
                     const int hl = tid - ncomp;
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        const int4 h = hfetch[hl + 32 * k];
+                        int4 h = make_int4(0, 0, 0, 0);
+                        if (RD_DBG_SHARED(hfetch + hl + 32 * k, 16, kSiteHaloDesc))
+                            h = hfetch[hl + 32 * k];
                         const Fetch f{h.x, h.y, h.z, h.w};
-                        fetch_all<ST, NS>(f, buf, PEB, gld, fstride, nx, elems, px);
-                        if constexpr (MUF) fetch_mu<ST>(f, buf + mu0_b, gmu, nx, elems, px);
+                        fetch_all<ST, NS>(f, buf, PEB, gld, fstride, nx, elems, px, sd);
+                        if constexpr (MUF) fetch_mu<ST>(f, buf + mu0_b, gmu, nx, elems, px, sd);
                     }
                 } else {
-                    fetch_all<ST, NS>(fo, buf, PEB, gld, fstride, nx, elems, px);
-                    if constexpr (MUF) fetch_mu<ST>(fo, buf + mu0_b, gmu, nx, elems, px);
+                    fetch_all<ST, NS>(fo, buf, PEB, gld, fstride, nx, elems, px, sd);
+                    if constexpr (MUF) fetch_mu<ST>(fo, buf + mu0_b, gmu, nx, elems, px, sd);
                 }
             }
             ++nld;
@@ -364,7 +370,8 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e)
                         mu[e] = __fmaf_rn(-k6[0], lap6[0][e], M::g(sd, c_0[0][e]));
-                    if (computes) Store<float>::store(gmu_st, mu);
+                    if (computes && RD_DBG_GLOBAL(sd, gmu_st, 16, kSiteMu))
+                        Store<float>::store(gmu_st, mu);
                 } else {
                     // state of plane q: a, b (and every PASS 0 species) from
                     // the summed fields, c of PASS 2 from its own vector
@@ -398,7 +405,7 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
                             upwind_axis(cz, cen[s], zm, c_p[s < NSUM ? s : 0], inc[s]);
                         }
                     }
-                    const float cx = (!PLAIN && courant) ? courant[zq] : 0.0f;
+                    const float cx = PLAIN ? 0.0f : courant_at(sd, courant, zq);
                     const bool src_here = src_col && zq == sd.src_z;
                     const unsigned faces = xyf | z_faces(q, nz);
 #pragma unroll
@@ -414,7 +421,9 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
                         species19<PLAIN>(sd, s, k6[s], cen[s], ls, inc[s], cx, left, right,
                                          src_here, px, xs, o);
                         if constexpr (!PLAIN) held_layers_at(sd, s, faces, xs, y, q, o);
-                        if (computes) Store<ST>::store(gst + s * fstride, o);
+                        if (computes && RD_DBG_GLOBAL(sd, gst + s * fstride, 4 * (int)sizeof(ST),
+                                                      kSiteStateStore))
+                            Store<ST>::store(gst + s * fstride, o);
                     }
                 }
 #pragma unroll

@@ -42,6 +42,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "rd_debug.cuh"
 #include "rd_internal.h"
 
 namespace rdk {
@@ -53,22 +54,34 @@ constexpr int kRW = kNQ * kVEC;       // elements per shared-memory row
 // ---------------------------------------------------------------- storage
 template <class ST> struct Store;
 
+// Loads and stores of 4-cell vectors and single cells in either space, and
+// asynchronous global-to-shared copies.  In the bounds-checked debug build
+// (rd_debug.cuh) each checks its shared-memory side and skips an access out
+// of range (a load then yields 0); global sides are checked by the callers,
+// which know the instance.
 template <> struct Store<float> {
     __device__ __forceinline__ static void load(const float* p, float (&v)[4]) {
+        if (!RD_DBG_ANY(p, 16, kSiteSharedLoad)) { v[0] = v[1] = v[2] = v[3] = 0.0f; return; }
         const float4 t = *reinterpret_cast<const float4*>(p);
         v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     }
     __device__ __forceinline__ static void store(float* p, const float (&v)[4]) {
+        if (!RD_DBG_ANY(p, 16, kSiteSharedStore)) return;
         *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
-    __device__ __forceinline__ static float get(const float* p) { return *p; }
+    __device__ __forceinline__ static float get(const float* p) {
+        if (!RD_DBG_ANY(p, 4, kSiteSharedLoad)) return 0.0f;
+        return *p;
+    }
     __device__ __forceinline__ static float round(float x) { return x; }
     __device__ __forceinline__ static void cp_async(float* smem, const float* g) {
+        if (!RD_DBG_SHARED(smem, 16, kSiteCopyDst)) return;
         const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
     }
     // copy only where ``pred`` holds (no branch)
     __device__ __forceinline__ static void cp_async_if(float* smem, const float* g, int pred) {
+        if (pred && !RD_DBG_SHARED(smem, 16, kSiteCopyDst)) return;
         const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
         asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n"
                      " @p cp.async.cg.shared.global [%0], [%1], 16;\n}\n" ::"r"(s), "l"(g),
@@ -77,6 +90,7 @@ template <> struct Store<float> {
     }
     // one element (4 bytes), asynchronously
     __device__ __forceinline__ static void cp_async_elem(float* smem, const float* g) {
+        if (!RD_DBG_SHARED(smem, 4, kSiteCopyDst)) return;
         const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g) : "memory");
     }
@@ -84,6 +98,7 @@ template <> struct Store<float> {
 
 template <> struct Store<__nv_bfloat16> {
     __device__ __forceinline__ static void load(const __nv_bfloat16* p, float (&v)[4]) {
+        if (!RD_DBG_ANY(p, 8, kSiteSharedLoad)) { v[0] = v[1] = v[2] = v[3] = 0.0f; return; }
         const uint2 t = *reinterpret_cast<const uint2*>(p);
         v[0] = __uint_as_float(t.x << 16);
         v[1] = __uint_as_float(t.x & 0xffff0000u);
@@ -91,28 +106,33 @@ template <> struct Store<__nv_bfloat16> {
         v[3] = __uint_as_float(t.y & 0xffff0000u);
     }
     __device__ __forceinline__ static void store(__nv_bfloat16* p, const float (&v)[4]) {
+        if (!RD_DBG_ANY(p, 8, kSiteSharedStore)) return;
         __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
         __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
         *reinterpret_cast<uint2*>(p) =
             make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b));
     }
     __device__ __forceinline__ static float get(const __nv_bfloat16* p) {
+        if (!RD_DBG_ANY(p, 2, kSiteSharedLoad)) return 0.0f;
         return __bfloat162float(*p);
     }
     __device__ __forceinline__ static float round(float x) {
         return __bfloat162float(__float2bfloat16_rn(x));
     }
     __device__ __forceinline__ static void cp_async(__nv_bfloat16* smem, const __nv_bfloat16* g) {
+        if (!RD_DBG_SHARED(smem, 8, kSiteCopyDst)) return;
         const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
     }
     // 2-byte elements have no asynchronous copy: element copies are plain
     __device__ __forceinline__ static void cp_async_elem(__nv_bfloat16* smem,
                                                          const __nv_bfloat16* g) {
+        if (!RD_DBG_SHARED(smem, 2, kSiteCopyDst)) return;
         *smem = *g;
     }
     __device__ __forceinline__ static void cp_async_if(__nv_bfloat16* smem,
                                                        const __nv_bfloat16* g, int pred) {
+        if (pred && !RD_DBG_SHARED(smem, 8, kSiteCopyDst)) return;
         const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
         asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n"
                      " @p cp.async.ca.shared.global [%0], [%1], 8;\n}\n" ::"r"(s), "l"(g),
@@ -131,6 +151,12 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 __device__ __forceinline__ int wrapi(int i, int n) {
     int r = i % n;
     return r < 0 ? r + n : r;
+}
+
+// Entry z of the Courant table ``tab`` (0 without a table).
+__device__ __forceinline__ float courant_at(const InstDesc& sd, const float* tab, int z) {
+    if (!tab || !RD_DBG_GLOBAL(sd, tab + z, 4, kSiteTable)) return 0.0f;
+    return tab[z];
 }
 
 // ----------------------------------------------------------------- models
@@ -422,6 +448,7 @@ __device__ __forceinline__ void wind3d(const InstDesc& sd, int lin, long long lo
     cy = 0.0f;
     cz = 0.0f;
     if (!sd.stepn) return;
+    if (!RD_DBG_GLOBAL(sd, sd.stepn, 16, kSiteTable)) return;
     const long long n = sd.stepn[lin];
     cy = sd.cy;
     cz = (float)(sd.wz_amp * sin((double)n * sd.wz_omega));
@@ -585,10 +612,16 @@ __global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const __grid_co
                     const ST* g = reinterpret_cast<const ST*>(sd.base[lin][s]) + zoff;
                     ST* dst = state_plane(0, s, nld) + ps.own;
                     if (ld_mode == 1) {
-                        Store<ST>::cp_async(dst, g);
+                        if (RD_DBG_GLOBAL(sd, g, 4 * (int)sizeof(ST), kSiteCopySrc))
+                            Store<ST>::cp_async(dst, g);
                     } else {
 #pragma unroll
-                        for (int e = 0; e < kVEC; ++e) dst[e] = g[wrapi(ps.xs + e, nx)];
+                        for (int e = 0; e < kVEC; ++e) {
+                            const ST* ge = g + wrapi(ps.xs + e, nx);
+                            if (RD_DBG_GLOBAL(sd, ge, (int)sizeof(ST), kSiteCopySrc) &&
+                                RD_DBG_SHARED(dst + e, (int)sizeof(ST), kSiteCopyDst))
+                                dst[e] = *ge;
+                        }
                     }
                 }
             }
@@ -648,7 +681,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const __grid_co
                         for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
                     }
                 }
-                const float cx = sd.courant ? sd.courant[zw] : 0.0f;
+                const float cx = courant_at(sd, sd.courant, zw);
                 const bool src_here = src_col && zw == sd.src_z;
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
@@ -677,8 +710,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const __grid_co
                     }
                     if (CH && s == 2) held_layers(sd, s, ps.xs, ps.y, q, o);
                     if (fin) {
-                        ST* g = reinterpret_cast<ST*>(sd.base[lin ^ 1][s]);
-                        Store<ST>::store(g + (long long)q * sd.plane + st_off, o);
+                        ST* g = reinterpret_cast<ST*>(sd.base[lin ^ 1][s]) +
+                                (long long)q * sd.plane + st_off;
+                        if (RD_DBG_GLOBAL(sd, g, 4 * (int)sizeof(ST), kSiteStateStore))
+                            Store<ST>::store(g, o);
                     } else {
                         // inner level, rounded exactly as a stored state
                         Store<ST>::store(state_plane(l, s, q) + ps.own, o);
@@ -764,11 +799,14 @@ __device__ __forceinline__ Fetch make_fetch(int yrow, int xs, int nx, int ny, in
 template <class ST, int S>
 __device__ __forceinline__ void fetch_all(const Fetch& f, unsigned char* plane_buf, int pe_bytes,
                                           const ST* gplane, long long fstride, int nx,
-                                          bool elems, bool px) {
+                                          bool elems, bool px, const InstDesc& sd) {
 #pragma unroll
-    for (int s = 0; s < S; ++s)
-        Store<ST>::cp_async_if(reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff),
-                               gplane + s * fstride + f.goff, f.mode == 1);
+    for (int s = 0; s < S; ++s) {
+        const ST* src = gplane + s * fstride + f.goff;
+        const int ok =
+            f.mode == 1 && RD_DBG_GLOBAL(sd, src, 4 * (int)sizeof(ST), kSiteCopySrc);
+        Store<ST>::cp_async_if(reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff), src, ok);
+    }
     if (elems && f.mode == 2) {
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -777,7 +815,9 @@ __device__ __forceinline__ void fetch_all(const Fetch& f, unsigned char* plane_b
             for (int e = 0; e < kVEC; ++e) {
                 const int x = f.xs + e;
                 const int xi = px ? wrapi(x, nx) : (x < 0 ? 0 : (x >= nx ? nx - 1 : x));
-                Store<ST>::cp_async_elem(d + e, gplane + s * fstride + f.goff + xi);
+                const ST* src = gplane + s * fstride + f.goff + xi;
+                if (RD_DBG_GLOBAL(sd, src, (int)sizeof(ST), kSiteCopySrc))
+                    Store<ST>::cp_async_elem(d + e, src);
             }
         }
     }
@@ -889,7 +929,8 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                     f = make_fetch<ST>(bottom ? y0 + TY : y0 - 1, x0 + hv * kVEC, nx, ny, pitch, px,
                                        py, (bottom ? TY + 1 : 0) * kRW + (hv + 1) * kVEC, true);
                 }
-                hfetch[j] = make_int4(f.mode, f.goff, f.soff, f.xs);
+                if (RD_DBG_SHARED(hfetch + j, 16, kSiteHaloDesc))
+                    hfetch[j] = make_int4(f.mode, f.goff, f.soff, f.xs);
             }
         }
         // ---- compute threads: own vector and its neighbours
@@ -921,12 +962,14 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                     const int hl = tid - ncomp;
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        const int4 h = hfetch[hl + 32 * k];
+                        int4 h = make_int4(0, 0, 0, 0);
+                        if (RD_DBG_SHARED(hfetch + hl + 32 * k, 16, kSiteHaloDesc))
+                            h = hfetch[hl + 32 * k];
                         fetch_all<ST, S>(Fetch{h.x, h.y, h.z, h.w}, buf, PEB, gld, fstride, nx,
-                                         elems, px);
+                                         elems, px, sd);
                     }
                 } else {
-                    fetch_all<ST, S>(fo, buf, PEB, gld, fstride, nx, elems, px);
+                    fetch_all<ST, S>(fo, buf, PEB, gld, fstride, nx, elems, px, sd);
                 }
             }
             ++nld;
@@ -976,7 +1019,7 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
 #pragma unroll
                     for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
                 }
-                const float cx = courant ? courant[zq] : 0.0f;
+                const float cx = courant_at(sd, courant, zq);
                 const bool src_here = src_col && zq == sd.src_z;
                 const unsigned faces = xyf | z_faces(q, nz);
 #pragma unroll
@@ -1006,7 +1049,9 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
                                      px, xs, o, cy, cz);
                         held_layers_at(sd, s, faces, xs, y, q, o);
                     }
-                    if (computes) Store<ST>::store(gst + s * fstride, o);
+                    if (computes &&
+                        RD_DBG_GLOBAL(sd, gst + s * fstride, 4 * (int)sizeof(ST), kSiteStateStore))
+                        Store<ST>::store(gst + s * fstride, o);
                 }
 #pragma unroll
                 for (int s = 0; s < S; ++s)
@@ -1110,18 +1155,24 @@ __device__ __forceinline__ FetchM make_fetch_mirror(int yrow, int xs, int nx, in
 
 template <class ST, int S>
 __device__ __forceinline__ void fetch_all_mirror(const FetchM& f, unsigned char* plane_buf,
-                                                 int pe_bytes, const ST* gplane, long long fstride) {
+                                                 int pe_bytes, const ST* gplane, long long fstride,
+                                                 const InstDesc& sd) {
 #pragma unroll
-    for (int s = 0; s < S; ++s)
-        Store<ST>::cp_async_if(reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff),
-                               gplane + s * fstride + f.goff, f.mode == 1);
+    for (int s = 0; s < S; ++s) {
+        const ST* src = gplane + s * fstride + f.goff;
+        const int ok =
+            f.mode == 1 && RD_DBG_GLOBAL(sd, src, 4 * (int)sizeof(ST), kSiteCopySrc);
+        Store<ST>::cp_async_if(reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff), src, ok);
+    }
     if (f.mode == 2) {
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             ST* d = reinterpret_cast<ST*>(plane_buf + s * pe_bytes + f.soff);
             const ST* g = gplane + s * fstride + f.goff;
 #pragma unroll
-            for (int e = 0; e < kVEC; ++e) Store<ST>::cp_async_elem(d + e, g + f.e[e]);
+            for (int e = 0; e < kVEC; ++e)
+                if (RD_DBG_GLOBAL(sd, g + f.e[e], (int)sizeof(ST), kSiteCopySrc))
+                    Store<ST>::cp_async_elem(d + e, g + f.e[e]);
         }
     }
 }
@@ -1219,8 +1270,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                 const int zs = pz ? wrapi(nld, nz) : mirror_index(nld, nz);
                 const ST* g = gin + (long long)zs * plane;
                 unsigned char* buf = ring + sld * SLOTB;
-                fetch_all_mirror<ST, S>(fo, buf, PEB, g, fstride);
-                if (tid < 2 * kNQ) fetch_all_mirror<ST, S>(fx, buf, PEB, g, fstride);
+                fetch_all_mirror<ST, S>(fo, buf, PEB, g, fstride, sd);
+                if (tid < 2 * kNQ) fetch_all_mirror<ST, S>(fx, buf, PEB, g, fstride, sd);
             }
             ++nld;
             sld = (sld == RING - 1) ? 0 : sld + 1;
@@ -1289,7 +1340,7 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
 #pragma unroll
                     for (int s = 0; s < S; ++s) inc[s][e] = iv[s];
                 }
-                const float cx = courant ? courant[p] : 0.0f;
+                const float cx = courant_at(sd, courant, p);
                 const bool src_here = src_col && p == sd.src_z;
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
@@ -1318,7 +1369,9 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                                      px, xs, o);
                     }
                     held_layers_at(sd, s, faces, xs, y, p, o);
-                    if (stores) Store<ST>::store(gst + s * fstride, o);
+                    if (stores &&
+                        RD_DBG_GLOBAL(sd, gst + s * fstride, 4 * (int)sizeof(ST), kSiteStateStore))
+                        Store<ST>::store(gst + s * fstride, o);
                 }
                 {
                     // c += dt M / h^2 * (7-point Laplacian of mu)
@@ -1326,8 +1379,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                     float mym[kVEC], myp[kVEC], o[kVEC];
                     Store<float>::load(Mc - kRW, mym);
                     Store<float>::load(Mc + kRW, myp);
-                    const float mleft = Mc[-1];
-                    const float mright = Mc[kVEC];
+                    const float mleft = Store<float>::get(Mc - 1);
+                    const float mright = Store<float>::get(Mc + kVEC);
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e) {
                         const float mxm = e ? mu_0[e - 1] : mleft;
@@ -1338,7 +1391,9 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                         o[e] = __fadd_rn(cen[2][e], __fmaf_rn(sd.p[1], lap, inc[2][e]));
                     }
                     held_layers_at(sd, 2, faces, xs, y, p, o);
-                    if (stores) Store<ST>::store(gst + 2 * fstride, o);
+                    if (stores &&
+                        RD_DBG_GLOBAL(sd, gst + 2 * fstride, 4 * (int)sizeof(ST), kSiteStateStore))
+                        Store<ST>::store(gst + 2 * fstride, o);
                 }
             }
             if (p >= z0) gst += plane;
