@@ -108,25 +108,33 @@ int species_of(int model) {
     }
 }
 
-size_t smem_of(int model, int storage, int T, int ty, int stencil = 7) {
+// tile width in cells of every kernel (16 vectors of 4 cells, or 8 of 8)
+constexpr int kTileW = 64;
+
+// cells per thread of the one-step 7-point kernel for a tile_q
+int vw_of(int tile_q) { return tile_q == 8 ? 8 : 4; }
+
+size_t smem_of(int model, int storage, int T, int ty, int stencil = 7, int tq = kTileQ) {
+    const int vw = vw_of(tq);
     if (stencil == 19)
         return is_ch(model) ? smem19_ch_bytes(elem_bytes(storage), ty)
                             : smem19_bytes(species_of(model), elem_bytes(storage), ty);
     switch (model) {
-    case RD_MODEL_DIFFUSION: return smem_diffusion(storage, T, ty);
-    case RD_MODEL_BRUSSELATOR: return smem_brusselator(storage, T, ty);
-    case RD_MODEL_CH_FRONT: return smem_ch_front(storage, T, ty);
-    case RD_MODEL_CH_TABLE1: return smem_ch_table1(storage, T, ty);
-    case RD_MODEL_AIR: return smem_air(storage, T, ty);
-    case RD_MODEL_TURING: return smem_turing(storage, T, ty);
+    case RD_MODEL_DIFFUSION: return smem_diffusion(storage, T, ty, vw);
+    case RD_MODEL_BRUSSELATOR: return smem_brusselator(storage, T, ty, vw);
+    case RD_MODEL_CH_FRONT: return smem_ch_front(storage, T, ty, vw);
+    case RD_MODEL_CH_TABLE1: return smem_ch_table1(storage, T, ty, vw);
+    case RD_MODEL_AIR: return smem_air(storage, T, ty, vw);
+    case RD_MODEL_TURING: return smem_turing(storage, T, ty, vw);
     }
     return 0;
 }
 
 // CTA size of a step kernel: the one-step kernel has a thread per tile
 // vector; the multi-level kernel (tile vectors + 2 halo) x (rows + 2 L)
-int threads_of(int model, int T, int ty, int stencil = 7) {
+int threads_of(int model, int T, int ty, int stencil = 7, int tq = kTileQ) {
     if (stencil == 19) return threads19(ty);
+    if (T == 1 && !is_ch(model) && vw_of(tq) == 8) return 8 * ty + 32;   // 8 cells per thread
     // the one-step kernel needs an even tile height (16 ty compute threads,
     // then a whole halo warp); an odd height at one step per launch (the
     // last launch of a call whose tuning steps 2 or 3 per launch) runs the
@@ -188,11 +196,11 @@ int variant_code(const rd_config& g) {
 }
 
 int occupancy(int model, int storage, int T, int ty, int regcap = 0, int plain = 0,
-              int stencil = 7) {
+              int stencil = 7, int tq = kTileQ) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int, int, int>, int> cache;
+    static std::map<std::tuple<int, int, int, int, int, int, int, int>, int> cache;
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_tuple(model, storage, T, ty, regcap, plain, stencil);
+    auto key = std::make_tuple(model, storage, T, ty, regcap, plain, stencil, tq);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int occ = 0;
@@ -203,7 +211,8 @@ int occupancy(int model, int storage, int T, int ty, int regcap = 0, int plain =
     dummy.plain = plain == 1;
     dummy.wind3 = plain == 2;
     dummy.ty = ty;
-    const size_t smem = smem_of(model, storage, T, ty, stencil);
+    dummy.vw = vw_of(tq);
+    const size_t smem = smem_of(model, storage, T, ty, stencil, tq);
     if (launch_model(model, storage, T, dummy, 0, smem, nullptr, &occ, stencil) != cudaSuccess)
         occ = 0;
     cudaGetLastError();
@@ -465,8 +474,7 @@ int tiles(int n, int t) { return (n + t - 1) / t; }
 
 // z chunk so one launch has about ``waves`` work items per resident CTA
 int auto_zchunk(const rd_config& g, const rd_tuning& t, int occ, int waves) {
-    const int vec = vec_of(g.storage);
-    const long long cols = (long long)tiles(g.nx, t.tile_q * vec) * tiles(g.ny, t.tile_y);
+    const long long cols = (long long)tiles(g.nx, kTileW) * tiles(g.ny, t.tile_y);
     const long long slots = (long long)std::max(occ, 1) * num_sms() * waves;
     long long nzc = std::max<long long>(1, (slots + cols - 1) / cols);
     int zc = (int)std::max<long long>(1, (g.nz + nzc - 1) / nzc);
@@ -478,16 +486,25 @@ int auto_zchunk(const rd_config& g, const rd_tuning& t, int occ, int waves) {
 rd_status check_tuning(const rd_config& g, const rd_tuning& t) {
     if (t.tsteps < 1 || t.tsteps > max_tsteps(g))
         return fail(nullptr, RD_EINVAL, "tsteps out of range");
-    if (t.tile_q != kTileQ)
-        return fail(nullptr, RD_EINVAL, "tile_q must be %d in this build", kTileQ);
+    if (t.tile_q != kTileQ && t.tile_q != 8)
+        return fail(nullptr, RD_EINVAL, "tile_q must be %d or 8 in this build", kTileQ);
+    if (t.tile_q == 8) {
+        // 8 cells per thread: the one-step 7-point kernel; its compute
+        // threads (8 per row) fill whole warps, as its shuffles need
+        if (t.tsteps != 1 || is_ch(g.model) || stencil_of(g) != 7)
+            return fail(nullptr, RD_EINVAL,
+                        "tile_q 8 is the one-step 7-point kernel without Cahn-Hilliard");
+        if (t.tile_y % 4 != 0 || t.tile_y > 40)
+            return fail(nullptr, RD_EINVAL, "tile_q 8 needs tile_y a multiple of 4, at most 40");
+    }
     if (t.tile_y < 1 || t.zchunk < 1) return fail(nullptr, RD_EINVAL, "tile out of range");
     if (t.regcap != 0 && t.regcap != 1) return fail(nullptr, RD_EINVAL, "regcap must be 0 or 1");
     if (t.tsteps == 1 && (!is_ch(g.model) || stencil_of(g) == 19) && (t.tile_y & 1))
         return fail(nullptr, RD_EINVAL, "tile_y must be even for one step per launch");
-    if (threads_of(g.model, t.tsteps, t.tile_y, stencil_of(g)) > kMaxThreads)
+    if (threads_of(g.model, t.tsteps, t.tile_y, stencil_of(g), t.tile_q) > kMaxThreads)
         return fail(nullptr, RD_EINVAL, "tile_y %d too tall for %d steps per launch", t.tile_y,
                     t.tsteps);
-    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_y, stencil_of(g));
+    const size_t sm = smem_of(g.model, g.storage, t.tsteps, t.tile_y, stencil_of(g), t.tile_q);
     if (sm + sizeof(InstDesc) + 64 > (size_t)max_smem_optin())
         return fail(nullptr, RD_EINVAL, "tile needs %zu bytes of shared memory", sm);
     return RD_OK;
@@ -529,7 +546,7 @@ rd_tuning default_tuning(const rd_config& g) {
     t.graph = 1;
     const int occ = occupancy(g.model, g.storage, t.tsteps, t.tile_y, 0, variant_code(g),
                               stencil_of(g));
-    const long long cols = (long long)tiles(g.nx, t.tile_q * vec_of(g.storage)) * tiles(g.ny, t.tile_y);
+    const long long cols = (long long)tiles(g.nx, kTileW) * tiles(g.ny, t.tile_y);
     t.zchunk = wave_zchunk({{cols, g.nz}}, (long long)std::max(occ, 1) * num_sms());
     return t;
 }
@@ -604,8 +621,7 @@ void fill_desc(rd_ctx* c, InstDesc& d, const rd_tuning& t) {
     d.src_s = g.src_species >= 0 ? g.src_species : -1;
     d.src_x = g.src_x; d.src_y = g.src_y; d.src_z = g.src_z;
     d.src_amt = (float)(g.src_rate * g.dt);
-    const int vec = c->vec;
-    d.ntx = tiles(g.nx, t.tile_q * vec);
+    d.ntx = tiles(g.nx, kTileW);
     d.wrap_elems = d.per_x && (g.nx % 4 != 0);
     d.nty = tiles(g.ny, t.tile_y);
     d.zchunk = std::max(1, std::min(t.zchunk, g.nz));
@@ -679,6 +695,7 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     a.regcap = c->tun.regcap;
     a.plain = plain_problem(c->cfg);
     a.wind3 = c->cfg.wind_kind == RD_WIND_3D;
+    a.vw = vw_of(c->tun.tile_q);
     a.ty = c->tun.tile_y;
     if (c->kernel != RD_KERNEL_MARCH) {   // the paper's designs, one step each
         if (T != 1) return fail(c, RD_EINVAL, "the ablation kernels step once per launch");
@@ -688,10 +705,10 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
         return RD_OK;
     }
     const int sten = stencil_of(c->cfg);
-    const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty, sten);
+    const size_t sm = smem_of(c->cfg.model, c->cfg.storage, T, a.ty, sten, c->tun.tile_q);
     const int occ = std::max(
         1, occupancy(c->cfg.model, c->cfg.storage, T, a.ty, a.regcap,
-                     a.plain ? 1 : a.wind3 ? 2 : 0, sten));
+                     a.plain ? 1 : a.wind3 ? 2 : 0, sten, c->tun.tile_q));
     const long long grid = std::min<long long>(a.nitems, (long long)occ * num_sms());
     cudaError_t e =
         launch_model(c->cfg.model, c->cfg.storage, T, a, (int)grid, sm, st, nullptr, sten);
@@ -1103,15 +1120,18 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
     std::vector<rd_tuning> cands;
     const int sten = stencil_of(g);
     for (int T = 1; T <= max_tsteps(g); ++T)
-        for (int ty : {4, 8, 10, 12, 14, 16, 20, 24, 32}) {
-          // the register cap is a variant of the 7-point one-step kernel
-          const bool rc_variant = T == 1 && !is_ch(g.model) && sten == 7;
+      for (int tq : {kTileQ, 8}) {
+        // 8 cells per thread: the one-step 7-point kernel (heights 4k)
+        if (tq == 8 && (T != 1 || is_ch(g.model) || sten != 7)) continue;
+        for (int ty : {4, 8, 10, 12, 14, 16, 20, 24, 28, 32}) {
+          // the register cap is a variant of the 7-point 4-cell one-step kernel
+          const bool rc_variant = T == 1 && !is_ch(g.model) && sten == 7 && tq == kTileQ;
           for (int rc = 0; rc <= (rc_variant ? 1 : 0); ++rc) {
             rd_tuning t{};
-            t.tsteps = T; t.tile_q = kTileQ; t.tile_y = ty; t.graph = 1; t.zchunk = 1;
+            t.tsteps = T; t.tile_q = tq; t.tile_y = ty; t.graph = 1; t.zchunk = 1;
             t.regcap = rc;
             if (check_tuning(g, t) != RD_OK) continue;
-            const int occ = occupancy(g.model, g.storage, T, ty, rc, variant_code(g), sten);
+            const int occ = occupancy(g.model, g.storage, T, ty, rc, variant_code(g), sten, tq);
             if (occ < 1) continue;
             // z-chunks for 1, 2, 4, 8 waves of CTAs; for one step per launch
             // also every split of z into 1..16 chunks, since how evenly the
@@ -1124,12 +1144,13 @@ rd_status rd_autotune(rd_ctx* c, rd_tuning* best_out) {
                 t.zchunk = zc;
                 bool dup = false;
                 for (auto& o : cands)
-                    dup |= (o.tsteps == t.tsteps && o.tile_y == t.tile_y && o.zchunk == t.zchunk &&
-                            o.regcap == t.regcap);
+                    dup |= (o.tsteps == t.tsteps && o.tile_q == t.tile_q && o.tile_y == t.tile_y &&
+                            o.zchunk == t.zchunk && o.regcap == t.regcap);
                 if (!dup) cands.push_back(t);
             }
           }
         }
+      }
     cudaEvent_t e0, e1;
     RD_CUDA(c, cudaEventCreate(&e0));
     RD_CUDA(c, cudaEventCreate(&e1));
@@ -1304,7 +1325,7 @@ rd_tuning batch_tuning(rd_batch* b) {
     const int occ = occupancy(b->model, b->storage, 1, t.tile_y, 0, 0, b->stencil);
     std::vector<std::pair<long long, int>> cols_nz;
     for (rd_ctx* c : b->members)
-        cols_nz.push_back({(long long)tiles(c->cfg.nx, t.tile_q * vec_of(b->storage)) *
+        cols_nz.push_back({(long long)tiles(c->cfg.nx, kTileW) *
                                tiles(c->cfg.ny, t.tile_y),
                            c->cfg.nz});
     t.zchunk = cols_nz.empty() ? 32 : wave_zchunk(cols_nz, (long long)std::max(occ, 1) * num_sms());
@@ -1374,10 +1395,11 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
         a.wind3 = a.wind3 || m->cfg.wind_kind == RD_WIND_3D;
     }
     a.ty = t.tile_y;
-    const size_t sm = smem_of(b->model, b->storage, T, a.ty, b->stencil);
+    a.vw = vw_of(t.tile_q);
+    const size_t sm = smem_of(b->model, b->storage, T, a.ty, b->stencil, t.tile_q);
     const int occ = std::max(
         1, occupancy(b->model, b->storage, T, a.ty, a.regcap, a.plain ? 1 : a.wind3 ? 2 : 0,
-                     b->stencil));
+                     b->stencil, t.tile_q));
     const long long grid = std::min<long long>(nitems, (long long)occ * num_sms());
     cudaError_t e = launch_model(b->model, b->storage, T, a, (int)grid, sm, st, nullptr, b->stencil);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch step launch");

@@ -62,6 +62,8 @@ struct LaunchArgs {
                                // wind, and isotropic diffusivities
     int wind3;                 // some instance has the 3-D wind (kernels take
                                // the variant with upwind along y and z)
+    int vw;                    // cells per thread of the one-step 7-point
+                               // kernel: 4 (16 threads per tile row) or 8
     InstDesc one;              // the instance of a single-instance launch
 };
 
@@ -78,11 +80,11 @@ cudaError_t launch_air(int storage, int tsteps, const LaunchArgs& a, int grid,
 cudaError_t launch_ch_table1(int storage, int tsteps, const LaunchArgs& a, int grid,
                              size_t smem, cudaStream_t st, int* occ);
 // Dynamic shared memory (bytes) and CTA size of one step kernel variant.
-size_t smem_diffusion(int storage, int tsteps, int ty);
-size_t smem_brusselator(int storage, int tsteps, int ty);
-size_t smem_ch_front(int storage, int tsteps, int ty);
-size_t smem_air(int storage, int tsteps, int ty);
-size_t smem_ch_table1(int storage, int tsteps, int ty);
+size_t smem_diffusion(int storage, int tsteps, int ty, int vw);
+size_t smem_brusselator(int storage, int tsteps, int ty, int vw);
+size_t smem_ch_front(int storage, int tsteps, int ty, int vw);
+size_t smem_air(int storage, int tsteps, int ty, int vw);
+size_t smem_ch_table1(int storage, int tsteps, int ty, int vw);
 int step_threads(int model, int tsteps, int ty);
 
 // Auxiliary kernels (rd_aux.cu).

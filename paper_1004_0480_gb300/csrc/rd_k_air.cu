@@ -10,8 +10,8 @@ cudaError_t launch_air(int storage, int tsteps, const LaunchArgs& a, int grid,
     return launch_model<MAir>(storage, tsteps, a, grid, smem, st, occ);
 }
 
-size_t smem_air(int storage, int tsteps, int ty) {
-    return smem_for<MAir>(storage, tsteps, ty);
+size_t smem_air(int storage, int tsteps, int ty, int vw) {
+    return smem_for<MAir>(storage, tsteps, ty, vw);
 }
 
 }  // namespace rdk

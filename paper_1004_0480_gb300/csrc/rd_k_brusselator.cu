@@ -10,8 +10,8 @@ cudaError_t launch_brusselator(int storage, int tsteps, const LaunchArgs& a, int
     return launch_model<MBrusselator>(storage, tsteps, a, grid, smem, st, occ);
 }
 
-size_t smem_brusselator(int storage, int tsteps, int ty) {
-    return smem_for<MBrusselator>(storage, tsteps, ty);
+size_t smem_brusselator(int storage, int tsteps, int ty, int vw) {
+    return smem_for<MBrusselator>(storage, tsteps, ty, vw);
 }
 
 }  // namespace rdk

@@ -10,8 +10,8 @@ cudaError_t launch_ch_front(int storage, int tsteps, const LaunchArgs& a, int gr
     return launch_model<MChFront>(storage, tsteps, a, grid, smem, st, occ);
 }
 
-size_t smem_ch_front(int storage, int tsteps, int ty) {
-    return smem_for<MChFront>(storage, tsteps, ty);
+size_t smem_ch_front(int storage, int tsteps, int ty, int vw) {
+    return smem_for<MChFront>(storage, tsteps, ty, vw);
 }
 
 }  // namespace rdk

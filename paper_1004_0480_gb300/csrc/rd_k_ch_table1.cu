@@ -10,8 +10,8 @@ cudaError_t launch_ch_table1(int storage, int tsteps, const LaunchArgs& a, int g
     return launch_model<MChTable1>(storage, tsteps, a, grid, smem, st, occ);
 }
 
-size_t smem_ch_table1(int storage, int tsteps, int ty) {
-    return smem_for<MChTable1>(storage, tsteps, ty);
+size_t smem_ch_table1(int storage, int tsteps, int ty, int vw) {
+    return smem_for<MChTable1>(storage, tsteps, ty, vw);
 }
 
 }  // namespace rdk

@@ -10,8 +10,8 @@ cudaError_t launch_diffusion(int storage, int tsteps, const LaunchArgs& a, int g
     return launch_model<MDiffusion>(storage, tsteps, a, grid, smem, st, occ);
 }
 
-size_t smem_diffusion(int storage, int tsteps, int ty) {
-    return smem_for<MDiffusion>(storage, tsteps, ty);
+size_t smem_diffusion(int storage, int tsteps, int ty, int vw) {
+    return smem_for<MDiffusion>(storage, tsteps, ty, vw);
 }
 
 }  // namespace rdk

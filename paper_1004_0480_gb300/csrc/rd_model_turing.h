@@ -28,7 +28,7 @@ struct MTuring {
 // 19-point kernel (one step per launch).  Same contracts as the other models.
 cudaError_t launch_turing(int storage, int tsteps, const LaunchArgs& a, int grid, size_t smem,
                           cudaStream_t st, int* occ);
-size_t smem_turing(int storage, int tsteps, int ty);
+size_t smem_turing(int storage, int tsteps, int ty, int vw);
 cudaError_t launch19_turing(int storage, const LaunchArgs& a, int grid, size_t smem,
                             cudaStream_t st, int* occ);
 

@@ -1411,6 +1411,12 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
     }
 }
 
+}  // namespace rdk
+
+#include "rd_step1w_kernel.cuh"
+
+namespace rdk {
+
 // Launch helper used by the per-model translation units.
 template <class M, class ST, int T, bool ONE>
 cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t st, int* occ) {
@@ -1420,8 +1426,14 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
     const bool lean = (T == 1 && !M::CH) && !(a.ty & 1);
     constexpr bool lean_ch = (T == 1 && M::CH);
     void (*k)(const LaunchArgs);
+    // 8 cells per thread: the one-step kernel of rd_step1w_kernel.cuh
+    const bool wide = lean && a.vw == 8;
     if constexpr (lean_ch) {
         k = a.plain ? rd_stepch_kernel<M, ST, ONE, true> : rd_stepch_kernel<M, ST, ONE, false>;
+    } else if (wide) {
+        k = a.plain  ? rd_step1w_kernel<M, ST, ONE, true, false>
+            : a.wind3 ? rd_step1w_kernel<M, ST, ONE, false, true>
+                      : rd_step1w_kernel<M, ST, ONE, false, false>;
     } else if (lean) {
         // register budget of the one-step kernel: 128 (regcap 0) or 64 (regcap 1)
         if (a.plain)
@@ -1437,9 +1449,11 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
         k = rd_step_kernel<M, ST, T, ONE>;
     }
     // dynamic shared memory granted so far, per kernel variant (4: the
-    // multi-level kernel at T = 1; 5, 6: the one-step kernel with 3-D wind)
-    static size_t configured[7] = {0, 0, 0, 0, 0, 0, 0};
-    const int variant = (T == 1 && !M::CH && !lean) ? 4
+    // multi-level kernel at T = 1; 5, 6: the one-step kernel with 3-D wind;
+    // 7, 8, 9: the 8-cell kernel, plain, 3-D wind, general)
+    static size_t configured[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const int variant = wide ? (a.plain ? 7 : a.wind3 ? 8 : 9)
+                        : (T == 1 && !M::CH && !lean) ? 4
                         : (lean && !a.plain && a.wind3) ? 5 + (a.regcap ? 1 : 0)
                         : (lean && a.regcap ? 1 : 0) + ((lean || lean_ch) && a.plain ? 2 : 0);
     size_t& conf = configured[variant];
@@ -1449,7 +1463,8 @@ cudaError_t launch_one(const LaunchArgs& a, int grid, size_t smem, cudaStream_t 
         if (e != cudaSuccess) return e;
         conf = smem;
     }
-    const int threads = lean      ? Layout1<M, ST>::threads(a.ty)
+    const int threads = wide      ? Layout1w<M, ST>::threads(a.ty)
+                        : lean    ? Layout1<M, ST>::threads(a.ty)
                         : lean_ch ? LayoutCH<ST>::threads(a.ty)
                                   : Layout<M, ST, T>::threads(a.ty);
     if (threads > kMaxThreads) return cudaErrorInvalidConfiguration;
@@ -1490,7 +1505,10 @@ cudaError_t launch_model(int storage, int tsteps, const LaunchArgs& a, int grid,
 }
 
 template <class M>
-size_t smem_for(int storage, int tsteps, int ty) {
+size_t smem_for(int storage, int tsteps, int ty, int vw = 4) {
+    if (tsteps == 1 && !M::CH && vw == 8)
+        return storage == RD_STORE_F32 ? Layout1w<M, float>::total(ty)
+                                       : Layout1w<M, __nv_bfloat16>::total(ty);
     if (storage == RD_STORE_F32) {
         switch (tsteps) {
         case 1: return M::CH ? LayoutCH<float>::total(ty)
