@@ -11,6 +11,8 @@ cudaError_t launch_turing(int storage, int tsteps, const LaunchArgs& a, int grid
     return launch_model<MTuring>(storage, tsteps, a, grid, smem, st, occ);
 }
 
-size_t smem_turing(int storage, int tsteps, int ty) { return smem_for<MTuring>(storage, tsteps, ty); }
+size_t smem_turing(int storage, int tsteps, int ty, int vw) {
+    return smem_for<MTuring>(storage, tsteps, ty, vw);
+}
 
 }  // namespace rdk
