@@ -304,9 +304,11 @@ rd_step1w_kernel(const __grid_constant__ LaunchArgs a) {
                     const float lsh = __shfl_up_sync(FULL, own_0[s][kW8 - 1], 1);
                     const float rsh = __shfl_down_sync(FULL, own_0[s][0], 1);
                     const unsigned char* Ps = Pc + s * PEB;
-                    left[s] = v != 0 ? lsh : (lface ? own_0[s][0] : lds_one<ST>(Ps - EB));
-                    right[s] = v != kQ8 - 1 ? rsh
-                                            : (rface ? own_0[s][kW8 - 1] : lds_one<ST>(Ps + kW8 * EB));
+                    // a zero-flux face first: it may end a vector inside the
+                    // tile row (the lanes beyond it hold no cells)
+                    left[s] = lface ? own_0[s][0] : (v != 0 ? lsh : lds_one<ST>(Ps - EB));
+                    right[s] = rface ? own_0[s][kW8 - 1]
+                                     : (v != kQ8 - 1 ? rsh : lds_one<ST>(Ps + kW8 * EB));
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {

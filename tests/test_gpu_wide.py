@@ -55,7 +55,9 @@ def run_gpu(rd, cfg, steps, storage="f32", tuning=None, fields=None):
 
 def cases():
     out = {}
-    for nx in (64, 65, 66, 67, 68, 69, 70, 71, 141):
+    # nx % 8 = 0..7, and zero-flux faces ending a vector at every lane of a
+    # tile row (nx % 64 = 8, 16, ..., 56)
+    for nx in (64, 65, 66, 67, 68, 69, 70, 71, 141, 16, 24, 40, 72, 80, 104, 120):
         out[f"diffusion_neumann_{nx}"] = (W.diffusion_blob(shape=(nx, 23, 19)), TOL_DIFF)
     per_d = W.diffusion_blob(shape=(132, 23, 19))
     per_d["bc"] = [["periodic"] * 6]
@@ -67,6 +69,8 @@ def cases():
     out["brusselator_periodic_132"] = (W.brusselator(shape=(132, 24, 17)), TOL_NONLIN)
     out["brusselator_periodic_70"] = (W.brusselator(shape=(70, 20, 17)), TOL_NONLIN)
     out["brusselator_neumann"] = (W.brusselator(shape=(141, 23, 19), bc="neumann"), TOL_NONLIN)
+    out["brusselator_neumann_48"] = (W.brusselator(shape=(48, 23, 19), bc="neumann"), TOL_NONLIN)
+    out["air_neumann_16"] = (W.air((16, 33, 25), src=(1, 2, 3)), TOL_NONLIN)
     out["air_neumann"] = (W.air((141, 23, 19), src=(5, 17, 2)), TOL_NONLIN)
     air_per = W.air((133, 24, 19), src=(130, 0, 17))
     air_per["bc"] = [["periodic"] * 6 for _ in range(3)]
