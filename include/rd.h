@@ -231,6 +231,23 @@ rd_status rd_step(rd_ctx* ctx, int64_t nsteps);
  * loop.  Synchronises the stream. */
 rd_status rd_get_field(rd_ctx* ctx, int s, float* dst, size_t count);
 
+/* Bytes of one plane of one species: ny rows of the row pitch in elements of
+ * the storage type (see rd_attach).  0 for a NULL context. */
+size_t rd_plane_bytes(const rd_ctx* ctx);
+
+/* Copy planes z0 .. z0 + k - 1 of species ``s`` of the current level
+ * between the context and the caller's device buffer ``buf`` of ``bytes`` =
+ * k * rd_plane_bytes(ctx) bytes (the planes back to back in the context's
+ * layout, storage type and row pitch kept): to_buf = 1 reads the context
+ * into buf, 0 writes buf into the context.  The ghost-plane exchange of a
+ * z-slab decomposition of one problem over several GPUs, as the paper's
+ * host loop moves whole arrays between host and device (Table 3).  One
+ * device-to-device copy, asynchronous on the context's stream; the caller
+ * keeps buf alive until that stream has passed it.  RD_EINVAL for planes
+ * outside the grid, a wrong size or a host pointer. */
+rd_status rd_copy_planes(rd_ctx* ctx, int s, int z0, int k, void* buf, size_t bytes,
+                         int32_t to_buf);
+
 /* FP64 reduction of species ``s`` of the current level: out[0] = sum,
  * out[1] = sum of squares, out[2] = count of non-finite values.  The sums
  * are accumulated in double precision in a fixed order, so repeated calls

@@ -94,6 +94,8 @@ SIGNATURES = {
     "rd_batch_launch_count": (_I64, [_P]),
     "rd_moments_noalloc": (_I, [_P, _I32, _I32, _I32, _I32, _I64, _P, _P]),
     "rd_debug_fail_alloc": (_I, [_I64]),
+    "rd_plane_bytes": (_SZ, [_P]),
+    "rd_copy_planes": (_I, [_P, _I, _I, _I, _P, _SZ, _I32]),
     "rd_debug_bounds": (_I, [ctypes.POINTER(ctypes.c_uint64), _I32]),
 }
 

@@ -991,6 +991,32 @@ rd_status rd_get_field(rd_ctx* c, int s, float* dst, size_t count) {
     return RD_OK;
 }
 
+size_t rd_plane_bytes(const rd_ctx* c) {
+    return c ? (size_t)c->plane * c->ebytes : 0;
+}
+
+rd_status rd_copy_planes(rd_ctx* c, int s, int z0, int k, void* buf, size_t bytes,
+                         int32_t to_buf) {
+    if (!c || !buf) return fail(c, RD_EINVAL, "null argument");
+    if (!c->state) return fail(c, RD_EINVAL, "no memory attached");
+    if (s < 0 || s >= c->S) return fail(c, RD_EINVAL, "species %d out of range", s);
+    if (k < 0 || z0 < 0 || (long long)z0 + k > c->cfg.nz)
+        return fail(c, RD_EINVAL, "planes %d..%d outside 0..%d", z0, z0 + k - 1, c->cfg.nz - 1);
+    const size_t pb = rd_plane_bytes(c);
+    if (bytes != pb * (size_t)k)
+        return fail(c, RD_EINVAL, "buffer of %zu bytes for %d planes of %zu bytes", bytes, k, pb);
+    if (!is_device_ptr(buf)) return fail(c, RD_EINVAL, "the buffer must be device memory");
+    if (k == 0) return RD_OK;
+    drain_batch(c);
+    // the planes of one species are contiguous: one copy
+    char* field = field_ptr(c, c->cur, s) + (size_t)z0 * pb;
+    if (to_buf)
+        RD_CUDA(c, cudaMemcpyAsync(buf, field, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    else
+        RD_CUDA(c, cudaMemcpyAsync(field, buf, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    return RD_OK;
+}
+
 rd_status rd_step(rd_ctx* c, int64_t nsteps) {
     if (!c || nsteps < 0) return fail(c, RD_EINVAL, "bad argument");
     if (!c->state) return fail(c, RD_EINVAL, "no memory attached");

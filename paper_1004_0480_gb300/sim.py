@@ -167,6 +167,22 @@ class Sim:
     def get_fields(self):
         return np.stack([self.get_field(s) for s in range(self.nspecies)])
 
+    # -- planes (z-slab exchange)
+    @property
+    def plane_bytes(self):
+        """Bytes of one plane of one species in the context's layout."""
+        return self.lib.rd_plane_bytes(self.ctx)
+
+    def copy_planes(self, s, z0, k, buf, to_buf):
+        """Copy planes z0 .. z0+k-1 of species s between the context and the
+        device tensor ``buf`` (k * plane_bytes bytes, contiguous);
+        asynchronous on the context's stream."""
+        if not buf.is_cuda or not buf.is_contiguous():
+            raise ValueError("buf must be a contiguous device tensor")
+        nbytes = buf.numel() * buf.element_size()
+        self._check(self.lib.rd_copy_planes(self.ctx, s, z0, k, ctypes.c_void_p(buf.data_ptr()),
+                                            nbytes, 1 if to_buf else 0), "rd_copy_planes")
+
     # -- stepping
     def step(self, n):
         self._check(self.lib.rd_step(self.ctx, int(n)), "rd_step")

@@ -4,7 +4,7 @@ instance larger than one GPU's memory.
 Each rank owns a contiguous range of z planes.  A side of the slab that
 borders another rank (or wraps round, for periodic z) carries ``halo``
 ghost planes: 1 for one step of the 7- or 19-point update, 2 for the
-Cahn-Hilliard model, whose chained Laplacian reaches two planes.  A side on
+Cahn-Hilliard models, whose chained Laplacian reaches two planes.  A side on
 a global non-periodic face has no ghost planes and keeps the global face
 rule (zero flux, or a held layer).  After every step the ranks send their
 outermost owned planes to their z neighbours, which refills the ghost
@@ -14,11 +14,17 @@ cell reads them.  Every owned cell therefore sees exactly the neighbours it
 has in the undivided grid, and the owned planes of all ranks equal the
 undivided result bit for bit.
 
-The step itself is a callable ``step_fn(fields, nsteps) -> fields`` on the
-rank's local problem (``local_config``), so the decomposition does not
-depend on the stepper.  Point-to-point messages go through
-``torch.distributed`` (NCCL between GPUs, gloo on CPU); the fields are
-float arrays of shape (S, nz_local, ny, nx).
+A rank's slab is an object with ``read(z0, k)``, ``empty(k)``,
+``write(z0, k, buf)`` and ``step(n)``: ``HostSlab`` holds float arrays and
+steps them with any callable (the CPU tests use the FP64 oracle);
+``DeviceSlab`` keeps the fields on the rank's GPU in a context of the CUDA
+library, moves ghost planes with ``rd_copy_planes`` (device to device, the
+context's own layout) and steps with ``rd_step``.  ``exchange`` moves the
+planes with ``torch.distributed`` point-to-point messages (NCCL between
+GPUs, into each receiving GPU's own buffers; gloo on CPU);
+``exchange_local`` moves them between slabs held by one process (the same
+messages, no collective).  ``owned_moments`` reduces the owned planes in
+FP64 and sums the ranks' results with an FP64 all-reduce.
 
 Not supported: the logarithmic wind profile (its u(z) depends on the global
 plane index and nz, which a local problem does not know) and slabs thinner
@@ -66,7 +72,7 @@ class SlabPlan:
 
 
 def halo_width(cfg) -> int:
-    return 2 if cfg["model"] == "ch_front" else 1
+    return 2 if cfg["model"] in ("ch_front", "ch_table1") else 1
 
 
 def plan(cfg, world: int, rank: int) -> SlabPlan:
@@ -123,47 +129,187 @@ def owned(fields_local, p: SlabPlan):
     return fields_local[:, p.owned]
 
 
-def exchange(fields_local, p: SlabPlan, dist, torch):
-    """Refill the ghost planes from the neighbours' outermost owned planes.
-
-    Messages: the lowest ``lo_peer``-facing owned planes go to ``lo_peer``
-    (tag 1: they become its upper ghost planes), the highest go to
-    ``hi_peer`` (tag 0: its lower ghost planes).  Receives are posted
-    before sends; with two ranks and periodic z both messages go to the
-    same peer and are told apart by their tags."""
+def messages(p: SlabPlan):
+    """The plane transfers of one exchange, as (peer, tag, local z0, k):
+    the lowest owned planes go to ``lo_peer`` with tag 1 (they become its
+    upper ghost planes), the highest to ``hi_peer`` with tag 0 (its lower
+    ghost planes); receives mirror them.  With two ranks and periodic z both
+    messages go to the same peer and are told apart by their tags."""
     if p.world == 1:
-        return fields_local
-    f = torch.from_numpy(fields_local) if isinstance(fields_local, np.ndarray) else fields_local
+        return [], []
+    nzl = p.cfg["shape"][2]
     own = p.owned
-    reqs, recv = [], []
+    sends, recvs = [], []
     if p.lo:
-        buf = torch.empty_like(f[:, :p.lo]).contiguous()
-        reqs.append(dist.irecv(buf, src=p.lo_peer, tag=0))
-        recv.append((slice(0, p.lo), buf))
+        recvs.append((p.lo_peer, 0, 0, p.lo))
+        sends.append((p.lo_peer, 1, own.start, p.lo))
     if p.hi:
-        buf = torch.empty_like(f[:, f.shape[1] - p.hi:]).contiguous()
-        reqs.append(dist.irecv(buf, src=p.hi_peer, tag=1))
-        recv.append((slice(f.shape[1] - p.hi, f.shape[1]), buf))
-    sends = []
-    if p.lo:
-        sends.append(f[:, own.start:own.start + p.lo].contiguous())
-        reqs.append(dist.isend(sends[-1], dst=p.lo_peer, tag=1))
-    if p.hi:
-        sends.append(f[:, own.stop - p.hi:own.stop].contiguous())
-        reqs.append(dist.isend(sends[-1], dst=p.hi_peer, tag=0))
+        recvs.append((p.hi_peer, 1, nzl - p.hi, p.hi))
+        sends.append((p.hi_peer, 0, own.stop - p.hi, p.hi))
+    return sends, recvs
+
+
+def exchange(slab, p: SlabPlan, dist):
+    """Refill the slab's ghost planes from the neighbours' outermost owned
+    planes by point-to-point messages; receives are posted before sends."""
+    sends, recvs = messages(p)
+    reqs, landed = [], []
+    for peer, tag, z0, k in recvs:
+        buf = slab.empty(k)
+        reqs.append(dist.irecv(buf, src=peer, tag=tag))
+        landed.append((z0, k, buf))
+    outgoing = []
+    for peer, tag, z0, k in sends:
+        outgoing.append(slab.read(z0, k))
+        reqs.append(dist.isend(outgoing[-1], dst=peer, tag=tag))
     for r in reqs:
         r.wait()
-    for sl, buf in recv:
-        f[:, sl] = buf
-    return fields_local
+    for z0, k, buf in landed:
+        slab.write(z0, k, buf)
 
 
-def run(fields_local, p: SlabPlan, nsteps: int, step_fn, dist, torch):
+def exchange_local(slabs, plans):
+    """The same exchange between the slabs of all ranks held by one process
+    (every outgoing plane is read before any ghost plane is written)."""
+    mail = {}
+    for r, (slab, p) in enumerate(zip(slabs, plans)):
+        for peer, tag, z0, k in messages(p)[0]:
+            mail[(r, peer, tag)] = slab.read(z0, k)
+    for r, (slab, p) in enumerate(zip(slabs, plans)):
+        for peer, tag, z0, k in messages(p)[1]:
+            slab.write(z0, k, mail[(peer, r, tag)])
+
+
+def run_slab(slab, p: SlabPlan, nsteps: int, dist):
     """Advance the rank's slab by ``nsteps`` steps, one exchange per step.
-    ``fields_local`` must hold valid ghost planes (``scatter``, or a
-    preceding ``run``)."""
-    f = fields_local
+    The slab must hold valid ghost planes (its initial fields cut by
+    ``scatter``, or a preceding run)."""
     for _ in range(int(nsteps)):
-        f = np.ascontiguousarray(step_fn(f, 1))
-        f = exchange(f, p, dist, torch)
-    return f
+        slab.step(1)
+        exchange(slab, p, dist)
+
+
+def run_local(slabs, plans, nsteps: int):
+    """``run_slab`` for the slabs of all ranks held by one process."""
+    for _ in range(int(nsteps)):
+        for slab in slabs:
+            slab.step(1)
+        exchange_local(slabs, plans)
+
+
+class HostSlab:
+    """A slab as a float array (S, nz_local, ny, nx) stepped by
+    ``step_fn(fields, nsteps) -> fields`` (on the CPU); ``plan`` names the
+    owned planes for ``moments``."""
+
+    def __init__(self, fields_local, step_fn, plan: SlabPlan | None = None):
+        import torch
+        self._torch = torch
+        self.fields = np.ascontiguousarray(fields_local)
+        self.step_fn = step_fn
+        self.plan = plan
+
+    def moments(self, s):
+        """FP64 (sum, sum of squares, non-finite count) of species ``s`` over
+        the owned planes."""
+        f = np.asarray(self.fields[s, self.plan.owned], dtype=np.float64)
+        ok = np.isfinite(f)
+        return self._torch.tensor([f[ok].sum(), (f[ok] ** 2).sum(), float((~ok).sum())],
+                                  dtype=self._torch.float64)
+
+    def read(self, z0, k):
+        return self._torch.from_numpy(np.ascontiguousarray(self.fields[:, z0:z0 + k]))
+
+    def empty(self, k):
+        S, _, ny, nx = self.fields.shape
+        return self._torch.empty((S, k, ny, nx), dtype=self._torch.from_numpy(self.fields[:0]).dtype)
+
+    def write(self, z0, k, buf):
+        self.fields[:, z0:z0 + k] = buf.numpy()
+
+    def step(self, n):
+        self.fields = np.ascontiguousarray(self.step_fn(self.fields, n))
+
+
+class DeviceSlab:
+    """A slab kept on the rank's GPU: a context of the CUDA library for the
+    local problem, on torch's current stream (so NCCL messages and the
+    plane copies are ordered with the steps).  Ghost planes move as raw
+    planes of the context's layout (storage type, row pitch), one
+    device-to-device copy per species and side."""
+
+    def __init__(self, p: SlabPlan, storage="f32", tuning=None):
+        import torch
+
+        from .sim import Sim
+        self._torch = torch
+        self.plan = p
+        self.storage = storage
+        self.sim = Sim(p.cfg, storage, stream=torch.cuda.current_stream(), tuning=tuning)
+        self.S = p.cfg["nspecies"]
+        self.pb = self.sim.plane_bytes
+
+    def set_fields(self, fields_local):
+        self.sim.set_fields(fields_local)
+
+    def empty(self, k):
+        return self._torch.empty(self.S * k * self.pb, dtype=self._torch.uint8, device="cuda")
+
+    def read(self, z0, k):
+        buf = self.empty(k)
+        n = k * self.pb
+        for s in range(self.S):
+            self.sim.copy_planes(s, z0, k, buf[s * n:(s + 1) * n], to_buf=True)
+        return buf
+
+    def write(self, z0, k, buf):
+        n = k * self.pb
+        for s in range(self.S):
+            self.sim.copy_planes(s, z0, k, buf[s * n:(s + 1) * n], to_buf=False)
+
+    def step(self, n):
+        self.sim.step(n)
+
+    def owned_fields(self):
+        return self.sim.get_fields()[:, self.plan.owned]
+
+    def moments(self, s):
+        """FP64 (sum, sum of squares, non-finite count) of species ``s`` over
+        the owned planes (the library's allocation-free reduction on a copy
+        of those planes)."""
+        import ctypes
+
+        from . import _lib as L
+        p = self.plan
+        k = p.z1 - p.z0
+        nx, ny, _ = p.cfg["shape"]
+        buf = self.empty(k)
+        self.sim.copy_planes(s, p.owned.start, k, buf, to_buf=True)
+        out = self._torch.zeros(3, dtype=self._torch.float64, device="cuda")
+        eb = 2 if self.storage == "bf16" else 4
+        st = self.sim.lib.rd_moments_noalloc(
+            ctypes.c_void_p(buf.data_ptr()), L.STORAGE[self.storage], nx, ny, k,
+            self.pb // (ny * eb), ctypes.c_void_p(out.data_ptr()),
+            ctypes.c_void_p(self._torch.cuda.current_stream().cuda_stream))
+        L.check(st, None, "rd_moments_noalloc")
+        return out
+
+    def close(self):
+        self.sim.close()
+
+
+def owned_moments(slab, s, dist=None):
+    """The whole grid's FP64 moments of species ``s``: each rank's owned
+    planes, summed over ranks by an FP64 all-reduce."""
+    out = slab.moments(s)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(out)
+    return out
+
+
+def run(fields_local, p: SlabPlan, nsteps: int, step_fn, dist, torch=None):
+    """Advance a host slab (float arrays, ghost planes included, stepped by
+    ``step_fn``) by ``nsteps`` steps; returns the new local fields."""
+    slab = HostSlab(fields_local, step_fn)
+    run_slab(slab, p, nsteps, dist)
+    return slab.fields

@@ -102,3 +102,59 @@ def test_split_and_plan_host_logic():
         Z.plan(W.air((8, 8, 8), src=(1, 1, 1)), 2, 0)  # logarithmic wind
     with pytest.raises(ValueError):
         Z.plan(W.ch_front(shape=(8, 8, 5)), 3, 0)      # a slab thinner than the halo
+
+
+def _rank_moments(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    import oracle
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        cfg = CASES["ch_front"]
+        p = Z.plan(cfg, ws, rank)
+        slab = Z.HostSlab(Z.scatter(W.initial_fields(cfg).astype(np.float64), p),
+                          lambda g, n, c=p.cfg: oracle.run(c, g, n), p)
+        Z.run_slab(slab, p, STEPS, dist)
+        out[rank] = [Z.owned_moments(slab, s, dist).numpy() for s in range(3)]
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(240)
+def test_owned_moments_are_all_reduced_in_fp64(orc):
+    # every rank ends with the whole grid's moments: the FP64 sums of its
+    # owned planes, added over the ranks by an all-reduce
+    ws = 3
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_rank_moments, args=(r, ws, port, out)) for r in range(ws)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(200)
+            assert p.exitcode == 0
+        res = dict(out)
+    cfg = CASES["ch_front"]
+    ref = orc.run(cfg, W.initial_fields(cfg).astype(np.float64), STEPS)
+    for s in range(3):
+        want = np.array([ref[s].sum(), (ref[s] ** 2).sum(), 0.0])
+        for r in range(ws):
+            np.testing.assert_allclose(res[r][s], want, rtol=1e-12, atol=1e-12)
+
+
+def test_messages_pair_up():
+    # every send has the matching receive on its peer (same tag, same size)
+    for cfg in CASES.values():
+        for ws in (2, 3, 4):
+            try:
+                plans = [Z.plan(cfg, ws, r) for r in range(ws)]
+            except ValueError:
+                continue
+            sends = {(r, peer, tag): k for r, p in enumerate(plans)
+                     for peer, tag, _, k in Z.messages(p)[0]}
+            recvs = {(peer, r, tag): k for r, p in enumerate(plans)
+                     for peer, tag, _, k in Z.messages(p)[1]}
+            assert sends == recvs
