@@ -283,7 +283,7 @@ class DeviceSlab:
         p = self.plan
         k = p.z1 - p.z0
         nx, ny, _ = p.cfg["shape"]
-        buf = self.empty(k)
+        buf = self._torch.empty(k * self.pb, dtype=self._torch.uint8, device="cuda")
         self.sim.copy_planes(s, p.owned.start, k, buf, to_buf=True)
         out = self._torch.zeros(3, dtype=self._torch.float64, device="cuda")
         eb = 2 if self.storage == "bf16" else 4
