@@ -39,6 +39,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE_FILE = os.path.join(ROOT, "profiles", "rd_step_brusselator_256.md")
 WORKLOAD = "brusselator_256^3_periodic_10000_steps"
 KERNEL_SOURCES = ["paper_1004_0480_gb300/csrc/rd_step_kernel.cuh",
+                  "paper_1004_0480_gb300/csrc/rd_step1w_kernel.cuh",
+                  "paper_1004_0480_gb300/csrc/rd_debug.cuh",
                   "paper_1004_0480_gb300/csrc/rd_k_brusselator.cu",
                   "paper_1004_0480_gb300/csrc/rd_internal.h"]
 
@@ -284,9 +286,7 @@ def run_ours(args, ws, rank, local):
     sim = Sim(cfg, stream=stream)
     sim.set_fields(f)
     if args.tuning:
-        vals = [int(x) for x in args.tuning.split(",")]
-        sim.set_tuning(tsteps=vals[0], tile_y=vals[1], zchunk=vals[2],
-                       regcap=vals[3] if len(vals) > 3 else 0)
+        sim.set_tuning(**parse_tuning(args.tuning))
         tun = sim.tuning()
     else:
         tun = sim.autotune()
@@ -419,25 +419,39 @@ def run_ours(args, ws, rank, local):
 
 
 PROFILE_WORKLOADS = {
-    "air_512x512x64": lambda: W.cfg_air_512(),
-    "ch_front_256": lambda: W.ch_front(256),
-    "brusselator_256_19pt": lambda: W.cfg_brusselator_256_19pt(),
+    # name: (problem, storage)
+    "air_512x512x64": (lambda: W.cfg_air_512(), "f32"),
+    "ch_front_256": (lambda: W.ch_front(256), "f32"),
+    "brusselator_256_19pt": (lambda: W.cfg_brusselator_256_19pt(), "f32"),
+    "brusselator_256_bf16": (lambda: W.cfg_brusselator_256(), "bf16"),
+    "ch_table1_192_19pt": (lambda: W.ch_table1(192), "f32"),
+    "plume_144x144x384_19pt": (lambda: W.with_(W.plume(), stencil=19), "f32"),
 }
+
+
+def parse_tuning(text):
+    """--tuning 'tsteps,tile_y,zchunk[,regcap[,tile_q]]' as rd_tuning fields."""
+    vals = [int(x) for x in text.split(",")]
+    t = dict(tsteps=vals[0], tile_y=vals[1], zchunk=vals[2],
+             regcap=vals[3] if len(vals) > 3 else 0)
+    if len(vals) > 4:
+        t["tile_q"] = vals[4]
+    return t
 
 
 def profile_other(args, Sim, torch):
     """A few single launches of another workload's step kernel (for ncu):
     the problem with the given tuning, two warm-up steps, then ``--profile``
     single-step calls, no graph."""
-    cfg = PROFILE_WORKLOADS[args.profile_workload]()
-    vals = [int(x) for x in args.tuning.split(",")]
-    with Sim(cfg) as sim:
+    mk, storage = PROFILE_WORKLOADS[args.profile_workload]
+    cfg = mk()
+    tun = parse_tuning(args.tuning)
+    with Sim(cfg, storage) as sim:
         sim.set_fields(W.initial_fields_torch(cfg, "cuda"))
-        sim.set_tuning(tsteps=vals[0], tile_y=vals[1], zchunk=vals[2],
-                       regcap=vals[3] if len(vals) > 3 else 0, graph=0)
+        sim.set_tuning(graph=0, **tun)
         sim.step(2)
         for _ in range(args.profile):
-            sim.step(vals[0])
+            sim.step(tun["tsteps"])
         sim.sync()
     return 0
 
@@ -748,7 +762,8 @@ def main():
     ap.add_argument("--job-steps", type=int, default=0,
                     help="time steps per job (default: the workload's 10 000)")
     ap.add_argument("--tuning", default="",
-                    help="fixed tuning 'tsteps,tile_y,zchunk[,regcap]' instead of the autotuner")
+                    help="fixed tuning 'tsteps,tile_y,zchunk[,regcap[,tile_q]]' instead of the "
+                         "autotuner")
     ap.add_argument("--profile", type=int, default=0,
                     help="only run this many single step-kernel launches (for ncu)")
     ap.add_argument("--profile-workload", default="brusselator_256",
