@@ -560,6 +560,13 @@ def run_extras(args, Sim, Batch, torch):
         tun = sim.autotune()
         t = _timed_steps(torch, sim, 400)
         out["diffusion_512"] = _entry(W.cell_count(cfg), 400, t, 8, tun)
+    # the front model (Cahn-Hilliard) on one 256^3 instance (24 B per cell-step)
+    fcfg = W.ch_front(256)
+    with Sim(fcfg) as sim:
+        sim.set_fields(W.initial_fields_torch(fcfg, "cuda"))
+        tun = sim.autotune()
+        t = _timed_steps(torch, sim, 1000)
+        out["ch_front_256"] = _entry(W.cell_count(fcfg), 1000, t, 24, tun)
     # air 512 x 512 x 64, 3 species (24 B per cell-step)
     cfg = W.cfg_air_512()
     with Sim(cfg) as sim:
@@ -576,6 +583,8 @@ def run_extras(args, Sim, Batch, torch):
         sm.set_fields(W.initial_fields_torch(c, "cuda"))
     stream = torch.cuda.Stream()
     b = Batch("ch_front", stream=stream)
+    # 12-row tiles and 32-plane chunks (measured best for these members:
+    # longer chunks leave fewer items to balance the uneven instances)
     btun = dict(tsteps=1, tile_q=16, tile_y=12, zchunk=32, graph=1)
     b.set_tuning(**btun)
     for sm in sims:

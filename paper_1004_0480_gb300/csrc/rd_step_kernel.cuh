@@ -1285,7 +1285,9 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
         float mu_m[kVEC] = {}, mu_0[kVEC] = {};       // own mu of planes p-1, p
         float cz_m[kVEC] = {}, cz_0[kVEC] = {};       // own c of planes p, p+1
         int sc = 0;                                   // ring slot of plane p
-#pragma unroll 1
+        // unrolled by 3: the three-plane windows of mu and c rotate by
+        // renaming registers instead of moves
+#pragma unroll 3
         for (int p = z0 - 2; p < z1; ++p) {
             // planes through p + 2 must have landed: of the P + (p - z0 + 3)
             // groups issued so far, all but the newest P - 2
