@@ -1226,11 +1226,6 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
     }
     const int own = (r + 1) * kRW + v * kVEC;       // element offset in a plane
     const int own_b = own * EB;
-    // x neighbours of the inner positions by warp shuffle: the inner
-    // positions fill whole warps when 16 TY is a multiple of 32 (even TY);
-    // block-uniform, so an odd TY takes every neighbour from shared memory
-    const bool use_shfl = (ninner & 31) == 0;
-    constexpr unsigned FULL = 0xffffffffu;
 
     int cur_inst = -1;
     if (tid == 0) s_inst = 0;
@@ -1289,7 +1284,6 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
         ST* gst = gout + (long long)z0 * plane + (long long)y * pitch + xs;
         float mu_m[kVEC] = {}, mu_0[kVEC] = {};       // own mu of planes p-1, p
         float cz_m[kVEC] = {}, cz_0[kVEC] = {};       // own c of planes p, p+1
-        float ab_m[2][kVEC], ab_0[2][kVEC];           // own a, b of planes p-1, p
         int sc = 0;                                   // ring slot of plane p
         // unrolled by 3: the three-plane windows of mu and c rotate by
         // renaming registers instead of moves
@@ -1318,18 +1312,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                 lds_vec<ST>(ring + s2 * SLOTB + 2 * PEB + own_b, cz_p);
                 lds_vec<ST>(Cc - RWB, ym);
                 lds_vec<ST>(Cc + RWB, yp);
-                float left, right;
-                if (use_shfl && inner) {
-                    // the lanes beside hold the neighbouring vectors of the
-                    // row; the tile row's end vectors read the halo column
-                    const float lsh = __shfl_up_sync(FULL, c[kVEC - 1], 1);
-                    const float rsh = __shfl_down_sync(FULL, c[0], 1);
-                    left = v == 1 ? lds_one<ST>(Cc - EB) : lsh;
-                    right = v == kTileQ ? lds_one<ST>(Cc + kVEC * EB) : rsh;
-                } else {
-                    left = lds_one<ST>(Cc - EB);
-                    right = lds_one<ST>(Cc + kVEC * EB);
-                }
+                const float left = lds_one<ST>(Cc - EB);
+                const float right = lds_one<ST>(Cc + kVEC * EB);
 #pragma unroll
                 for (int e = 0; e < kVEC; ++e) {
                     const float xm = e ? c[e - 1] : left;
@@ -1344,23 +1328,9 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                 const unsigned char* Sm = ring + sm * SLOTB + own_b;
                 const unsigned char* Sp = ring + s1 * SLOTB + own_b;
                 const unsigned faces = xyf | z_faces(p, nz);
-                // a and b: own vectors of planes p - 1 and p carried down the
-                // march (loaded at the first step), plane p + 1 read now
-                if (p == z0) {
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        lds_vec<ST>(Sm + s * PEB, ab_m[s]);
-                        lds_vec<ST>(Sc + s * PEB, ab_0[s]);
-                    }
-                }
-                float ab_p[2][kVEC];
-#pragma unroll
-                for (int s = 0; s < 2; ++s) lds_vec<ST>(Sp + s * PEB, ab_p[s]);
                 float cen[S][kVEC], inc[S][kVEC];
 #pragma unroll
-                for (int s = 0; s < 2; ++s)
-#pragma unroll
-                    for (int e = 0; e < kVEC; ++e) cen[s][e] = ab_0[s][e];
+                for (int s = 0; s < 2; ++s) lds_vec<ST>(Sc + s * PEB, cen[s]);
 #pragma unroll
                 for (int e = 0; e < kVEC; ++e) cen[2][e] = cz_m[e];   // c of plane p, carried
 #pragma unroll
@@ -1377,21 +1347,13 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const unsigned char* Ps = Sc + s * PEB;
-                    float xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], o[kVEC];
-                    const float(&zm)[kVEC] = ab_m[s];
-                    const float(&zp)[kVEC] = ab_p[s];
+                    float xm[kVEC], xp[kVEC], ym[kVEC], yp[kVEC], zm[kVEC], zp[kVEC], o[kVEC];
+                    lds_vec<ST>(Sm + s * PEB, zm);
+                    lds_vec<ST>(Sp + s * PEB, zp);
                     lds_vec<ST>(Ps - RWB, ym);
                     lds_vec<ST>(Ps + RWB, yp);
-                    float left, right;
-                    if (use_shfl) {
-                        const float lsh = __shfl_up_sync(FULL, cen[s][kVEC - 1], 1);
-                        const float rsh = __shfl_down_sync(FULL, cen[s][0], 1);
-                        left = v == 1 ? lds_one<ST>(Ps - EB) : lsh;
-                        right = v == kTileQ ? lds_one<ST>(Ps + kVEC * EB) : rsh;
-                    } else {
-                        left = lds_one<ST>(Ps - EB);
-                        right = lds_one<ST>(Ps + kVEC * EB);
-                    }
+                    const float left = lds_one<ST>(Ps - EB);
+                    const float right = lds_one<ST>(Ps + kVEC * EB);
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e) {
                         xm[e] = e ? cen[s][e - 1] : left;
@@ -1419,16 +1381,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                     float mym[kVEC], myp[kVEC], o[kVEC];
                     Store<float>::load(Mc - kRW, mym);
                     Store<float>::load(Mc + kRW, myp);
-                    float mleft, mright;
-                    if (use_shfl) {
-                        const float lsh = __shfl_up_sync(FULL, mu_0[kVEC - 1], 1);
-                        const float rsh = __shfl_down_sync(FULL, mu_0[0], 1);
-                        mleft = v == 1 ? Store<float>::get(Mc - 1) : lsh;
-                        mright = v == kTileQ ? Store<float>::get(Mc + kVEC) : rsh;
-                    } else {
-                        mleft = Store<float>::get(Mc - 1);
-                        mright = Store<float>::get(Mc + kVEC);
-                    }
+                    const float mleft = Store<float>::get(Mc - 1);
+                    const float mright = Store<float>::get(Mc + kVEC);
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e) {
                         const float mxm = e ? mu_0[e - 1] : mleft;
@@ -1443,13 +1397,6 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                         RD_DBG_GLOBAL(sd, gst + 2 * fstride, 4 * (int)sizeof(ST), kSiteStateStore))
                         Store<ST>::store(gst + 2 * fstride, o);
                 }
-#pragma unroll
-                for (int s = 0; s < 2; ++s)
-#pragma unroll
-                    for (int e = 0; e < kVEC; ++e) {
-                        ab_m[s][e] = ab_0[s][e];
-                        ab_0[s][e] = ab_p[s][e];
-                    }
             }
             if (p >= z0) gst += plane;
 #pragma unroll
