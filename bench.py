@@ -553,6 +553,16 @@ def run_extras(args, Sim, Batch, torch):
         t = _timed_steps(torch, sim, cfg["steps"], reps=5)
         out["diffusion_64"] = _entry(W.cell_count(cfg), cfg["steps"], t, 8, tun,
                                      note="1 MiB per level: L2-resident, launch-bound")
+    # the same run with the resident kernel: one cooperative launch for the
+    # 100 steps, a grid-wide barrier between steps (same bits as above)
+    with Sim(cfg) as sim:
+        sim.set_fields(W.initial_fields(cfg))
+        sim.set_kernel("resident")
+        t = _timed_steps(torch, sim, cfg["steps"], reps=5)
+        out["diffusion_64_resident"] = _entry(W.cell_count(cfg), cfg["steps"], t, 8,
+                                              kernel="resident", plan=sim.resident_plan(),
+                                              note="one launch for the 100 steps, K steps "
+                                                   "per grid barrier, state in L2")
     # the same kinetics at 512^3 (1 GiB per level) for the HBM roofline
     cfg = W.diffusion_blob(512, steps=400, dt=0.1)
     with Sim(cfg) as sim:

@@ -314,14 +314,49 @@ rd_status rd_autotune(rd_ctx* ctx, rd_tuning* best);
  * Cahn-Hilliard and no held layer, point source or wind (else
  * RD_EUNSUPPORTED); they ignore rd_tuning except `graph`, and rd_autotune
  * refuses them (RD_EUNSUPPORTED).  Results agree with the march kernel to
- * rounding (other summation order), not bit for bit. */
+ * rounding (other summation order), not bit for bit.
+ *   RD_KERNEL_RESIDENT  for small grids whose state stays in L2 (the 64^3
+ *                     problems): one cooperative launch advances up to
+ *                     65536 steps (rd_step splits longer runs).  Each CTA
+ *                     owns tiles of full x rows; a round copies a tile with
+ *                     a halo of K rows and planes into shared memory,
+ *                     advances it K steps there (K <= 4, see
+ *                     rd_set_resident_plan) and writes the tile's rows; a
+ *                     grid-wide barrier separates rounds.  Every level is
+ *                     eq. (5) with the march kernel's per-cell arithmetic
+ *                     and neighbour values, rounded to the state's type, so
+ *                     results equal the march kernel's bit for bit.  Needs
+ *                     the 7-point stencil, a model without Cahn-Hilliard, no
+ *                     3-D wind, and rows that fit shared memory with a
+ *                     one-row tile (else RD_EUNSUPPORTED); FP32 or BF16
+ *                     state; rd_tuning is ignored and rd_autotune refuses
+ *                     it.  Every barrier wait is bounded (about 0.2 s): a
+ *                     wait that runs out stops the launch, and the next
+ *                     rd_sync (or rd_batch_sync of a batch of one) returns
+ *                     RD_ETIMEOUT.  After rd_step the current level holds
+ *                     the result; the other level need not hold the step
+ *                     before it.
+ * A batch of two or more members steps them with the march kernel whatever
+ * their own kernel. */
 typedef enum rd_kernel {
     RD_KERNEL_MARCH = 0,
     RD_KERNEL_SHARED = 1,
-    RD_KERNEL_TILES = 2
+    RD_KERNEL_TILES = 2,
+    RD_KERNEL_RESIDENT = 3
 } rd_kernel;
 rd_status rd_set_kernel(rd_ctx* ctx, int32_t kernel);
 int32_t rd_get_kernel(const rd_ctx* ctx);   /* -1 for a NULL context */
+
+/* Plan of the resident kernel: K steps per round (1..4) and tiles of
+ * tile_y rows by tile_z planes (clamped to the grid); 0 leaves a choice to
+ * the library's cost model (the default for all three).  The choice is kept
+ * for later rd_set_kernel(RD_KERNEL_RESIDENT) calls.  RD_EUNSUPPORTED
+ * unless the context's kernel is RD_KERNEL_RESIDENT; RD_EINVAL for values
+ * out of range or a tile whose rows and halo do not fit shared memory (the
+ * previous plan stays).  rd_get_resident_plan writes out[0..6] = K, tile_y,
+ * tile_z, tiles, CTAs, threads per CTA, shared memory bytes per CTA. */
+rd_status rd_set_resident_plan(rd_ctx* ctx, int32_t K, int32_t tile_y, int32_t tile_z);
+rd_status rd_get_resident_plan(const rd_ctx* ctx, int32_t out[7]);
 
 /* Launch statistics: kernels this context enqueued since creation. */
 int64_t rd_launch_count(const rd_ctx* ctx);
@@ -339,8 +374,8 @@ const char* rd_last_error(const rd_ctx* ctx);
  * is recorded in a device word: bit 63 set, bits 40..55 a site code (1
  * shared load, 2 shared store, 3 copy destination, 4 copy source, 5 state
  * store, 6 Courant table or step counter, 7 mu field, 8 halo descriptors,
- * 0xFFFF the self-test), bits 0..39 the byte offset from the start of the
- * window missed.  rd_sync and rd_batch_sync then return RD_EBOUNDS (and
+ * 9 state load of the resident kernel, 0xFFFF the self-test), bits 0..39
+ * the byte offset from the start of the window missed.  rd_sync and rd_batch_sync then return RD_EBOUNDS (and
  * clear the word), with the site and offset in rd_last_error.
  *   op 0: *word = the word; 1: the same, then clear it; 2: launch a
  *   self-test kernel that records a violation at site 0xFFFF without
@@ -355,6 +390,16 @@ rd_status rd_debug_bounds(uint64_t* word, int32_t op);
  * The call that meets the failure returns RD_ENOMEM and frees what it had
  * obtained.  RD_EINVAL for k < 0. */
 rd_status rd_debug_fail_alloc(int64_t k);
+
+/* Testing hook for the resident kernel's bounded barrier waits (the paper
+ * has no counterpart): the context's next resident launch of more than one
+ * round (more steps than the plan's K) counts `phantom` (> 0) CTAs that
+ * never arrive, so its first grid barrier wait runs out after about 0.2 s;
+ * every CTA then leaves after the launch's first round, so the state is not
+ * the one asked for, and the next rd_sync returns RD_ETIMEOUT.  Only that launch is affected; 0 disarms.
+ * RD_EINVAL for a null context or phantom < 0, RD_EUNSUPPORTED unless the
+ * context's kernel is RD_KERNEL_RESIDENT. */
+rd_status rd_debug_resident_stall(rd_ctx* ctx, int32_t phantom);
 
 /* FP64 moments of one field held anywhere in device memory, for callers
  * that must not allocate device memory at that point: code that is

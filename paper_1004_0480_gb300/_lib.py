@@ -16,7 +16,7 @@ MODEL = {"diffusion": 0, "brusselator": 1, "ch_front": 2, "air": 3, "turing": 4,
          "ch_table1": 5}
 STORAGE = {"f32": 0, "bf16": 1}
 WIND = {None: 0, "log": 1, "const": 2, "3d": 3}
-KERNEL = {"march": 0, "shared": 1, "tiles": 2}
+KERNEL = {"march": 0, "shared": 1, "tiles": 2, "resident": 3}
 FLAG_NO_ALLOC, FLAG_FORCE = 1, 2
 
 
@@ -94,6 +94,9 @@ SIGNATURES = {
     "rd_batch_launch_count": (_I64, [_P]),
     "rd_moments_noalloc": (_I, [_P, _I32, _I32, _I32, _I32, _I64, _P, _P]),
     "rd_debug_fail_alloc": (_I, [_I64]),
+    "rd_debug_resident_stall": (_I, [_P, _I32]),
+    "rd_set_resident_plan": (_I, [_P, _I32, _I32, _I32]),
+    "rd_get_resident_plan": (_I, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "rd_plane_bytes": (_SZ, [_P]),
     "rd_copy_planes": (_I, [_P, _I, _I, _I, _P, _SZ, _I32]),
     "rd_debug_bounds": (_I, [ctypes.POINTER(ctypes.c_uint64), _I32]),

@@ -24,6 +24,7 @@
 #include "rd_internal.h"
 #include "rd_ablation.h"
 #include "rd_model_turing.h"
+#include "rd_resident.h"
 #include "rd_step19.h"
 
 using namespace rdk;
@@ -241,6 +242,10 @@ struct rd_ctx {
     float* courant = nullptr;      // u(z) dt / h per plane
     float* mu = nullptr;           // 19-point Cahn-Hilliard: the mu field
     long long* stepn = nullptr;    // 3-D wind: step index per time level
+    rdk::ResidentBar* bar = nullptr;   // the resident kernel's grid barrier
+    int res_phantom = 0;           // rd_debug_resident_stall, next launch only
+    rdk::ResidentPlan res_plan{};  // the resident kernel's plan (rd_set_kernel)
+    int res_force[3] = {0, 0, 0};  // rd_set_resident_plan: K, ty, tz (0 = planned)
     bool stepn_dirty = true;       // the host's step count is not on the device
     int cur = 0;                   // current time level
     cudaStream_t stream = nullptr;
@@ -444,7 +449,7 @@ void layout(rd_ctx* c) {
     const size_t res = 256;
     const size_t desc = align_up(sizeof(InstDesc), 256);
     const size_t cour = align_up((size_t)g.nz * sizeof(float), 256);
-    c->scratch_bytes = dense + part + res + desc + cour + 256 + mu_bytes(c);
+    c->scratch_bytes = dense + part + res + desc + cour + 256 + 256 + mu_bytes(c);
 }
 
 void carve(rd_ctx* c) {
@@ -461,6 +466,8 @@ void carve(rd_ctx* c) {
     c->courant = reinterpret_cast<float*>(p);
     p += align_up((size_t)g.nz * sizeof(float), 256);
     c->stepn = g.wind_kind == RD_WIND_3D ? reinterpret_cast<long long*>(p) : nullptr;
+    p += 256;
+    c->bar = reinterpret_cast<rdk::ResidentBar*>(p);
     p += 256;
     c->mu = mu_bytes(c) ? reinterpret_cast<float*>(p) : nullptr;
 }
@@ -676,6 +683,7 @@ rd_status finish_setup(rd_ctx* c) {
     carve(c);
     RD_CUDA(c, cudaMemsetAsync(c->state, 0, c->state_bytes, c->stream));
     if (c->stepn) RD_CUDA(c, cudaMemsetAsync(c->stepn, 0, 2 * sizeof(long long), c->stream));
+    RD_CUDA(c, cudaMemsetAsync(c->bar, 0, sizeof(rdk::ResidentBar), c->stream));
     RD_CUDA(c, cudaStreamSynchronize(c->stream));
     rd_status st = write_courant(c);
     if (st != RD_OK) return st;
@@ -697,6 +705,18 @@ rd_status launch_ctx(rd_ctx* c, int T, int parity, cudaStream_t st) {
     a.wind3 = c->cfg.wind_kind == RD_WIND_3D;
     a.vw = vw_of(c->tun.tile_q);
     a.ty = c->tun.tile_y;
+    if (c->kernel == RD_KERNEL_RESIDENT) {
+        // T steps in one cooperative launch (zeroed barrier count and word)
+        RD_CUDA(c, cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st));
+        const bool barriers = T > c->res_plan.K;
+        const unsigned phantom = barriers ? (unsigned)c->res_phantom : 0u;
+        if (barriers) c->res_phantom = 0;
+        cudaError_t e = launch_resident(c->cfg.model, c->cfg.storage, a, c->res_plan, T, c->bar,
+                                        phantom, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "resident kernel launch");
+        c->launches++;
+        return RD_OK;
+    }
     if (c->kernel != RD_KERNEL_MARCH) {   // the paper's designs, one step each
         if (T != 1) return fail(c, RD_EINVAL, "the ablation kernels step once per launch");
         cudaError_t e = launch_ablation(c->kernel, c->cfg.model, a, st);
@@ -766,6 +786,18 @@ rd_status step_ctx(rd_ctx* c, int64_t n) {
     rd_status st = upload_desc(c);
     if (st != RD_OK) return st;
     if ((st = sync_stepn(c, c->stream)) != RD_OK) return st;
+    if (c->kernel == RD_KERNEL_RESIDENT) {   // many steps per launch, no graph
+        for (int64_t left = n; left > 0;) {
+            const int k = (int)std::min<int64_t>(left, rdk::kResidentMaxSteps);
+            if ((st = launch_ctx(c, k, c->cur, c->stream)) != RD_OK) return st;
+            // each round of K steps is one transition between the levels
+            const int rounds = (k + c->res_plan.K - 1) / c->res_plan.K;
+            c->cur ^= rounds & 1;
+            left -= k;
+        }
+        c->steps += n;
+        return RD_OK;
+    }
     const int T = c->tun.tsteps;
     int64_t full = n / T;
     const int rem = (int)(n % T);
@@ -1053,10 +1085,25 @@ static rd_status bounds_status(rd_ctx* c) {
                 (int)((w >> 40) & 0xFFFF), off);
 }
 
+// A resident launch whose grid barrier timed out since the last check
+// (RD_ETIMEOUT; the flag is cleared).  Only contexts that use the kernel
+// pay the read.
+static rd_status resident_status(rd_ctx* c) {
+    if (c->kernel != RD_KERNEL_RESIDENT || !c->bar) return RD_OK;
+    unsigned failed = 0;
+    RD_CUDA(c, cudaMemcpy(&failed, &c->bar->failed, sizeof(failed), cudaMemcpyDeviceToHost));
+    if (!failed) return RD_OK;
+    RD_CUDA(c, cudaMemset(&c->bar->failed, 0, sizeof(unsigned)));
+    return fail(c, RD_ETIMEOUT, "resident kernel: a grid barrier wait ran out; the steps of "
+                                "that launch are incomplete");
+}
+
 rd_status rd_sync(rd_ctx* c) {
     if (!c) return RD_EINVAL;
     drain_batch(c);
     RD_CUDA(c, cudaStreamSynchronize(c->stream));
+    rd_status st = resident_status(c);
+    if (st != RD_OK) return st;
     return bounds_status(c);
 }
 
@@ -1093,9 +1140,24 @@ rd_status rd_get_tuning(const rd_ctx* c, rd_tuning* out) {
 
 rd_status rd_set_kernel(rd_ctx* c, int32_t kernel) {
     if (!c) return fail(nullptr, RD_EINVAL, "null context");
-    if (kernel < RD_KERNEL_MARCH || kernel > RD_KERNEL_TILES)
+    if (kernel < RD_KERNEL_MARCH || kernel > RD_KERNEL_RESIDENT)
         return fail(c, RD_EINVAL, "unknown kernel %d", kernel);
-    if (kernel != RD_KERNEL_MARCH) {
+    if (kernel == RD_KERNEL_RESIDENT) {
+        const rd_config& g = c->cfg;
+        if (stencil_of(g) != 7 || is_ch(g.model) || g.wind_kind == RD_WIND_3D)
+            return fail(c, RD_EUNSUPPORTED,
+                        "the resident kernel needs the 7-point stencil, a model without "
+                        "Cahn-Hilliard and no 3-D wind");
+        rdk::ResidentPlan plan{};
+        const cudaError_t e = rdk::plan_resident(g.model, g.storage, plain_problem(g), g.nx,
+                                                 g.ny, g.nz, c->res_force[0],
+                                                 c->res_force[1], c->res_force[2], &plan);
+        if (e == cudaErrorInvalidValue)
+            return fail(c, RD_EUNSUPPORTED,
+                        "the resident kernel's rows do not fit shared memory (nx = %d)", g.nx);
+        if (e != cudaSuccess) return cuda_fail(c, e, "resident plan");
+        c->res_plan = plan;
+    } else if (kernel != RD_KERNEL_MARCH) {
         const rd_config& g = c->cfg;
         if (stencil_of(g) != 19 || g.storage != RD_STORE_F32 || is_ch(g.model) ||
             !plain_problem(g))
@@ -1261,6 +1323,49 @@ const char* rd_status_str(rd_status st) {
 }
 
 const char* rd_last_error(const rd_ctx* c) { return c ? c->err : g_err; }
+
+rd_status rd_set_resident_plan(rd_ctx* c, int32_t K, int32_t tile_y, int32_t tile_z) {
+    if (!c) return fail(nullptr, RD_EINVAL, "null context");
+    if (c->kernel != RD_KERNEL_RESIDENT)
+        return fail(c, RD_EUNSUPPORTED, "the context's kernel is not the resident kernel");
+    if (K < 0 || K > rdk::kResidentMaxK || tile_y < 0 || tile_z < 0)
+        return fail(c, RD_EINVAL, "plan out of range: K %d, tile %d x %d", K, tile_y, tile_z);
+    const rd_config& g = c->cfg;
+    rdk::ResidentPlan plan{};
+    const cudaError_t e = rdk::plan_resident(g.model, g.storage, plain_problem(g), g.nx, g.ny,
+                                             g.nz, K, tile_y, tile_z, &plan);
+    if (e == cudaErrorInvalidValue)
+        return fail(c, RD_EINVAL, "K %d with a %d x %d tile does not fit shared memory", K,
+                    tile_y, tile_z);
+    if (e != cudaSuccess) return cuda_fail(c, e, "resident plan");
+    c->res_force[0] = K;
+    c->res_force[1] = tile_y;
+    c->res_force[2] = tile_z;
+    c->res_plan = plan;
+    return RD_OK;
+}
+
+rd_status rd_get_resident_plan(const rd_ctx* c, int32_t out[7]) {
+    if (!c || !out) return RD_EINVAL;
+    if (c->kernel != RD_KERNEL_RESIDENT) return RD_EUNSUPPORTED;
+    const rdk::ResidentPlan& p = c->res_plan;
+    out[0] = p.K;
+    out[1] = p.ty;
+    out[2] = p.tz;
+    out[3] = p.nty * p.ntz;
+    out[4] = p.grid;
+    out[5] = p.threads;
+    out[6] = p.smem;
+    return RD_OK;
+}
+
+rd_status rd_debug_resident_stall(rd_ctx* c, int32_t phantom) {
+    if (!c || phantom < 0) return fail(c, RD_EINVAL, "bad argument");
+    if (c->kernel != RD_KERNEL_RESIDENT)
+        return fail(c, RD_EUNSUPPORTED, "the context's kernel is not the resident kernel");
+    c->res_phantom = phantom;
+    return RD_OK;
+}
 
 rd_status rd_debug_fail_alloc(int64_t k) {
     if (k < 0) return RD_EINVAL;
@@ -1511,6 +1616,10 @@ rd_status rd_batch_sync(rd_batch* b) {
     if (!b) return RD_EINVAL;
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch sync");
+    if (b->members.size() == 1) {   // a batch of one steps with its member's kernel
+        rd_status st = resident_status(b->members[0]);
+        if (st != RD_OK) return st;
+    }
     return bounds_status(nullptr);
 }
 

@@ -27,6 +27,7 @@ enum DbgSite : int {
     kSiteTable = 6,          // the Courant table or the step counter
     kSiteMu = 7,             // the mu field (19-point Cahn-Hilliard)
     kSiteHaloDesc = 8,       // the halo fetch descriptors
+    kSiteStateLoad = 9,      // a direct load of state (resident kernel)
     kSiteSelfTest = 0xFFFF   // rd_debug_bounds' self-test
 };
 

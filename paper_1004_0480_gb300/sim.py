@@ -222,9 +222,23 @@ class Sim:
         self._check(self.lib.rd_set_tuning(self.ctx, ctypes.byref(t)), "rd_set_tuning")
 
     def set_kernel(self, name):
-        """Step kernel: "march" (default), or the paper's "shared" / "tiles"
-        designs (ablation baselines; 19-point stencil, FP32, plain problems)."""
+        """Step kernel: "march" (default), the paper's "shared" / "tiles"
+        designs (ablation baselines; 19-point stencil, FP32, plain problems),
+        or "resident" (many steps per cooperative launch for small grids held
+        in L2; 7-point, no Cahn-Hilliard, no 3-D wind; same bits as march)."""
         self._check(self.lib.rd_set_kernel(self.ctx, L.KERNEL[name]), "rd_set_kernel")
+
+    def set_resident_plan(self, K=0, tile_y=0, tile_z=0):
+        """Resident kernel: K steps per round and tile_y x tile_z tiles
+        (0 = the library's choice)."""
+        self._check(self.lib.rd_set_resident_plan(self.ctx, K, tile_y, tile_z),
+                    "rd_set_resident_plan")
+
+    def resident_plan(self):
+        out = (ctypes.c_int32 * 7)()
+        self._check(self.lib.rd_get_resident_plan(self.ctx, out), "rd_get_resident_plan")
+        return dict(zip(("K", "tile_y", "tile_z", "tiles", "ctas", "threads", "smem"),
+                        list(out)))
 
     @property
     def kernel(self):
