@@ -419,7 +419,8 @@ def run_ours(args, ws, rank, local):
 
 
 PROFILE_WORKLOADS = {
-    # name: (problem, storage)
+    # name: (problem, storage); the resident workload takes no --tuning
+    "diffusion_64_resident": (lambda: W.cfg_diffusion_64(), "f32"),
     "air_512x512x64": (lambda: W.cfg_air_512(), "f32"),
     "ch_front_256": (lambda: W.ch_front(256), "f32"),
     "brusselator_256_19pt": (lambda: W.cfg_brusselator_256_19pt(), "f32"),
@@ -442,9 +443,19 @@ def parse_tuning(text):
 def profile_other(args, Sim, torch):
     """A few single launches of another workload's step kernel (for ncu):
     the problem with the given tuning, two warm-up steps, then ``--profile``
-    single-step calls, no graph."""
+    single-step calls, no graph.  The resident workload instead runs its
+    whole job (one launch) ``--profile`` times with the library's plan."""
     mk, storage = PROFILE_WORKLOADS[args.profile_workload]
     cfg = mk()
+    if args.profile_workload.endswith("_resident"):
+        with Sim(cfg, storage) as sim:
+            sim.set_fields(W.initial_fields_torch(cfg, "cuda"))
+            sim.set_kernel("resident")
+            for _ in range(args.profile):
+                sim.step(cfg["steps"])
+            sim.sync()
+            print(json.dumps({"plan": sim.resident_plan()}), flush=True)
+        return 0
     tun = parse_tuning(args.tuning)
     with Sim(cfg, storage) as sim:
         sim.set_fields(W.initial_fields_torch(cfg, "cuda"))
