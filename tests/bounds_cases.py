@@ -20,7 +20,8 @@ SHAPE = (70, 21, 13)         # two x-tiles (ragged), ragged y tiles and z chunks
 
 
 def cases():
-    """name -> (problem, storage, tuning, steps)"""
+    """name -> (problem, storage, tuning, steps); a tuning with "kernel":
+    "resident" selects the resident kernel with the plan under "plan"."""
     per_b = W.brusselator(shape=(67, 18, 11))
     t1 = dict(tsteps=1, tile_y=6, zchunk=5, graph=0)
     out = {
@@ -41,6 +42,12 @@ def cases():
                              init="uniform_noise"), "f32", t1, 6),
         "plume_7": (W.with_(W.plume(shape=SHAPE, src=(30, 10, 6)), init="uniform_noise"),
                     "f32", dict(t1, graph=1), 20),
+        "resident_diffusion": (W.diffusion_blob(shape=SHAPE), "f32",
+                               dict(kernel="resident", plan=(3, 4, 5)), 13),
+        "resident_brusselator_periodic": (per_b, "f32",
+                                          dict(kernel="resident", plan=(4, 5, 3)), 11),
+        "resident_air_bf16": (W.air(SHAPE, src=(9, 4, 3)), "bf16",
+                              dict(kernel="resident", plan=(2, 3, 2)), 9),
     }
     return out
 
@@ -55,7 +62,11 @@ def main(path):
     from paper_1004_0480_gb300.sim import Batch, Sim
     res = {}
     for name, (cfg, storage, tun, steps) in cases().items():
-        with Sim(cfg, storage, tuning=tun) as sim:
+        resident = tun.get("kernel") == "resident"
+        with Sim(cfg, storage, tuning=None if resident else tun) as sim:
+            if resident:
+                sim.set_kernel("resident")
+                sim.set_resident_plan(*tun["plan"])
             sim.set_fields(W.initial_fields(cfg))
             sim.step(steps)
             res[f"status_{name}"] = np.array(L.load().rd_sync(sim.ctx))
