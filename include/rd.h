@@ -319,7 +319,9 @@ rd_status rd_autotune(rd_ctx* ctx, rd_tuning* best);
  *                     problems): one cooperative launch advances up to
  *                     65536 steps (rd_step splits longer runs).  Each CTA
  *                     owns tiles of full x rows; a round copies a tile with
- *                     a halo of K rows and planes into shared memory,
+ *                     a halo of K rows and planes into shared memory (one
+ *                     tensor-memory box per tile where y and z are not
+ *                     periodic),
  *                     advances it K steps there (K <= 4, see
  *                     rd_set_resident_plan) and writes the tile's rows; a
  *                     grid-wide barrier separates rounds.  Every level is
@@ -353,10 +355,12 @@ int32_t rd_get_kernel(const rd_ctx* ctx);   /* -1 for a NULL context */
  * for later rd_set_kernel(RD_KERNEL_RESIDENT) calls.  RD_EUNSUPPORTED
  * unless the context's kernel is RD_KERNEL_RESIDENT; RD_EINVAL for values
  * out of range or a tile whose rows and halo do not fit shared memory (the
- * previous plan stays).  rd_get_resident_plan writes out[0..6] = K, tile_y,
- * tile_z, tiles, CTAs, threads per CTA, shared memory bytes per CTA. */
+ * previous plan stays).  rd_get_resident_plan writes out[0..7] = K, tile_y,
+ * tile_z, tiles, CTAs, threads per CTA, shared memory bytes per CTA, and 1
+ * if tiles arrive as tensor-memory (TMA) boxes (y and z not periodic, rows
+ * of at most 256 elements; else per-thread copies, 0). */
 rd_status rd_set_resident_plan(rd_ctx* ctx, int32_t K, int32_t tile_y, int32_t tile_z);
-rd_status rd_get_resident_plan(const rd_ctx* ctx, int32_t out[7]);
+rd_status rd_get_resident_plan(const rd_ctx* ctx, int32_t out[8]);
 
 /* Launch statistics: kernels this context enqueued since creation. */
 int64_t rd_launch_count(const rd_ctx* ctx);

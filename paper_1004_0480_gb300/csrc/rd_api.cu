@@ -1149,9 +1149,9 @@ rd_status rd_set_kernel(rd_ctx* c, int32_t kernel) {
                         "the resident kernel needs the 7-point stencil, a model without "
                         "Cahn-Hilliard and no 3-D wind");
         rdk::ResidentPlan plan{};
-        const cudaError_t e = rdk::plan_resident(g.model, g.storage, plain_problem(g), g.nx,
-                                                 g.ny, g.nz, c->res_force[0],
-                                                 c->res_force[1], c->res_force[2], &plan);
+        const cudaError_t e = rdk::plan_resident(
+            g.model, g.storage, plain_problem(g), !periodic_axis(g, 0, 1) && !periodic_axis(g, 0, 2),
+            g.nx, g.ny, g.nz, c->res_force[0], c->res_force[1], c->res_force[2], &plan);
         if (e == cudaErrorInvalidValue)
             return fail(c, RD_EUNSUPPORTED,
                         "the resident kernel's rows do not fit shared memory (nx = %d)", g.nx);
@@ -1332,8 +1332,9 @@ rd_status rd_set_resident_plan(rd_ctx* c, int32_t K, int32_t tile_y, int32_t til
         return fail(c, RD_EINVAL, "plan out of range: K %d, tile %d x %d", K, tile_y, tile_z);
     const rd_config& g = c->cfg;
     rdk::ResidentPlan plan{};
-    const cudaError_t e = rdk::plan_resident(g.model, g.storage, plain_problem(g), g.nx, g.ny,
-                                             g.nz, K, tile_y, tile_z, &plan);
+    const cudaError_t e = rdk::plan_resident(
+        g.model, g.storage, plain_problem(g), !periodic_axis(g, 0, 1) && !periodic_axis(g, 0, 2),
+        g.nx, g.ny, g.nz, K, tile_y, tile_z, &plan);
     if (e == cudaErrorInvalidValue)
         return fail(c, RD_EINVAL, "K %d with a %d x %d tile does not fit shared memory", K,
                     tile_y, tile_z);
@@ -1345,7 +1346,7 @@ rd_status rd_set_resident_plan(rd_ctx* c, int32_t K, int32_t tile_y, int32_t til
     return RD_OK;
 }
 
-rd_status rd_get_resident_plan(const rd_ctx* c, int32_t out[7]) {
+rd_status rd_get_resident_plan(const rd_ctx* c, int32_t out[8]) {
     if (!c || !out) return RD_EINVAL;
     if (c->kernel != RD_KERNEL_RESIDENT) return RD_EUNSUPPORTED;
     const rdk::ResidentPlan& p = c->res_plan;
@@ -1356,6 +1357,7 @@ rd_status rd_get_resident_plan(const rd_ctx* c, int32_t out[7]) {
     out[4] = p.grid;
     out[5] = p.threads;
     out[6] = p.smem;
+    out[7] = p.tma;
     return RD_OK;
 }
 

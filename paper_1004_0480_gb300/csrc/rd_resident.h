@@ -29,6 +29,7 @@ struct ResidentPlan {
     int grid;           // CTAs (all resident at once)
     int threads;        // per CTA
     int smem;           // dynamic shared memory per CTA (bytes)
+    int tma;            // 1: tiles arrive as tensor-memory boxes
 };
 
 constexpr int kResidentMaxK = 4;
@@ -38,12 +39,14 @@ constexpr int kResidentMaxSteps = 1 << 16;
 
 // Plan for a problem (FP32 or BF16 state, a 7-point model without
 // Cahn-Hilliard; ``plain`` as LaunchArgs::plain, which picks the kernel
-// variant whose occupancy counts).  K, ty, tz > 0 fix those choices
+// variant whose occupancy counts).  ``tma_ok``: y and z are not periodic
+// (a box cannot wrap), so tiles may arrive as tensor-memory boxes when
+// rows are at most 256 elements.  K, ty, tz > 0 fix those choices
 // (clamped to the grid); 0 leaves them to a cost model.
 // cudaErrorInvalidValue when no candidate fits shared memory (very wide
 // rows, or a forced tile too large).
-cudaError_t plan_resident(int model, int storage, bool plain, int nx, int ny, int nz, int K,
-                          int ty, int tz, ResidentPlan* out);
+cudaError_t plan_resident(int model, int storage, bool plain, bool tma_ok, int nx, int ny,
+                          int nz, int K, int ty, int tz, ResidentPlan* out);
 
 // Advance a single instance (a.use_one) by ``nsteps`` >= 1 steps reading
 // level a.one.par ^ a.parity.  Each round of the plan's K steps is one

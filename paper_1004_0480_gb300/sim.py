@@ -235,9 +235,9 @@ class Sim:
                     "rd_set_resident_plan")
 
     def resident_plan(self):
-        out = (ctypes.c_int32 * 7)()
+        out = (ctypes.c_int32 * 8)()
         self._check(self.lib.rd_get_resident_plan(self.ctx, out), "rd_get_resident_plan")
-        return dict(zip(("K", "tile_y", "tile_z", "tiles", "ctas", "threads", "smem"),
+        return dict(zip(("K", "tile_y", "tile_z", "tiles", "ctas", "threads", "smem", "tma"),
                         list(out)))
 
     @property

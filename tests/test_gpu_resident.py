@@ -251,3 +251,31 @@ def test_resident_barrier_timeout_is_reported_and_the_context_recovers(rd):
         sim.step(6)
         sim.sync()
         assert np.array_equal(sim.get_fields(), march)
+
+
+def test_resident_tile_copies_by_tensor_memory_where_no_box_wraps(rd):
+    """Tiles arrive as one tensor-memory box unless y or z is periodic (a
+    box cannot wrap) or rows exceed 256 elements; both paths are covered by
+    the bit-for-bit comparisons above (zero-flux cases take boxes, the
+    periodic ones per-thread copies)."""
+    per_x = W.diffusion_blob(shape=(40, 12, 10))
+    per_x["bc"] = [["periodic", "periodic", "neumann", "neumann", "neumann", "neumann"]]
+    per_z = W.diffusion_blob(shape=(40, 12, 10))
+    per_z["bc"] = [["neumann", "neumann", "neumann", "neumann", "periodic", "periodic"]]
+    expect = [(W.cfg_diffusion_64(), 1), (per_x, 1), (per_z, 0),
+              (W.brusselator(shape=(70, 20, 17)), 0),          # periodic on every axis
+              (W.diffusion_blob(shape=(300, 6, 6)), 0)]         # rows wider than 256
+    for cfg, tma in expect:
+        with rd.Sim(cfg) as sim:
+            sim.set_kernel("resident")
+            assert sim.resident_plan()["tma"] == tma, cfg["name"]
+    f = W.initial_fields(per_x)
+    march = run_gpu(rd, per_x, 9, "march", fields=f)
+    for plan in (None, (3, 5, 2), (1, 12, 10)):
+        got = run_gpu(rd, per_x, 9, "resident", fields=f, plan=plan)
+        assert np.array_equal(got.view(np.uint32), march.view(np.uint32)), plan
+    cfg = W.diffusion_blob(shape=(300, 6, 6))
+    f = W.initial_fields(cfg)
+    march = run_gpu(rd, cfg, 7, "march", fields=f)
+    got = run_gpu(rd, cfg, 7, "resident", fields=f)
+    assert np.array_equal(got.view(np.uint32), march.view(np.uint32))
