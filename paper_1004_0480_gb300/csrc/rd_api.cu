@@ -1088,12 +1088,15 @@ static rd_status bounds_status(rd_ctx* c) {
 // A resident launch whose grid barrier timed out since the last check
 // (RD_ETIMEOUT; the flag is cleared).  Only contexts that use the kernel
 // pay the read.
-static rd_status resident_status(rd_ctx* c) {
+static rd_status resident_status(rd_ctx* c, cudaStream_t st) {
     if (c->kernel != RD_KERNEL_RESIDENT || !c->bar) return RD_OK;
     unsigned failed = 0;
-    RD_CUDA(c, cudaMemcpy(&failed, &c->bar->failed, sizeof(failed), cudaMemcpyDeviceToHost));
+    RD_CUDA(c, cudaMemcpyAsync(&failed, &c->bar->failed, sizeof(failed), cudaMemcpyDeviceToHost,
+                               st));
+    RD_CUDA(c, cudaStreamSynchronize(st));
     if (!failed) return RD_OK;
-    RD_CUDA(c, cudaMemset(&c->bar->failed, 0, sizeof(unsigned)));
+    RD_CUDA(c, cudaMemsetAsync(&c->bar->failed, 0, sizeof(unsigned), st));
+    RD_CUDA(c, cudaStreamSynchronize(st));
     return fail(c, RD_ETIMEOUT, "resident kernel: a grid barrier wait ran out; the steps of "
                                 "that launch are incomplete");
 }
@@ -1102,7 +1105,7 @@ rd_status rd_sync(rd_ctx* c) {
     if (!c) return RD_EINVAL;
     drain_batch(c);
     RD_CUDA(c, cudaStreamSynchronize(c->stream));
-    rd_status st = resident_status(c);
+    rd_status st = resident_status(c, c->stream);
     if (st != RD_OK) return st;
     return bounds_status(c);
 }
@@ -1619,7 +1622,7 @@ rd_status rd_batch_sync(rd_batch* b) {
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch sync");
     if (b->members.size() == 1) {   // a batch of one steps with its member's kernel
-        rd_status st = resident_status(b->members[0]);
+        rd_status st = resident_status(b->members[0], b->stream);
         if (st != RD_OK) return st;
     }
     return bounds_status(nullptr);
