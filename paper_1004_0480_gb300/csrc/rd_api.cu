@@ -268,6 +268,7 @@ struct rd_batch {
     std::vector<rd_ctx*> members;
     InstDesc* desc_dev = nullptr;
     size_t desc_cap = 0;
+    unsigned long long* work = nullptr;  // work-item counter, after the descriptors
     InstDesc* desc_host = nullptr;   // pinned
     cudaEvent_t upload_done = nullptr;
     cudaStream_t stream = nullptr;       // where work is enqueued
@@ -1477,8 +1478,12 @@ rd_status batch_upload(rd_batch* b, const rd_tuning& t, long long* nitems) {
         if (b->desc_host) cudaFreeHost(b->desc_host);
         b->desc_dev = nullptr;
         b->desc_host = nullptr;
+        b->work = nullptr;
         size_t cap = std::max<size_t>(16, n * 2);
-        if (dev_alloc(reinterpret_cast<void**>(&b->desc_dev), cap * sizeof(InstDesc)) != cudaSuccess ||
+        // the descriptors, then the work-item counter (InstDesc is a
+        // multiple of 16 bytes, so the counter is aligned)
+        if (dev_alloc(reinterpret_cast<void**>(&b->desc_dev),
+                      cap * sizeof(InstDesc) + 256) != cudaSuccess ||
             host_alloc(reinterpret_cast<void**>(&b->desc_host), cap * sizeof(InstDesc)) != cudaSuccess) {
             cudaGetLastError();
             // keep nothing of a half-made pair
@@ -1490,6 +1495,9 @@ rd_status batch_upload(rd_batch* b, const rd_tuning& t, long long* nitems) {
             return fail(nullptr, RD_ENOMEM, "batch descriptor allocation failed");
         }
         b->desc_cap = cap;
+        b->work = reinterpret_cast<unsigned long long*>(b->desc_dev + cap);
+        cudaError_t e = cudaMemsetAsync(b->work, 0, sizeof(unsigned long long), b->stream);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch work counter");
         b->graph.reset();
     }
     // the previous upload must have left the pinned buffer
@@ -1514,6 +1522,9 @@ rd_status batch_upload(rd_batch* b, const rd_tuning& t, long long* nitems) {
     return RD_OK;
 }
 
+static_assert(sizeof(InstDesc) % alignof(unsigned long long) == 0,
+              "the batch's work counter follows its descriptor array");
+
 // launches (of T steps each, alternating parity) captured in a batch's graph
 constexpr int kBatchGraphLaunches = 16;
 
@@ -1521,6 +1532,7 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
                        cudaStream_t st) {
     LaunchArgs a{};
     a.desc = b->desc_dev;
+    a.work = b->work;
     a.ninst = (int)b->members.size();
     a.parity = parity;
     a.nitems = nitems;

@@ -64,6 +64,9 @@ struct LaunchArgs {
                                // the variant with upwind along y and z)
     int vw;                    // cells per thread of the one-step 7-point
                                // kernel: 4 (16 threads per tile row) or 8
+    unsigned long long* work;  // batches: the work-item counter CTAs pull
+                               // from (zero between launches); nullptr: a
+                               // CTA takes every gridDim-th item
     InstDesc one;              // the instance of a single-instance launch
 };
 

@@ -388,6 +388,35 @@ __device__ __forceinline__ void load_desc(const LaunchArgs& a, long long item, I
     __syncthreads();
 }
 
+// Work items of a CTA.  A single instance's items cost the same, so a CTA
+// takes every gridDim-th one; a batch's differ (partial tiles, short last
+// z-chunks, unequal instances), so its CTAs pull the next item from the
+// batch's counter as they finish one.  Each CTA's last pull fails (its
+// ticket is at least nitems); the CTA holding the launch's last ticket,
+// nitems + gridDim - 1, pulls after every other, and zeroes the counter
+// for the next launch.  Called by every thread of the CTA together; the
+// item loops end with a block barrier, so s_item is free to overwrite.
+__device__ __forceinline__ long long pull_item(const LaunchArgs& a, long long& s_item) {
+    if (threadIdx.x == 0) {
+        const unsigned long long t = atomicAdd(a.work, 1ull);
+        if (t == (unsigned long long)a.nitems + gridDim.x - 1) atomicExch(a.work, 0ull);
+        s_item = (long long)t;
+    }
+    __syncthreads();
+    return s_item;
+}
+template <bool ONE>
+__device__ __forceinline__ long long first_item(const LaunchArgs& a, long long& s_item) {
+    if (ONE || !a.work) return blockIdx.x;
+    return pull_item(a, s_item);
+}
+template <bool ONE>
+__device__ __forceinline__ long long next_item(const LaunchArgs& a, long long item,
+                                               long long& s_item) {
+    if (ONE || !a.work) return item + gridDim.x;
+    return pull_item(a, s_item);
+}
+
 // Held (Dirichlet) layers: the first face in -x,+x,-y,+y,-z,+z wins.
 __device__ __forceinline__ void held_layers(const InstDesc& sd, int s, int xs, int y, int q,
                                             float (&o)[kVEC]) {
@@ -523,6 +552,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const __grid_co
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ InstDesc sdm;
     __shared__ int s_inst;
+    __shared__ long long s_item;
 
     const int tid = threadIdx.x;
     const int TY = a.ty;
@@ -544,7 +574,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const __grid_co
 
     int cur_inst = -1;
     if (tid == 0) s_inst = 0;
-    for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    for (long long item = first_item<ONE>(a, s_item); item < a.nitems;
+         item = next_item<ONE>(a, item, s_item)) {
         if constexpr (!ONE) load_desc(a, item, sdm, s_inst, cur_inst);
         const InstDesc& sd = desc_of<ONE>(a, sdm);
 
@@ -871,6 +902,7 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ InstDesc sdm;
     __shared__ int s_inst;
+    __shared__ long long s_item;
 
     const int tid = threadIdx.x;
     const int TY = a.ty;
@@ -886,7 +918,8 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
 
     int cur_inst = -1;
     if (tid == 0) s_inst = 0;
-    for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    for (long long item = first_item<ONE>(a, s_item); item < a.nitems;
+         item = next_item<ONE>(a, item, s_item)) {
         if constexpr (!ONE) load_desc(a, item, sdm, s_inst, cur_inst);
         const InstDesc& sd = desc_of<ONE>(a, sdm);
 

@@ -128,6 +128,7 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ InstDesc sdm;
     __shared__ int s_inst;
+    __shared__ long long s_item;
 
     const int tid = threadIdx.x;
     const int TY = a.ty;
@@ -165,7 +166,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
 
     int cur_inst = -1;
     if (tid == 0) s_inst = 0;
-    for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    for (long long item = first_item<ONE>(a, s_item); item < a.nitems;
+         item = next_item<ONE>(a, item, s_item)) {
         if constexpr (!ONE) load_desc(a, item, sdm, s_inst, cur_inst);
         const InstDesc& sd = desc_of<ONE>(a, sdm);
 
