@@ -462,6 +462,14 @@ rd_status rd_batch_set_tuning(rd_batch* b, const rd_tuning* t);
  * member steps it exactly as rd_step would (the member's own tuning), on
  * the batch's stream. */
 rd_status rd_batch_step(rd_batch* b, int64_t nsteps);
+/* Advance member i (in the order of rd_batch_add) by steps[i] >= 0 steps in
+ * one batched launch sequence of max(steps) steps (asynchronous): a member
+ * whose count is used up is left alone for the rest of the sequence (its
+ * work items are skipped), so members with different counts need not be
+ * stepped in separate calls.  Results equal rd_batch_step of each member
+ * alone bit for bit.  Needs one step per launch in the batch's tuning
+ * (RD_EINVAL otherwise, and for a negative count or a NULL array). */
+rd_status rd_batch_step_each(rd_batch* b, const int64_t* steps);
 /* Wait for the batch's stream. */
 rd_status rd_batch_sync(rd_batch* b);
 /* Destroy the batch (members are left intact and detached). */

@@ -89,6 +89,7 @@ SIGNATURES = {
     "rd_batch_set_stream": (_I, [_P, _P]),
     "rd_batch_set_tuning": (_I, [_P, _TUN]),
     "rd_batch_step": (_I, [_P, _I64]),
+    "rd_batch_step_each": (_I, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "rd_batch_sync": (_I, [_P]),
     "rd_batch_destroy": (_I, [_P]),
     "rd_batch_launch_count": (_I64, [_P]),

@@ -1471,7 +1471,10 @@ rd_tuning batch_tuning(rd_batch* b) {
 
 // Rebuild and upload the descriptor array: member i reads level cur_i at
 // parity 0.
-rd_status batch_upload(rd_batch* b, const rd_tuning& t, long long* nitems) {
+// ``caps``: launches each member takes part in (rd_batch_step_each), or
+// nullptr for every launch.
+rd_status batch_upload(rd_batch* b, const rd_tuning& t, long long* nitems,
+                       const long long* caps = nullptr) {
     const size_t n = b->members.size();
     if (n > b->desc_cap) {
         if (b->desc_dev) cudaFree(b->desc_dev);
@@ -1496,7 +1499,7 @@ rd_status batch_upload(rd_batch* b, const rd_tuning& t, long long* nitems) {
         }
         b->desc_cap = cap;
         b->work = reinterpret_cast<unsigned long long*>(b->desc_dev + cap);
-        cudaError_t e = cudaMemsetAsync(b->work, 0, sizeof(unsigned long long), b->stream);
+        cudaError_t e = cudaMemsetAsync(b->work, 0, 2 * sizeof(unsigned long long), b->stream);
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch work counter");
         b->graph.reset();
     }
@@ -1510,6 +1513,7 @@ rd_status batch_upload(rd_batch* b, const rd_tuning& t, long long* nitems) {
         fill_desc(c, b->desc_host[i], ti);
         b->desc_host[i].par = c->cur;
         b->desc_host[i].item_begin = begin;
+        b->desc_host[i].launch_cap = caps ? caps[i] : -1;
         begin += items_of(b->desc_host[i]);
     }
     *nitems = begin;
@@ -1557,9 +1561,9 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
 
 }  // namespace
 
-rd_status rd_batch_step(rd_batch* b, int64_t nsteps) {
-    if (!b || nsteps < 0) return RD_EINVAL;
-    if (b->members.empty() || nsteps == 0) return RD_OK;
+// ``steps``: per-member step counts (each at most nsteps), or nullptr for
+// nsteps steps of every member.
+rd_status batch_step_impl(rd_batch* b, int64_t nsteps, const int64_t* steps) {
     if (b->members.size() == 1) {
         // a batch of one steps its member as a single context does (its own
         // tuning, descriptor in the kernel parameters), on the batch's stream
@@ -1575,10 +1579,20 @@ rd_status rd_batch_step(rd_batch* b, int64_t nsteps) {
     const rd_tuning t = batch_tuning(b);
     rd_status st = check_tuning(b->members[0]->cfg, t);
     if (st != RD_OK) return st;
+    if (steps && t.tsteps != 1)
+        return fail(nullptr, RD_EINVAL, "per-member step counts need one step per launch");
     long long nitems = 0;
     for (rd_ctx* c : b->members)
         if ((st = sync_stepn(c, b->stream)) != RD_OK) return st;
-    if ((st = batch_upload(b, t, &nitems)) != RD_OK) return st;
+    std::vector<long long> caps;
+    if (steps) {
+        const int kps = kernels_per_step(b->members[0]->cfg);
+        for (size_t i = 0; i < b->members.size(); ++i) caps.push_back(steps[i] * kps);
+    }
+    if ((st = batch_upload(b, t, &nitems, steps ? caps.data() : nullptr)) != RD_OK) return st;
+    // launches completed in this call: the members' caps count from zero
+    cudaError_t ew = cudaMemsetAsync(b->work + 1, 0, sizeof(unsigned long long), b->stream);
+    if (ew != cudaSuccess) return cuda_fail(nullptr, ew, "batch launch count");
     const int T = t.tsteps;
     int64_t full = nsteps / T;
     const int rem = (int)(nsteps % T);
@@ -1622,11 +1636,32 @@ rd_status rd_batch_step(rd_batch* b, int64_t nsteps) {
         parity ^= 1;
     }
     const int64_t launches = nsteps / T + (rem ? 1 : 0);
-    for (rd_ctx* c : b->members) {
-        c->cur ^= (int)(launches & 1);
-        c->steps += nsteps;
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        rd_ctx* c = b->members[i];
+        // one transition between the levels per step (per launch of T steps)
+        const int64_t n = steps ? steps[i] : nsteps;
+        c->cur ^= (int)((steps ? n : launches) & 1);
+        c->steps += n;
+        if (steps && n < nsteps) c->stepn_dirty = true;   // its counter stopped early
     }
     return RD_OK;
+}
+
+rd_status rd_batch_step(rd_batch* b, int64_t nsteps) {
+    if (!b || nsteps < 0) return RD_EINVAL;
+    if (b->members.empty() || nsteps == 0) return RD_OK;
+    return batch_step_impl(b, nsteps, nullptr);
+}
+
+rd_status rd_batch_step_each(rd_batch* b, const int64_t* steps) {
+    if (!b || (!steps && !b->members.empty())) return RD_EINVAL;
+    int64_t n = 0;
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        if (steps[i] < 0) return fail(nullptr, RD_EINVAL, "negative step count");
+        n = std::max(n, steps[i]);
+    }
+    if (n == 0) return RD_OK;
+    return batch_step_impl(b, n, steps);
 }
 
 rd_status rd_batch_sync(rd_batch* b) {

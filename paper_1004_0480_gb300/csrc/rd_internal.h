@@ -46,6 +46,9 @@ struct InstDesc {
     int wrap_elems;            // periodic x with nx % 4 != 0: some halo
                                // vectors straddle the wrap point
     long long item_begin;      // first global item index of this instance
+    long long launch_cap;      // batches: launches of the current step call
+                               // that step this instance (it is left alone
+                               // from then on); -1: every launch
     const char* mem_lo[2];     // the instance's state and scratch allocations,
     const char* mem_hi[2];     // [lo, hi): the debug build's global bounds
 };
@@ -64,9 +67,11 @@ struct LaunchArgs {
                                // the variant with upwind along y and z)
     int vw;                    // cells per thread of the one-step 7-point
                                // kernel: 4 (16 threads per tile row) or 8
-    unsigned long long* work;  // batches: the work-item counter CTAs pull
-                               // from (zero between launches); nullptr: a
-                               // CTA takes every gridDim-th item
+    unsigned long long* work;  // batches: work[0] the work-item counter CTAs
+                               // pull from (zero between launches), work[1]
+                               // the launches completed in the current step
+                               // call; nullptr: a CTA takes every
+                               // gridDim-th item
     InstDesc one;              // the instance of a single-instance launch
 };
 

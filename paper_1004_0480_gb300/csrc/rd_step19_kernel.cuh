@@ -201,6 +201,7 @@ rd_step19_kernel(const __grid_constant__ LaunchArgs a) {
          item = next_item<ONE>(a, item, s_item)) {
         if constexpr (!ONE) load_desc(a, item, sdm, s_inst, cur_inst);
         const InstDesc& sd = desc_of<ONE>(a, sdm);
+        if (member_done<ONE>(a, sd)) continue;   // block-uniform
 
         const int nx = sd.nx, ny = sd.ny, nz = sd.nz, pitch = sd.pitch;
         const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;

@@ -393,17 +393,30 @@ __device__ __forceinline__ void load_desc(const LaunchArgs& a, long long item, I
 // z-chunks, unequal instances), so its CTAs pull the next item from the
 // batch's counter as they finish one.  Each CTA's last pull fails (its
 // ticket is at least nitems); the CTA holding the launch's last ticket,
-// nitems + gridDim - 1, pulls after every other, and zeroes the counter
-// for the next launch.  Called by every thread of the CTA together; the
-// item loops end with a block barrier, so s_item is free to overwrite.
+// nitems + gridDim - 1, pulls after every other CTA has finished its
+// items, so it also counts the launch as completed (work[1]) and zeroes
+// the item counter for the next launch.  Called by every thread of the CTA
+// together; the item loops end with a block barrier, so s_item is free to
+// overwrite.
 __device__ __forceinline__ long long pull_item(const LaunchArgs& a, long long& s_item) {
     if (threadIdx.x == 0) {
         const unsigned long long t = atomicAdd(a.work, 1ull);
-        if (t == (unsigned long long)a.nitems + gridDim.x - 1) atomicExch(a.work, 0ull);
+        if (t == (unsigned long long)a.nitems + gridDim.x - 1) {
+            atomicAdd(a.work + 1, 1ull);
+            atomicExch(a.work, 0ull);
+        }
         s_item = (long long)t;
     }
     __syncthreads();
     return s_item;
+}
+// A batch member whose launches for the current step call are used up
+// (rd_batch_step_each) is left alone: its items are skipped, its fields
+// keep the level its last step wrote.  The same for every thread.
+template <bool ONE>
+__device__ __forceinline__ bool member_done(const LaunchArgs& a, const InstDesc& sd) {
+    if (ONE || !a.work || sd.launch_cap < 0) return false;
+    return (long long)a.work[1] >= sd.launch_cap;
 }
 template <bool ONE>
 __device__ __forceinline__ long long first_item(const LaunchArgs& a, long long& s_item) {
@@ -578,6 +591,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) rd_step_kernel(const __grid_co
          item = next_item<ONE>(a, item, s_item)) {
         if constexpr (!ONE) load_desc(a, item, sdm, s_inst, cur_inst);
         const InstDesc& sd = desc_of<ONE>(a, sdm);
+        if (member_done<ONE>(a, sd)) continue;   // block-uniform
 
         const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
         const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;
@@ -922,6 +936,7 @@ rd_step1_kernel(const __grid_constant__ LaunchArgs a) {
          item = next_item<ONE>(a, item, s_item)) {
         if constexpr (!ONE) load_desc(a, item, sdm, s_inst, cur_inst);
         const InstDesc& sd = desc_of<ONE>(a, sdm);
+        if (member_done<ONE>(a, sd)) continue;   // block-uniform
 
         const int nx = sd.nx, ny = sd.ny, nz = sd.nz, pitch = sd.pitch;
         const bool px = sd.per_x, py = sd.per_y, pz = sd.per_z;

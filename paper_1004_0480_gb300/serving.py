@@ -183,6 +183,16 @@ class CudaEngine:
         ev.record(self.streams[family][1 if high else 0])
         self.events[family] = ev
 
+    def step_each(self, family, counts, high=False):
+        """As ``step``, each running request of the family advancing its own
+        count (``counts``: (handle, steps) pairs; one batched launch sequence
+        of the largest count, members whose count is used up left alone)."""
+        self._stream_for(family, high)
+        self.batches[family].step_each(dict(counts))
+        ev = self._torch.cuda.Event()
+        ev.record(self.streams[family][1 if high else 0])
+        self.events[family] = ev
+
     def busy(self, family):
         """True while the family's last enqueued steps have not completed
         (cudaEventQuery: no synchronisation)."""
@@ -244,9 +254,11 @@ class Server:
     next admitted requests join it, and enqueues its next chunk, while the
     other families keep running.  Arrivals are admitted between polls.
 
-    ``quantum``    steps per chunk of a family batch (a chunk never steps a
-                   request past its count: the batch advances by the smallest
-                   remaining count if that is smaller)
+    ``quantum``    steps per chunk of a family batch; in a chunk each running
+                   request advances by the quantum or its remaining count,
+                   whichever is smaller (one batched launch sequence: a
+                   request that finishes early is left alone for the rest
+                   of the chunk)
     ``budget``     bytes of device memory the admitted requests may hold
     ``run_cells``  cells the running requests may hold together: requests
                    start in admission order while the running ones hold
@@ -344,10 +356,11 @@ class Server:
             for fam, slots in by_family.items():
                 if not idle[fam]:
                     continue
-                n = min(self.quantum, min(s["left"] for s in slots))
-                self.engine.step(fam, n, high=(fam == oldest))
-                for s in slots:
-                    s["left"] -= n
+                counts = [min(self.quantum, s["left"]) for s in slots]
+                self.engine.step_each(fam, [(s["handle"], k) for s, k in zip(slots, counts)],
+                                      high=(fam == oldest))
+                for s, k in zip(slots, counts):
+                    s["left"] -= k
             if self.progress:
                 self.progress(self.clock() - t0, len(admitted), len(running), len(results))
             # ---- wait for a family to go idle (or the next arrival)

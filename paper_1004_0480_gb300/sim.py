@@ -305,6 +305,13 @@ class Batch:
     def step(self, n):
         L.check(self.lib.rd_batch_step(self.b, int(n)), None, "rd_batch_step")
 
+    def step_each(self, counts):
+        """Advance each member by its own count: ``counts`` maps a member
+        Sim to its steps (members left out: 0)."""
+        arr = (ctypes.c_int64 * max(len(self.members), 1))(
+            *[int(counts.get(m, 0)) for m in self.members])
+        L.check(self.lib.rd_batch_step_each(self.b, arr), None, "rd_batch_step_each")
+
     def sync(self):
         L.check(self.lib.rd_batch_sync(self.b), None, "rd_batch_sync")
 

@@ -27,6 +27,7 @@ class FakeEngine:
         self.clock, self.rate = clock, rate
         self.members = {}        # family -> running requests
         self.step_log = []       # (family, n, ids of the running requests)
+        self.count_log = []      # per chunk: request id -> its steps
         self.done_at = {}        # family -> fake time its last chunk completes
         self.used = 0
         self.peak = 0
@@ -55,6 +56,19 @@ class FakeEngine:
         self.done_at[fam] = self.clock.t + work / self.rate
         for r in self.members[fam]:
             self.steps_done[r.id] += n
+        self.nlaunch += n
+
+    def step_each(self, fam, counts, high=False):
+        assert not self.busy(fam), "a family is stepped only when idle"
+        k = {id(h): n for h, n in counts}
+        assert all(id(h) in {id(r) for r in self.members[fam]} and n >= 0 for h, n in counts)
+        n = max(k.values())
+        self.step_log.append((fam, n, sorted(r.id for r in self.members[fam])))
+        self.count_log.append({r.id: k.get(id(r), 0) for r in self.members[fam]})
+        work = sum(r.cells * k.get(id(r), 0) for r in self.members[fam])
+        self.done_at[fam] = self.clock.t + work / self.rate
+        for r in self.members[fam]:
+            self.steps_done[r.id] += k.get(id(r), 0)
         self.nlaunch += n
 
     def busy(self, fam):
@@ -206,4 +220,20 @@ def test_a_finished_request_never_takes_more_steps():
     eng = FakeEngine(clk)
     reqs = [mk(i, 0.0, 10, 7 + 11 * i) for i in range(5)]
     Server(eng, budget_bytes=1e12, quantum=9, clock=clk, sleep=clk.sleep).run(reqs)
+    assert all(eng.steps_done[r.id] == r.steps for r in reqs)
+
+
+def test_a_chunk_advances_each_request_by_its_own_count():
+    # three requests of one family with 5, 12 and 30 steps, quantum 10: the
+    # first chunk steps them 5, 10, 10 at once (not 5 each), the request
+    # with 5 steps is left alone after its fifth
+    clk = FakeClock()
+    eng = FakeEngine(clk)
+    reqs = [mk(0, 0.0, 10, 5), mk(1, 0.0, 10, 12), mk(2, 0.0, 10, 30)]
+    Server(eng, budget_bytes=1e12, quantum=10, clock=clk, sleep=clk.sleep).run(reqs)
+    assert eng.count_log[0] == {0: 5, 1: 10, 2: 10}
+    assert eng.step_log[0] == ("brusselator", 10, [0, 1, 2])
+    assert eng.count_log[1] == {1: 2, 2: 10}
+    assert eng.count_log[2] == {2: 10}
+    assert len(eng.count_log) == 3
     assert all(eng.steps_done[r.id] == r.steps for r in reqs)
