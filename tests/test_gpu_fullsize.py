@@ -12,7 +12,7 @@ times:
   32 front instances batched   FP32 <= 1e-4 per instance, for the three
                                smallest and the largest instance (one
                                batched launch sequence, the benchmark's
-                               tile 12 x 64, 32-plane chunks, graph replay)
+                               tile 12 x 64, 48-plane chunks, graph replay)
 
 The oracle legs run in worker processes started with the session
 (tests/fullsize_oracle.py).  With RD_ERROR_REPORT=<path> the errors are
@@ -110,7 +110,7 @@ def test_ch_front_batch_32_200_steps(rd, legs):
         for c, s in zip(cfgs, sims):
             s.set_fields(W.initial_fields(c))
         b = rd.Batch("ch_front")
-        b.set_tuning(tsteps=1, tile_q=16, tile_y=12, zchunk=32, graph=1)
+        b.set_tuning(tsteps=1, tile_q=16, tile_y=12, zchunk=48, graph=1)
         for s in sims:
             b.add(s)
         b.step(FO.STEPS)
