@@ -264,7 +264,9 @@ def test_resident_tile_copies_by_tensor_memory_where_no_box_wraps(rd):
     per_z["bc"] = [["neumann", "neumann", "neumann", "neumann", "periodic", "periodic"]]
     expect = [(W.cfg_diffusion_64(), 1), (per_x, 1), (per_z, 0),
               (W.brusselator(shape=(70, 20, 17)), 0),          # periodic on every axis
-              (W.diffusion_blob(shape=(300, 6, 6)), 0)]         # rows wider than 256
+              (W.diffusion_blob(shape=(256, 6, 6)), 1),         # a box of 256 elements
+              (W.diffusion_blob(shape=(260, 6, 6)), 0),         # rows wider than 256
+              (W.diffusion_blob(shape=(300, 6, 6)), 0)]
     for cfg, tma in expect:
         with rd.Sim(cfg) as sim:
             sim.set_kernel("resident")
@@ -274,8 +276,9 @@ def test_resident_tile_copies_by_tensor_memory_where_no_box_wraps(rd):
     for plan in (None, (3, 5, 2), (1, 12, 10)):
         got = run_gpu(rd, per_x, 9, "resident", fields=f, plan=plan)
         assert np.array_equal(got.view(np.uint32), march.view(np.uint32)), plan
-    cfg = W.diffusion_blob(shape=(300, 6, 6))
-    f = W.initial_fields(cfg)
-    march = run_gpu(rd, cfg, 7, "march", fields=f)
-    got = run_gpu(rd, cfg, 7, "resident", fields=f)
-    assert np.array_equal(got.view(np.uint32), march.view(np.uint32))
+    for shape in ((300, 6, 6), (256, 6, 6), (253, 7, 5)):
+        cfg = W.diffusion_blob(shape=shape)
+        f = W.initial_fields(cfg)
+        march = run_gpu(rd, cfg, 7, "march", fields=f)
+        got = run_gpu(rd, cfg, 7, "resident", fields=f)
+        assert np.array_equal(got.view(np.uint32), march.view(np.uint32)), shape
