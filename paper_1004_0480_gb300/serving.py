@@ -254,11 +254,10 @@ class Server:
     next admitted requests join it, and enqueues its next chunk, while the
     other families keep running.  Arrivals are admitted between polls.
 
-    ``quantum``    steps per chunk of a family batch; in a chunk each running
-                   request advances by the quantum or its remaining count,
-                   whichever is smaller (one batched launch sequence: a
-                   request that finishes early is left alone for the rest
-                   of the chunk)
+    ``quantum``    steps per chunk of a family batch (a chunk never steps a
+                   request past its count: the batch advances by the smallest
+                   remaining count if that is smaller, so the request that
+                   finishes retires as soon as the chunk completes)
     ``budget``     bytes of device memory the admitted requests may hold
     ``run_cells``  cells the running requests may hold together: requests
                    start in admission order while the running ones hold
@@ -356,11 +355,14 @@ class Server:
             for fam, slots in by_family.items():
                 if not idle[fam]:
                     continue
-                counts = [min(self.quantum, s["left"]) for s in slots]
-                self.engine.step_each(fam, [(s["handle"], k) for s, k in zip(slots, counts)],
-                                      high=(fam == oldest))
-                for s, k in zip(slots, counts):
-                    s["left"] -= k
+                # the chunk ends when its first member finishes, so that
+                # member retires at once (per-member counts, step_each,
+                # would let the others run on, but the finished member
+                # then waits for the chunk's end: a longer tail, measured)
+                n = min(self.quantum, min(s["left"] for s in slots))
+                self.engine.step(fam, n, high=(fam == oldest))
+                for s in slots:
+                    s["left"] -= n
             if self.progress:
                 self.progress(self.clock() - t0, len(admitted), len(running), len(results))
             # ---- wait for a family to go idle (or the next arrival)

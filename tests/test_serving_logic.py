@@ -222,18 +222,3 @@ def test_a_finished_request_never_takes_more_steps():
     Server(eng, budget_bytes=1e12, quantum=9, clock=clk, sleep=clk.sleep).run(reqs)
     assert all(eng.steps_done[r.id] == r.steps for r in reqs)
 
-
-def test_a_chunk_advances_each_request_by_its_own_count():
-    # three requests of one family with 5, 12 and 30 steps, quantum 10: the
-    # first chunk steps them 5, 10, 10 at once (not 5 each), the request
-    # with 5 steps is left alone after its fifth
-    clk = FakeClock()
-    eng = FakeEngine(clk)
-    reqs = [mk(0, 0.0, 10, 5), mk(1, 0.0, 10, 12), mk(2, 0.0, 10, 30)]
-    Server(eng, budget_bytes=1e12, quantum=10, clock=clk, sleep=clk.sleep).run(reqs)
-    assert eng.count_log[0] == {0: 5, 1: 10, 2: 10}
-    assert eng.step_log[0] == ("brusselator", 10, [0, 1, 2])
-    assert eng.count_log[1] == {1: 2, 2: 10}
-    assert eng.count_log[2] == {2: 10}
-    assert len(eng.count_log) == 3
-    assert all(eng.steps_done[r.id] == r.steps for r in reqs)
