@@ -1532,11 +1532,16 @@ static_assert(sizeof(InstDesc) % alignof(unsigned long long) == 0,
 // launches (of T steps each, alternating parity) captured in a batch's graph
 constexpr int kBatchGraphLaunches = 16;
 
+// ``caps``: the launch counts members' launches (rd_batch_step_each), so its
+// CTAs pull their items from the batch's counter, whose last pull counts the
+// launch.  Otherwise they pull only when the items fill four or more waves
+// of the grid (uneven items then balance; with fewer, the pulls' round
+// trips cost more than they balance: a served mix of small requests measured
+// a longer tail with them).
 rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long long nitems,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool caps) {
     LaunchArgs a{};
     a.desc = b->desc_dev;
-    a.work = b->work;
     a.ninst = (int)b->members.size();
     a.parity = parity;
     a.nitems = nitems;
@@ -1553,6 +1558,7 @@ rd_status batch_launch(rd_batch* b, const rd_tuning& t, int T, int parity, long 
         1, occupancy(b->model, b->storage, T, a.ty, a.regcap, a.plain ? 1 : a.wind3 ? 2 : 0,
                      b->stencil, t.tile_q));
     const long long grid = std::min<long long>(nitems, (long long)occ * num_sms());
+    a.work = (caps || nitems >= 4 * grid) ? b->work : nullptr;
     cudaError_t e = launch_model(b->model, b->storage, T, a, (int)grid, sm, st, nullptr, b->stencil);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch step launch");
     b->launches += kernels_per_step(b->members[0]->cfg);
@@ -1597,7 +1603,7 @@ rd_status batch_step_impl(rd_batch* b, int64_t nsteps, const int64_t* steps) {
     int64_t full = nsteps / T;
     const int rem = (int)(nsteps % T);
     int parity = 0;
-    const long long key = b->members_version * 1000003LL + nitems;
+    const long long key = (b->members_version * 1000003LL + nitems) * 2 + (steps ? 1 : 0);
     if (t.graph && full >= kBatchGraphLaunches) {
         if (!b->graph.exec || b->graph.key != key) {
             b->graph.reset();
@@ -1608,7 +1614,7 @@ rd_status batch_step_impl(rd_batch* b, int64_t nsteps, const int64_t* steps) {
             if (e != cudaSuccess) return cuda_fail(nullptr, e, "begin capture");
             const int64_t before = b->launches;
             for (int i = 0; i < kBatchGraphLaunches && st == RD_OK; ++i)
-                st = batch_launch(b, t, T, i & 1, nitems, b->capture_stream);
+                st = batch_launch(b, t, T, i & 1, nitems, b->capture_stream, steps != nullptr);
             cudaGraph_t g = nullptr;
             e = cudaStreamEndCapture(b->capture_stream, &g);
             if (st != RD_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -1628,11 +1634,13 @@ rd_status batch_step_impl(rd_batch* b, int64_t nsteps, const int64_t* steps) {
         }
     }
     for (int64_t i = 0; i < full; ++i) {
-        if ((st = batch_launch(b, t, T, parity, nitems, b->stream)) != RD_OK) return st;
+        if ((st = batch_launch(b, t, T, parity, nitems, b->stream, steps != nullptr)) != RD_OK)
+            return st;
         parity ^= 1;
     }
     if (rem) {
-        if ((st = batch_launch(b, t, rem, parity, nitems, b->stream)) != RD_OK) return st;
+        if ((st = batch_launch(b, t, rem, parity, nitems, b->stream, steps != nullptr)) != RD_OK)
+            return st;
         parity ^= 1;
     }
     const int64_t launches = nsteps / T + (rem ? 1 : 0);

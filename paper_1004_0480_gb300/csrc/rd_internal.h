@@ -67,11 +67,11 @@ struct LaunchArgs {
                                // the variant with upwind along y and z)
     int vw;                    // cells per thread of the one-step 7-point
                                // kernel: 4 (16 threads per tile row) or 8
-    unsigned long long* work;  // batches: work[0] the work-item counter CTAs
-                               // pull from (zero between launches), work[1]
-                               // the launches completed in the current step
-                               // call; nullptr: a CTA takes every
-                               // gridDim-th item
+    unsigned long long* work;  // batches that pull items: work[0] the
+                               // work-item counter (zero between launches),
+                               // work[1] the launches completed in the
+                               // current step call; nullptr: a CTA takes
+                               // every gridDim-th item
     InstDesc one;              // the instance of a single-instance launch
 };
 

@@ -389,9 +389,9 @@ __device__ __forceinline__ void load_desc(const LaunchArgs& a, long long item, I
 }
 
 // Work items of a CTA.  A single instance's items cost the same, so a CTA
-// takes every gridDim-th one; a batch's differ (partial tiles, short last
-// z-chunks, unequal instances), so its CTAs pull the next item from the
-// batch's counter as they finish one.  Each CTA's last pull fails (its
+// takes every gridDim-th one; a batch's may differ (partial tiles, short
+// last z-chunks, unequal instances), so when the host passes the batch's
+// counter (a.work) its CTAs pull the next item as they finish one.  Each CTA's last pull fails (its
 // ticket is at least nitems); the CTA holding the launch's last ticket,
 // nitems + gridDim - 1, pulls after every other CTA has finished its
 // items, so it also counts the launch as completed (work[1]) and zeroes
