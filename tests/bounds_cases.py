@@ -86,6 +86,23 @@ def main(path):
     b.close()
     for s in sims:
         s.close()
+    # members advancing their own counts: the CTAs pull their work items
+    cfgs = [W.brusselator(shape=s, seed=i) for i, s in enumerate([(23, 17, 11), (70, 9, 14),
+                                                                   (16, 33, 9)])]
+    sims = [Sim(c) for c in cfgs]
+    for c, s in zip(cfgs, sims):
+        s.set_fields(W.initial_fields(c))
+    b = Batch("brusselator")
+    b.set_tuning(tsteps=1, tile_q=16, tile_y=6, zchunk=5, graph=1)
+    for s in sims:
+        b.add(s)
+    b.step_each(dict(zip(sims, [3, 21, 0])))
+    res["status_batch_each"] = np.array(L.load().rd_batch_sync(b.b))
+    for i, s in enumerate(sims):
+        res[f"batch_each_{i}"] = s.get_fields()
+    b.close()
+    for s in sims:
+        s.close()
     np.savez(path, **res)
 
 
