@@ -27,7 +27,6 @@ class FakeEngine:
         self.clock, self.rate = clock, rate
         self.members = {}        # family -> running requests
         self.step_log = []       # (family, n, ids of the running requests)
-        self.count_log = []      # per chunk: request id -> its steps
         self.done_at = {}        # family -> fake time its last chunk completes
         self.used = 0
         self.peak = 0
@@ -56,19 +55,6 @@ class FakeEngine:
         self.done_at[fam] = self.clock.t + work / self.rate
         for r in self.members[fam]:
             self.steps_done[r.id] += n
-        self.nlaunch += n
-
-    def step_each(self, fam, counts, high=False):
-        assert not self.busy(fam), "a family is stepped only when idle"
-        k = {id(h): n for h, n in counts}
-        assert all(id(h) in {id(r) for r in self.members[fam]} and n >= 0 for h, n in counts)
-        n = max(k.values())
-        self.step_log.append((fam, n, sorted(r.id for r in self.members[fam])))
-        self.count_log.append({r.id: k.get(id(r), 0) for r in self.members[fam]})
-        work = sum(r.cells * k.get(id(r), 0) for r in self.members[fam])
-        self.done_at[fam] = self.clock.t + work / self.rate
-        for r in self.members[fam]:
-            self.steps_done[r.id] += k.get(id(r), 0)
         self.nlaunch += n
 
     def busy(self, fam):
