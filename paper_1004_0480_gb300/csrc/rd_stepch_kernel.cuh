@@ -62,11 +62,17 @@ struct FetchM {
 
 // Fetch with mirror-extended (zero-flux) or wrapped (periodic) coordinates.
 // Vectors past row ny + 1 or column nx + 1 feed no stored cell: not copied.
+// Nor the vectors wholly beyond a zero-flux x face that lies on a vector
+// boundary (x = 0, and x = nx when nx is a multiple of 4): their cells are
+// the mirror images of the face vector, c(-1) = c(0) and mu(-1) = mu(0) bit
+// for bit (mu's x sum adds the same two values in the other order), so the
+// face thread reads its own cells instead (see the kernel).
 template <class ST>
 __device__ __forceinline__ FetchM make_fetch_mirror(int yrow, int xs, int nx, int ny, int pitch,
                                                     bool px, bool py, int soff_elems) {
     FetchM f{0, 0, soff_elems * (int)sizeof(ST), {0, 0, 0, 0}};
     if (yrow > ny + 1 || xs > nx + 1) return f;
+    if (!px && (xs + kVEC <= 0 || (xs >= nx && nx % kVEC == 0))) return f;
     const int yw = py ? wrapi(yrow, ny) : mirror_index(yrow, ny);
     const int row = yw * pitch;
     f.goff = row;
@@ -190,6 +196,10 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
         const int y = y0 - 1 + r;                     // global row of the position
         const int xs = x0 - kVEC + v * kVEC;          // global x of its first element
         const bool stores = inner && y < ny && xs < nx;
+        // a zero-flux x face on the vector's edge: the neighbour beyond it is
+        // the own face cell, for c and for mu alike
+        const bool lface = !px && xs == 0;
+        const bool rface = !px && xs + kVEC == nx;
         const unsigned xyf = xy_faces(xs, y, nx, ny);
         const bool src_col = sd.src_s >= 0 && (py ? wrapi(y, ny) : y) == sd.src_y;
         // own state vector, and (first 2 x 18 threads) the outer halo rows
@@ -251,8 +261,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                 lds_vec<ST>(ring + s2 * SLOTB + 2 * PEB + own_b, cz_p);
                 lds_vec<ST>(Cc - RWB, ym);
                 lds_vec<ST>(Cc + RWB, yp);
-                const float left = lds_one<ST>(Cc - EB);
-                const float right = lds_one<ST>(Cc + kVEC * EB);
+                const float left = lface ? c[0] : lds_one<ST>(Cc - EB);
+                const float right = rface ? c[kVEC - 1] : lds_one<ST>(Cc + kVEC * EB);
 #pragma unroll
                 for (int e = 0; e < kVEC; ++e) {
                     const float xm = e ? c[e - 1] : left;
@@ -291,8 +301,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                     lds_vec<ST>(Sp + s * PEB, zp);
                     lds_vec<ST>(Ps - RWB, ym);
                     lds_vec<ST>(Ps + RWB, yp);
-                    const float left = lds_one<ST>(Ps - EB);
-                    const float right = lds_one<ST>(Ps + kVEC * EB);
+                    const float left = lface ? cen[s][0] : lds_one<ST>(Ps - EB);
+                    const float right = rface ? cen[s][kVEC - 1] : lds_one<ST>(Ps + kVEC * EB);
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e) {
                         xm[e] = e ? cen[s][e - 1] : left;
@@ -320,8 +330,8 @@ rd_stepch_kernel(const __grid_constant__ LaunchArgs a) {
                     float mym[kVEC], myp[kVEC], o[kVEC];
                     Store<float>::load(Mc - kRW, mym);
                     Store<float>::load(Mc + kRW, myp);
-                    const float mleft = Store<float>::get(Mc - 1);
-                    const float mright = Store<float>::get(Mc + kVEC);
+                    const float mleft = lface ? mu_0[0] : Store<float>::get(Mc - 1);
+                    const float mright = rface ? mu_0[kVEC - 1] : Store<float>::get(Mc + kVEC);
 #pragma unroll
                     for (int e = 0; e < kVEC; ++e) {
                         const float mxm = e ? mu_0[e - 1] : mleft;
