@@ -1,6 +1,8 @@
 """Host-side pieces of bench.py that need no GPU: the measured peak, the
-kernel hash that ties the committed ncu summary to the kernel sources, and
-the traffic lookup that must go null when they no longer match."""
+kernel hash that ties the committed ncu summary to the kernel sources, the
+traffic lookup that must go null when they no longer match, the summary of
+the clock samples (median SM clock under load, throttle reasons) and the
+tuning argument."""
 import json
 import re
 
@@ -46,3 +48,52 @@ def test_whole_job_rate_and_roofline_entry():
     e = bench._entry(cells=1_000_000, steps=1000, seconds=0.5, bytes_per_cell_step=16)
     assert e["glups"] == pytest.approx(2.0)
     assert e["roofline_frac"] == pytest.approx(2.0 * 16 / peak)
+
+
+def _sampler_with(rows):
+    s = bench.ClockSampler(0)
+    s.tmp.write("".join(r + "\n" for r in rows))
+    return s
+
+
+def test_clock_summary_takes_the_median_under_load_and_every_reason():
+    # nvidia-smi rows: index, sm, max sm, power, active mask, hw slowdown,
+    # hw thermal, sw thermal, sw power cap
+    rows = [
+        "0, 345, 2070, 180.5, 0x0000000000000001, Not Active, Not Active, Not Active, Not Active",
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1380.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2040, 2070, 1399.9, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, [N/A], 2070, 10, 0x0, Not Active, Not Active, Not Active, Not Active",   # skipped
+        "garbage line",                                                            # skipped
+    ]
+    out = _sampler_with(rows).summary()
+    # the idle sample (below half the maximum) is left out of the median
+    assert out["sm_mhz"] == 2055
+    assert out["sm_max_mhz"] == 2070
+    assert out["reasons"] == ["sw_power_cap"]
+    assert out["samples"] == 4
+
+
+def test_clock_summary_names_the_throttle_reasons_that_reject_a_run():
+    rows = [
+        "0, 1500, 2070, 1200, 0x8, Active, Not Active, Not Active, Not Active",
+        "0, 1600, 2070, 1200, 0x40, Not Active, Active, Not Active, Not Active",
+        "0, 1700, 2070, 1200, 0x20, Not Active, Not Active, Active, Not Active",
+    ]
+    out = _sampler_with(rows).summary()
+    assert out["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"]
+    assert out["sm_mhz"] == 1600
+
+
+def test_clock_summary_without_samples_says_so():
+    out = _sampler_with([]).summary()
+    assert out == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+
+def test_tuning_argument():
+    assert bench.parse_tuning("1,14,64") == dict(tsteps=1, tile_y=14, zchunk=64, regcap=0)
+    assert bench.parse_tuning("2,8,32,1,8") == dict(tsteps=2, tile_y=8, zchunk=32, regcap=1,
+                                                    tile_q=8)
+    with pytest.raises(ValueError):
+        bench.parse_tuning("1,x,64")
