@@ -97,3 +97,25 @@ def test_tuning_argument():
                                                     tile_q=8)
     with pytest.raises(ValueError):
         bench.parse_tuning("1,x,64")
+
+
+def test_every_profile_command_names_a_bench_workload_and_a_valid_tuning():
+    import glob
+    import os
+    files = sorted(glob.glob(os.path.join(os.path.dirname(bench.PROFILE_FILE), "*.md")))
+    assert files
+    for path in files:
+        text = open(path).read()
+        # the command block: the lines after "Command" up to the first blank line
+        cmd = " ".join(text.split("Command", 1)[1].split("\n\n")[1].replace("\\", " ").split())
+        assert "--clock-control none" in cmd, path
+        assert "python bench.py" in cmd, path
+        src = open(bench.__file__).read()
+        for flag in re.findall(r"(--[a-z][a-z-]*)", cmd.split("python bench.py", 1)[1]):
+            assert f'add_argument("{flag}"' in src, (path, flag)
+        m = re.search(r"--profile-workload (\S+)", cmd)
+        if m:
+            assert m.group(1) in bench.PROFILE_WORKLOADS, path
+        m = re.search(r"--tuning (\S+)", cmd)
+        if m:
+            bench.parse_tuning(m.group(1))
