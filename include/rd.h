@@ -270,8 +270,12 @@ rd_status rd_set_step_count(rd_ctx* ctx, int64_t n);
 /* Kernel tuning of a context.
  *   tsteps  steps per launch (temporal blocking depth), 1..3 (1..2 for
  *           the Cahn-Hilliard models, 1 for the 19-point stencil)
- *   tile_q  tile width in 4-cell vectors; this build fixes it at 16 (a tile
- *           is 64 cells wide)
+ *   tile_q  tile width in vectors, a tile being 64 cells wide: 16 (4 cells
+ *           per thread, every kernel) or 8 (8 cells per thread: the
+ *           one-step 7-point kernel of a model without Cahn-Hilliard, so
+ *           tsteps 1 and tile_y a multiple of 4, at most 40; its CTA is
+ *           8 tile_y compute threads, whose x neighbours come by warp
+ *           shuffle, plus one halo warp); else RD_EINVAL
  *   tile_y  tile height in rows, >= 1 (even for tsteps = 1 with the
  *           19-point stencil or without Cahn-Hilliard, where the CTA is 16
  *           tile_y compute threads plus one halo warp); otherwise the CTA
