@@ -383,8 +383,9 @@ const char* rd_last_error(const rd_ctx* ctx);
  * shared load, 2 shared store, 3 copy destination, 4 copy source, 5 state
  * store, 6 Courant table or step counter, 7 mu field, 8 halo descriptors,
  * 9 state load of the resident kernel, 0xFFFF the self-test), bits 0..39
- * the byte offset from the start of the window missed.  rd_sync and rd_batch_sync then return RD_EBOUNDS (and
- * clear the word), with the site and offset in rd_last_error.
+ * the byte offset from the start of the window missed.  rd_sync and
+ * rd_batch_sync then return RD_EBOUNDS (and clear the word), with the site
+ * and offset in rd_last_error.
  *   op 0: *word = the word; 1: the same, then clear it; 2: launch a
  *   self-test kernel that records a violation at site 0xFFFF without
  *   touching memory, then as 1.
@@ -404,7 +405,8 @@ rd_status rd_debug_fail_alloc(int64_t k);
  * round (more steps than the plan's K) counts `phantom` (> 0) CTAs that
  * never arrive, so its first grid barrier wait runs out after about 0.2 s;
  * every CTA then leaves after the launch's first round, so the state is not
- * the one asked for, and the next rd_sync returns RD_ETIMEOUT.  Only that launch is affected; 0 disarms.
+ * the one asked for, and the next rd_sync returns RD_ETIMEOUT.  Only that
+ * launch is affected; 0 disarms.
  * RD_EINVAL for a null context or phantom < 0, RD_EUNSUPPORTED unless the
  * context's kernel is RD_KERNEL_RESIDENT. */
 rd_status rd_debug_resident_stall(rd_ctx* ctx, int32_t phantom);
