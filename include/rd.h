@@ -260,7 +260,9 @@ rd_status rd_mass(rd_ctx* ctx, int s, double out[3]);
 rd_status rd_sync(rd_ctx* ctx);
 
 /* Like rd_sync, but give up after timeout_ms milliseconds of polling and
- * return RD_ETIMEOUT (the work keeps running; the context stays usable). */
+ * return RD_ETIMEOUT (the work keeps running; the context stays usable).
+ * RD_OK says only that the stream is idle: a resident barrier that ran out
+ * or a recorded bounds violation stays flagged for the next rd_sync. */
 rd_status rd_wait(rd_ctx* ctx, int64_t timeout_ms);
 
 /* Time steps taken since creation (or the last rd_set_step_count). */
