@@ -270,6 +270,17 @@ class Sim:
         self.close()
 
 
+def member_counts(members, counts):
+    """Step counts in member order for rd_batch_step_each; members missing
+    from ``counts`` take 0 steps, and a key that is not a member is an
+    error (its steps would otherwise be dropped without notice)."""
+    ids = {id(m) for m in members}
+    stray = [k for k in counts if id(k) not in ids]
+    if stray:
+        raise ValueError(f"{len(stray)} of the step counts name no member of the batch")
+    return [int(counts.get(m, 0)) for m in members]
+
+
 class Batch:
     """Contexts of one model and storage stepped by shared persistent launches."""
 
@@ -307,9 +318,9 @@ class Batch:
 
     def step_each(self, counts):
         """Advance each member by its own count: ``counts`` maps a member
-        Sim to its steps (members left out: 0)."""
-        arr = (ctypes.c_int64 * max(len(self.members), 1))(
-            *[int(counts.get(m, 0)) for m in self.members])
+        Sim to its steps (members left out: 0; a Sim that is not a member:
+        ValueError)."""
+        arr = (ctypes.c_int64 * max(len(self.members), 1))(*member_counts(self.members, counts))
         L.check(self.lib.rd_batch_step_each(self.b, arr), None, "rd_batch_step_each")
 
     def sync(self):

@@ -210,3 +210,16 @@ def test_validation_of_the_table1_cahn_hilliard_model(lib):
     c = _cfg(cfg)
     c.bc[2][0] = L.BC["dirichlet"]               # no held layer on c3
     assert q(c) == L.RD_EUNSUPPORTED
+
+
+def test_batch_step_counts_are_in_member_order_and_name_only_members():
+    from paper_1004_0480_gb300.sim import member_counts
+
+    class M:   # stands in for a Sim (members are compared by identity)
+        pass
+
+    a, b, c, stranger = M(), M(), M(), M()
+    assert member_counts([a, b, c], {c: 7, a: 2}) == [2, 0, 7]
+    assert member_counts([], {}) == []
+    with pytest.raises(ValueError):
+        member_counts([a, b], {a: 1, stranger: 3})
