@@ -149,20 +149,34 @@ def messages(p: SlabPlan):
     return sends, recvs
 
 
+def posting_order(p: SlabPlan):
+    """The exchange's sends and receives in the order every rank posts them:
+    by peer, then tag.  A backend that pairs the messages between two ranks
+    by their order and ignores tags (NCCL) then matches each send with the
+    receive meant for it, also where both neighbours are one rank (two
+    ranks, periodic z: a rank's lowest and highest owned planes both go to
+    the other rank)."""
+    sends, recvs = messages(p)
+    return sorted(sends), sorted(recvs)
+
+
 def exchange(slab, p: SlabPlan, dist):
     """Refill the slab's ghost planes from the neighbours' outermost owned
-    planes by point-to-point messages; receives are posted before sends."""
-    sends, recvs = messages(p)
-    reqs, landed = [], []
+    planes by point-to-point messages, posted as one batch
+    (``batch_isend_irecv``: a single NCCL group, so no rank's receive waits
+    behind its own sends; with NCCL the current CUDA device must be the
+    rank's own)."""
+    sends, recvs = posting_order(p)
+    if not sends and not recvs:
+        return
+    ops, landed = [], []
     for peer, tag, z0, k in recvs:
         buf = slab.empty(k)
-        reqs.append(dist.irecv(buf, src=peer, tag=tag))
+        ops.append(dist.P2POp(dist.irecv, buf, peer, tag=tag))
         landed.append((z0, k, buf))
-    outgoing = []
     for peer, tag, z0, k in sends:
-        outgoing.append(slab.read(z0, k))
-        reqs.append(dist.isend(outgoing[-1], dst=peer, tag=tag))
-    for r in reqs:
+        ops.append(dist.P2POp(dist.isend, slab.read(z0, k), peer, tag=tag))
+    for r in dist.batch_isend_irecv(ops):
         r.wait()
     for z0, k, buf in landed:
         slab.write(z0, k, buf)

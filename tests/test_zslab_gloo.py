@@ -158,3 +158,30 @@ def test_messages_pair_up():
             recvs = {(peer, r, tag): k for r, p in enumerate(plans)
                      for peer, tag, _, k in Z.messages(p)[1]}
             assert sends == recvs
+
+
+def test_messages_match_in_posting_order_without_tags():
+    # NCCL pairs the messages between two ranks by the order they are posted
+    # and ignores tags: the k-th send from A to B must be the k-th receive
+    # on B from A, for every pair, with the same tag and size
+    def pairs(order):
+        bad = 0
+        for cfg in CASES.values():
+            for ws in (2, 3, 4):
+                try:
+                    plans = [Z.plan(cfg, ws, r) for r in range(ws)]
+                except ValueError:
+                    continue
+                for a in range(ws):
+                    for b in range(ws):
+                        out = [(t, k) for peer, t, _, k in order(plans[a])[0] if peer == b]
+                        inc = [(t, k) for peer, t, _, k in order(plans[b])[1] if peer == a]
+                        assert len(out) == len(inc)
+                        bad += out != inc
+        return bad
+
+    assert pairs(Z.posting_order) == 0
+    # the order messages() lists them in would cross the two messages of a
+    # periodic two-rank split (a rank's lowest planes landing in the
+    # other's lower ghost planes)
+    assert pairs(Z.messages) > 0
