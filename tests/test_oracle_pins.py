@@ -134,6 +134,48 @@ def test_dense_operator_power(orc, bc):
     np.testing.assert_allclose(out, ref, rtol=0, atol=1e-13)
 
 
+def _three_point_1d(p, r, bc, n):
+    """The textbook explicit scheme u_i <- u_i + r (u_{i-1} - 2 u_i + u_{i+1}),
+    zero flux (u_{-1} = u_0, u_N = u_{N-1}) or periodic, n steps."""
+    u = [float(v) for v in p]
+    N = len(u)
+    for _ in range(n):
+        new = []
+        for i in range(N):
+            if bc == "periodic":
+                lo, hi = u[(i - 1) % N], u[(i + 1) % N]
+            else:
+                lo, hi = u[max(i - 1, 0)], u[min(i + 1, N - 1)]
+            new.append(u[i] + r * (lo - 2.0 * u[i] + hi))
+        u = new
+    return np.array(u)
+
+
+@pytest.mark.parametrize("impl", ["c", "np"])
+@pytest.mark.parametrize("bc", ["neumann", "periodic"])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_one_axis_profile_reduces_to_the_three_point_scheme(orc, impl, bc, axis):
+    # a field that varies along one axis only: the other axes' second
+    # differences vanish, and the 3-D step is the 1-D scheme with that
+    # axis's own D (every axis has a different one, so a D taken from the
+    # wrong axis, or a profile moved along the wrong axis, fails)
+    shape = (11, 7, 9)                       # (nx, ny, nz)
+    D = (0.9, 0.4, 0.15)
+    h, dt = 0.8, 0.1
+    cfg = _diff_cfg(shape, D=D, dt=dt, bc=bc, h=h)
+    N = shape[axis]
+    prof = np.random.default_rng(7 + axis).uniform(0.0, 2.0, N)
+    bshape = [1, 1, 1]
+    bshape[2 - axis] = N                     # arrays are (z, y, x)
+    c0 = np.broadcast_to(prof.reshape(bshape), shape[::-1]).copy()[None]
+    n = 20
+    want = _three_point_1d(prof, D[axis] * dt / h ** 2, bc, n)
+    run = orc.run if impl == "c" else orc.np_run
+    out = run(cfg, c0, n)[0]
+    np.testing.assert_allclose(out, np.broadcast_to(want.reshape(bshape), out.shape),
+                               rtol=0, atol=1e-13)
+
+
 # --------------------------------------------------------------------------
 # advection
 # --------------------------------------------------------------------------
