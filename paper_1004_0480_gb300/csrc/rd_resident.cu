@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <vector>
 
@@ -525,6 +526,7 @@ cudaError_t plan_st(bool plain, bool tma_ok, int nx, int ny, int nz, int Kf, int
                 if (occ < 1) continue;
                 const long long nty = (ny + ty - 1) / ty, ntz = (nz + tz - 1) / tz;
                 const long long tiles = nty * ntz;
+                if (tiles > INT_MAX) continue;    // the kernel counts tiles in int
                 const long long grid = std::min<long long>(tiles, (long long)occ * sms);
                 const double cost =
                     plan_cost(S, nvx, rw, ES, K, ty, tz, tiles, grid, sms, nt, tma);
