@@ -20,8 +20,9 @@ steps them with any callable (the CPU tests use the FP64 oracle);
 ``DeviceSlab`` keeps the fields on the rank's GPU in a context of the CUDA
 library, moves ghost planes with ``rd_copy_planes`` (device to device, the
 context's own layout) and steps with ``rd_step``.  ``exchange`` moves the
-planes with ``torch.distributed`` point-to-point messages (NCCL between
-GPUs, into each receiving GPU's own buffers; gloo on CPU);
+planes with ``torch.distributed`` point-to-point messages, posted as one
+batch in the same order on every rank (NCCL between GPUs, into each
+receiving GPU's own buffers; gloo on CPU);
 ``exchange_local`` moves them between slabs held by one process (the same
 messages, no collective).  ``owned_moments`` reduces the owned planes in
 FP64 and sums the ranks' results with an FP64 all-reduce.
