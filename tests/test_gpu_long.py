@@ -1,7 +1,9 @@
 """Long nonlinear runs on the GPU, beyond the horizon where FP32 and FP64
 trajectories stay close (rounding is amplified by the instabilities the
 problems are built on): the checks are the properties that hold at any
-length -- finiteness, positivity of concentrations, and the length scale of
+length -- finiteness, positivity of concentrations (also over the whole
+benchmark jobs: the 10 000-step 256^3 Brusselator and the 5 000-step
+512 x 512 x 64 air problem, autotuned as benchmarked), and the length scale of
 the Turing pattern, whose dominant wavelength the FP64 oracle puts at
 6.2-6.5 cells after 3 000 steps on the same grid (the linear dispersion of
 the Brusselator parameters peaks at q^2 ~ 0.83, 6.9 cells)."""
@@ -26,6 +28,15 @@ def rd():
 
 def run_gpu(rd, cfg, steps):
     with rd.Sim(cfg) as sim:
+        sim.set_fields(W.initial_fields(cfg))
+        sim.step(steps)
+        return sim.get_fields()
+
+
+def run_autotuned(rd, cfg, steps):
+    """The problem in the launch configuration the benchmark times."""
+    with rd.Sim(cfg) as sim:
+        sim.autotune()
         sim.set_fields(W.initial_fields(cfg))
         sim.step(steps)
         return sim.get_fields()
@@ -70,3 +81,24 @@ def test_air_species_stay_positive_over_5000_steps(rd):
     out = run_gpu(rd, cfg, 5000)
     assert np.all(np.isfinite(out))
     assert out.min() > 0.0
+
+
+def test_benchmark_brusselator_job_stays_bounded(rd):
+    # the whole 10 000-step job of the 256^3 periodic Brusselator, autotuned
+    # as the benchmark runs it: a saturated pattern, finite and positive
+    cfg = W.cfg_brusselator_256()
+    u, v = run_autotuned(rd, cfg, cfg["steps"])
+    ext = [float(u.min()), float(u.max()), float(v.min()), float(v.max())]
+    assert np.all(np.isfinite(u)) and np.all(np.isfinite(v)), ext
+    assert ext[0] > 0.0 and ext[2] > 0.0, ext
+    assert ext[1] < 20.0 and ext[3] < 20.0, ext
+    assert u.std() > 0.5, float(u.std())
+
+
+def test_benchmark_air_run_stays_finite_and_positive(rd):
+    # the full 5 000-step run of the 512 x 512 x 64 air problem, autotuned
+    cfg = W.cfg_air_512()
+    out = run_autotuned(rd, cfg, cfg["steps"])
+    ext = [(float(out[s].min()), float(out[s].max())) for s in range(3)]
+    assert np.all(np.isfinite(out)), ext
+    assert min(lo for lo, _ in ext) > 0.0, ext
